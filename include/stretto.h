@@ -1,0 +1,249 @@
+/*
+ * stretto.h -- C ABI of the B300 (sm_103a) KV-cache semantic operator library.
+ *
+ * The library evaluates a KV-cache-enabled semantic operator (filter or
+ * classify) over a table of tuples, in the three steps of Sec. 5 of the
+ * Stretto paper:
+ *
+ *   st_kv_build   offline KV-cache creation: every tuple's document is
+ *                 prefilled once through the decoder ("Offline: KV Cache
+ *                 Creation"); keys/values of every layer and kv head are kept
+ *                 with a query-agnostic retention score per slot.
+ *   st_kv_retain  query-agnostic compression to a retained fraction r
+ *                 (compression ratio 1 - r, the profiles of Sec. 5 and Sec. 6
+ *                 "Operators"): the top n_keep(L, r) slots per (layer, kv head),
+ *                 in rank order, optionally stored as FP8 E4M3.
+ *   st_op_eval    online execution ("Online: Query Execution"): the operator's
+ *                 prompt is appended after each cached document and forwarded
+ *                 in one batched pass; the logits of the label tokens are read
+ *                 at the last prompt position and turned into accept / reject /
+ *                 unsure with log-odds thresholds (Sec. 5; temperature-0 form
+ *                 of the soft-threshold equation of Sec. 4.1), or into a class.
+ *
+ * Conventions for every call
+ *   - Return value: ST_OK (0) or a positive ST_E* code; the message of the last
+ *     failure of a context is st_last_error(ctx).  Nothing aborts the process.
+ *   - "dev" pointers are CUDA device pointers owned by the caller; "host"
+ *     pointers are ordinary host memory owned by the caller.  The library never
+ *     frees caller memory and never keeps a caller pointer past the call,
+ *     except where stated.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue work on that stream and return without synchronising, unless
+ *     stated; outputs are valid once the stream reaches the enqueued work.
+ *   - Handles (st_ctx, st_kv, st_operator) are library-owned and not
+ *     thread-safe: use one handle from one host thread at a time.
+ *   - Weights, caches and workspaces are allocated by st_create, st_kv_alloc and
+ *     st_reserve; st_kv_build / st_kv_retain / st_op_eval allocate only when the
+ *     context's workspace must grow (never after st_reserve with the largest
+ *     sizes used).
+ */
+#ifndef STRETTO_H
+#define STRETTO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define ST_OK 0
+#define ST_EINVAL 1        /* invalid argument (message says which) */
+#define ST_ENOMEM 2        /* device allocation failed */
+#define ST_ECUDA 3         /* a CUDA runtime call failed */
+#define ST_ETIMEOUT 4      /* a bounded device wait gave up */
+#define ST_ENAN 5          /* a NaN retention score was found */
+#define ST_EUNSUPPORTED 6  /* shape not supported by the compiled kernels */
+
+/* ---- element types ---- */
+#define ST_F32 0           /* IEEE float32 */
+#define ST_BF16 1          /* bfloat16 */
+#define ST_E4M3 2          /* OCP FP8 E4M3 with per-(64-slot block) float32 scales */
+
+/* ---- operator kinds and filter decisions ---- */
+#define ST_OP_FILTER 0     /* binary filter: label_ids = {accept token, reject token} */
+#define ST_OP_CLASSIFY 1   /* n-way classify: argmax_k (z_k + bias_k), ties to lowest k */
+#define ST_REJECT 0
+#define ST_ACCEPT 1
+#define ST_UNSURE 2
+
+typedef struct st_ctx st_ctx;            /* model weights + workspace */
+typedef struct st_kv st_kv;              /* the KV caches of one table */
+typedef struct st_operator st_operator;  /* one operator's prompt, labels, r, thresholds */
+
+/* Decoder shape (Llama-style, pre-norm; RMSNorm without gains; RoPE
+ * rotate-half with frequencies rope_theta^(-2i/hd); SwiGLU FFN; untied LM head). */
+typedef struct {
+  int32_t layers;      /* decoder layers */
+  int32_t d;           /* model width */
+  int32_t hq, hkv;     /* query heads, key/value heads (hq % hkv == 0) */
+  int32_t hd;          /* head dim: 32 or 64 (ST_F32), 64 (ST_BF16) */
+  int32_t ffn;         /* SwiGLU hidden width (multiple of 128) */
+  int32_t vocab;       /* vocabulary size */
+  int32_t dtype;       /* ST_F32 or ST_BF16: weights, activations and the full cache */
+  int32_t max_pos;     /* largest position + 1 any call may use (document + prompt) */
+  float rope_theta;    /* RoPE base (10000) */
+  float eps;           /* RMSNorm epsilon (1e-5) */
+} st_model_cfg;
+
+/* One operator (Sec. 5 "Online: Query Execution"). */
+typedef struct {
+  const int32_t* prompt;     /* host [P] prompt token ids, each < vocab */
+  int32_t P;                 /* prompt length, 1..256 */
+  const int32_t* label_ids;  /* host [n_labels] label token ids; filter: {accept, reject} */
+  int32_t n_labels;          /* 2 for ST_OP_FILTER; 2..8 for ST_OP_CLASSIFY */
+  int32_t kind;              /* ST_OP_FILTER or ST_OP_CLASSIFY */
+  double r;                  /* retained fraction in (0, 1] of the KV profile it reads */
+  float theta_pos;           /* filter: accept iff s - theta_pos is the unique largest of
+                                (s - theta_pos, theta_neg - s, 0), s = z_accept - z_reject */
+  float theta_neg;           /* filter: reject threshold (ties: unsure, then reject) */
+  const float* bias;         /* host [n_labels] classify bias, or NULL for zeros */
+} st_op;
+
+/* ---- context ---- */
+
+/* Create a context holding a packed copy of the model weights.
+ * weights: 2 + 7*layers DEVICE pointers of cfg->dtype elements, row-major
+ *   [out][in], in this order: embed [vocab][d]; per layer wq [hq*hd][d],
+ *   wk [hkv*hd][d], wv [hkv*hd][d], wo [d][hq*hd], wg [ffn][d], wu [ffn][d],
+ *   wd [d][ffn]; then w_lm [vocab][d].  They are copied (the caller may free
+ *   them after the stream has passed this call's copies; the call synchronises
+ *   `stream` before returning).
+ * Errors: ST_EINVAL on an unsupported shape, ST_ENOMEM, ST_ECUDA. */
+int st_create(const st_model_cfg* cfg, const void* const* weights, void* stream, st_ctx** out);
+void st_destroy(st_ctx* ctx);
+const char* st_last_error(const st_ctx* ctx);   /* never NULL; "" when no error */
+const char* st_version(void);
+
+/* Pre-size the context's workspace for kv_build chunks of up to `build_rows`
+ * document tokens and op_eval batches of up to `eval_rows` prompt rows
+ * (tuples * P), so that later calls allocate nothing. */
+int st_reserve(st_ctx* ctx, int64_t build_rows, int64_t eval_rows);
+
+/* ---- KV caches ---- */
+
+/* Allocate the caches of a table of T tuples whose document i spans tokens
+ * offsets_host[i] .. offsets_host[i+1]-1 (monotone, offsets_host[0] == 0,
+ * every length in 1 .. max_pos-1).  Sizes the full cache (dtype of the model)
+ * and the retained cache for any r <= 1 (either dtype).
+ * Errors: ST_EINVAL (bad offsets), ST_ENOMEM. */
+int st_kv_alloc(st_ctx* ctx, const int64_t* offsets_host, int32_t T, st_kv** out);
+void st_kv_free(st_kv* kv);
+
+/* Offline KV-cache creation (Sec. 5).  tokens_dev: DEVICE int32 [offsets[T]]
+ * token ids (< vocab; not checked on the device).  Fills, for every layer l,
+ * kv head g and document slot j (positions 0..L-1, causal prefill of the
+ * document alone): the post-RoPE key and value, the retention score
+ *   score = mu.k/sqrt(hd) + sum_c sigma2_c k_c^2/(2 hd) + ln(||v|| + 1e-12)
+ * (mu, sigma2: mean and population variance of the group's post-RoPE queries
+ * over the document), and the pooled final-normed last-layer state of every
+ * tuple.  Processed in chunks of whole tuples. */
+int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, void* stream);
+
+/* Query-agnostic retention (Sec. 5): per tuple, layer and kv head, rank all
+ * slots by (score descending, slot index ascending; -0 == +0) and keep the
+ * first n_keep(L, r) = clamp(floor(r*L + 0.5), 1, L) (IEEE double arithmetic)
+ * in rank order, as kv_dtype (the model dtype, or ST_E4M3 with one float32
+ * scale = amax/448 per 64-slot block for K and for V).  Replaces the previous
+ * retained profile of `kv`.  A NaN score sets the device status read by
+ * st_kv_status (ST_ENAN). Errors: ST_EINVAL (r outside (0,1], kv_dtype). */
+int st_kv_retain(st_ctx* ctx, st_kv* kv, double r, int32_t kv_dtype, void* stream);
+
+/* Device status of the context's bounded waits: synchronises `stream`,
+ * returns ST_OK or ST_ETIMEOUT (a tcgen05 pipeline wait gave up; the kernel
+ * returned early and its outputs are invalid), and clears it. */
+int st_status(st_ctx* ctx, void* stream);
+
+/* Device status of the last retain on `kv`: synchronises `stream`, returns
+ * ST_OK or ST_ENAN (and clears it). */
+int st_kv_status(st_ctx* ctx, st_kv* kv, void* stream);
+
+/* Read-only device views of the cache buffers, for inspection and tests.
+ * which: see ST_VIEW_*.  *ptr receives a DEVICE pointer owned by `kv`, *bytes
+ * its size.  Layouts:
+ *   ST_VIEW_K / ST_VIEW_V        full cache, model dtype [layers][hkv][R][hd], R = offsets[T]
+ *   ST_VIEW_SCORES               float32 [layers][hkv][R]
+ *   ST_VIEW_POOLED               float32 [T][d]
+ *   ST_VIEW_RANK                 int32 [layers][hkv][R]: per tuple segment, slot indices
+ *                                (0..L-1) in rank order (valid after st_kv_retain)
+ *   ST_VIEW_KR / ST_VIEW_VR      retained cache [layers][hkv][Rp][hd] (model dtype, or one
+ *                                byte per E4M3 code); tuple i occupies rows
+ *                                offp[i] .. offp[i]+n_i-1, zero-filled to offp[i+1]
+ *   ST_VIEW_SCALES               float32 [layers][hkv][Rp/64][2] (K scale, V scale)
+ *   ST_VIEW_OFFP                 int64 [T+1] padded offsets (multiples of 64)
+ *   ST_VIEW_NKEEP                int32 [T] retained counts n_i */
+#define ST_VIEW_K 0
+#define ST_VIEW_V 1
+#define ST_VIEW_SCORES 2
+#define ST_VIEW_POOLED 3
+#define ST_VIEW_RANK 4
+#define ST_VIEW_KR 5
+#define ST_VIEW_VR 6
+#define ST_VIEW_SCALES 7
+#define ST_VIEW_OFFP 8
+#define ST_VIEW_NKEEP 9
+int st_kv_view(const st_kv* kv, int32_t which, void** ptr, size_t* bytes);
+/* Copy min(bytes, size of the view) bytes of a view into caller DEVICE memory
+ * dst_dev, enqueued on `stream`. */
+int st_kv_read(const st_kv* kv, int32_t which, void* dst_dev, size_t bytes, void* stream);
+
+/* ---- operators ---- */
+
+/* Upload an operator's prompt, labels and bias once (synchronous).
+ * Errors: ST_EINVAL (P, n_labels, ids out of range, r outside (0,1]). */
+int st_op_create(st_ctx* ctx, const st_op* op, st_operator** out);
+void st_op_free(st_operator* op);
+
+/* Online execution of one operator (Sec. 5) on the tuples tuple_ids_dev[0..n-1]
+ * (DEVICE int32, each < T, not checked on the device) of `kv`, whose retained
+ * profile must have r >= op->r (a smaller r reads the rank-order prefix
+ * n_keep(L, op->r), which is exactly the smaller profile's set).
+ * Outputs: logits_dev DEVICE float32 [n][n_labels] (label-token logits at the
+ * last prompt position), labels_dev DEVICE int32 [n] (ST_ACCEPT / ST_REJECT /
+ * ST_UNSURE for a filter, the class index for classify).
+ * Errors: ST_EINVAL (no retained profile, op->r above it, n < 0). */
+int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
+               const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
+               int32_t* labels_dev, void* stream);
+
+/* The whole path from HOST buffers: copy tokens_host (int32 [offsets[T]]) to
+ * the device, st_kv_build, st_kv_retain(op->r, kv_dtype), st_op_eval over all
+ * T tuples, and copy logits (float32 [T][n_labels]) and labels (int32 [T]) back
+ * to host memory.  Synchronises `stream` before returning. */
+int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,
+                const int32_t* tokens_host, float* logits_host, int32_t* labels_host,
+                void* stream);
+
+/* ---- kernel self-test entry ---- */
+
+/* The projection GEMM of the context's precision with a plain store epilogue:
+ * C_dev (float32 [M][N]) = A_dev ([M][K], model dtype) . W_dev ([N][K], model
+ * dtype)^T, row-major, on the tcgen05 path for ST_BF16 contexts and the
+ * CUDA-core path for ST_F32.  Shapes must satisfy the kernels' tiling (bf16:
+ * N % 256 == 0, K % 64 == 0). */
+int st_gemm(st_ctx* ctx, const void* A_dev, const void* W_dev, int32_t M, int32_t N, int32_t K,
+            float* C_dev, void* stream);
+
+/* ---- per-kernel timing (CUDA events on the launching stream) ---- */
+
+/* When enabled, every launch of the library's kernels is bracketed by CUDA
+ * events; st_prof_read sums, per kernel family, the launches, total device
+ * milliseconds and the algorithmic FLOPs and bytes of those launches.
+ * families: ST_PROF_GEMM, ST_PROF_ATTN, ST_PROF_RETAIN, ST_PROF_OTHER. */
+#define ST_PROF_GEMM 0
+#define ST_PROF_ATTN 1
+#define ST_PROF_RETAIN 2
+#define ST_PROF_OTHER 3
+#define ST_PROF_N 4
+int st_prof_enable(st_ctx* ctx, int32_t on);
+/* Synchronises all pending events; out[f] = {launches, ms, flops, bytes}. */
+int st_prof_read(st_ctx* ctx, double* out /* [ST_PROF_N][4] */);
+int st_prof_reset(st_ctx* ctx);
+/* Number of kernel launches the library enqueued since the last reset. */
+int64_t st_launch_count(const st_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STRETTO_H */

@@ -1,0 +1,913 @@
+// C ABI of libstretto: argument validation, memory, chunking and kernel
+// sequencing of the three steps of Sec. 5 (offline cache creation, retention,
+// online operator evaluation).  Every arithmetic step runs in a CUDA kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace st;
+
+namespace {
+
+thread_local std::string g_err;   // errors raised before a context exists
+
+int fail(const st_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) const_cast<st_ctx*>(ctx)->err = msg;
+  else g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, ST_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+#define CKLAUNCH()                                                                       \
+  do {                                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, ST_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+int dev_alloc(st_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return ST_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, ST_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  return ST_OK;
+}
+
+int grow(st_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return ST_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  int rc = dev_alloc(ctx, &b.p, bytes);
+  if (rc == ST_OK) b.bytes = bytes;
+  return rc;
+}
+
+// Carves aligned sub-buffers out of one workspace.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base((char*)b) {}
+  template <typename T> T* take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = (T*)(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+int n_keep_host(int64_t L, double r) {
+  volatile double rl = r * (double)L;   // rounded product, then the add (no fused multiply-add)
+  double n = std::floor(rl + 0.5);
+  if (n < 1) n = 1;
+  if (n > (double)L) n = (double)L;
+  return (int)n;
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---- chunk plan of kv_build: whole tuples, at most `cap` rows per chunk
+struct Chunk { int t0, t1; int64_t r0, rows; };
+
+std::vector<Chunk> plan_chunks(const std::vector<int64_t>& off, int64_t cap) {
+  std::vector<Chunk> out;
+  int T = (int)off.size() - 1;
+  int t = 0;
+  while (t < T) {
+    Chunk c{t, t, off[t], 0};
+    while (c.t1 < T && (c.t1 == c.t0 || off[c.t1 + 1] - off[c.t0] <= cap)) c.t1++;
+    c.rows = off[c.t1] - off[c.t0];
+    out.push_back(c);
+    t = c.t1;
+  }
+  return out;
+}
+
+struct BuildWs {
+  float *x, *inv_rms, *mu, *s2, *tmp;
+  void *xn, *q, *o, *h;
+  int32_t *rowtup, *pos;
+};
+
+size_t build_ws_bytes(const st_ctx* ctx, int64_t rows, int64_t tuples, BuildWs* w, void* base) {
+  const st_model_cfg& c = ctx->cfg;
+  Carve cv(base ? base : (void*)0);
+  const size_t e = ctx->esz;
+  BuildWs ws;
+  ws.x = cv.take<float>(rows * c.d);
+  ws.inv_rms = cv.take<float>(rows);
+  ws.mu = cv.take<float>(tuples * c.hkv * c.hd);
+  ws.s2 = cv.take<float>(tuples * c.hkv * c.hd);
+  ws.xn = cv.take<char>(rows * c.d * e);
+  ws.q = cv.take<char>(rows * c.hq * c.hd * e);
+  ws.o = cv.take<char>(rows * c.hq * c.hd * e);
+  ws.h = cv.take<char>(rows * c.ffn * e);
+  ws.tmp = c.dtype == ST_F32 ? cv.take<float>(rows * 2 * c.ffn) : nullptr;
+  ws.rowtup = cv.take<int32_t>(rows);
+  ws.pos = cv.take<int32_t>(rows);
+  if (w) *w = ws;
+  return cv.off + 256;
+}
+
+struct EvalWs {
+  float *x, *tmp;
+  void *xn, *q, *kp, *vp, *o, *h;
+  int32_t *pos, *tup, *len, *nk;
+};
+
+size_t eval_ws_bytes(const st_ctx* ctx, int64_t rows, int64_t tuples, EvalWs* w, void* base) {
+  const st_model_cfg& c = ctx->cfg;
+  Carve cv(base ? base : (void*)0);
+  const size_t e = ctx->esz;
+  EvalWs ws;
+  ws.x = cv.take<float>(rows * c.d);
+  ws.xn = cv.take<char>(rows * c.d * e);
+  ws.q = cv.take<char>(rows * c.hq * c.hd * e);
+  ws.kp = cv.take<char>(rows * c.hkv * c.hd * e);
+  ws.vp = cv.take<char>(rows * c.hkv * c.hd * e);
+  ws.o = cv.take<char>(rows * c.hq * c.hd * e);
+  ws.h = cv.take<char>(rows * c.ffn * e);
+  ws.tmp = c.dtype == ST_F32 ? cv.take<float>(rows * 2 * c.ffn) : nullptr;
+  ws.pos = cv.take<int32_t>(rows);
+  ws.tup = cv.take<int32_t>(tuples);
+  ws.len = cv.take<int32_t>(tuples);
+  ws.nk = cv.take<int32_t>(tuples);
+  if (w) *w = ws;
+  return cv.off + 256;
+}
+
+const int64_t kDefaultBuildRows = 1 << 20;
+const int64_t kDefaultEvalRows = 1 << 18;
+
+}  // namespace
+
+// ------------------------------------------------------------------ profiling
+namespace st {
+static cudaEvent_t take_event(st_ctx* ctx) {
+  if (!ctx->prof.pool.empty()) {
+    cudaEvent_t e = ctx->prof.pool.back();
+    ctx->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+Launch::Launch(st_ctx* c, cudaStream_t st, int fam, double fl, double by)
+    : ctx(c), s(st), family(fam), flops(fl), bytes(by) {
+  ctx->launches++;
+  if (ctx->prof.on) {
+    rec.family = fam;
+    rec.flops = fl;
+    rec.bytes = by;
+    rec.a = take_event(ctx);
+    rec.b = take_event(ctx);
+    cudaEventRecord(rec.a, s);
+  }
+}
+Launch::~Launch() {
+  if (ctx->prof.on) {
+    cudaEventRecord(rec.b, s);
+    ctx->prof.pending.push_back(rec);
+  }
+}
+}  // namespace st
+
+// ------------------------------------------------------------------ internal step helpers
+namespace {
+
+// One projection: dispatches to the tensor-core GEMM (bf16) or the CUDA-core GEMM (f32).
+int project(st_ctx* ctx, const void* A, const void* W, int M, int N, int K, EpiParams ep,
+            float* tmp, void* h_out, cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  ep.M = M;
+  ep.N = N;
+  if (M <= 0) return ST_OK;
+  const double flops = 2.0 * M * (double)N * K;
+  const double bytes = ((double)M * K + (double)N * K) * ctx->esz;
+  if (c.dtype == ST_BF16) {
+    Launch L(ctx, s, ST_PROF_GEMM, flops, bytes);
+    int rc = gemm_tc((const bf16*)A, (const bf16*)W, M, N, K, ep, ctx->dstatus, s);
+    if (rc != ST_OK) return fail(ctx, rc, "tcgen05 GEMM: unsupported shape or tensor-map encoding failed");
+  } else if (ep.mode == EPI_SWIGLU) {
+    EpiParams e2 = ep;
+    e2.mode = EPI_STORE_F32;
+    e2.out = tmp;
+    e2.ld = N;
+    {
+      Launch L(ctx, s, ST_PROF_GEMM, flops, bytes);
+      gemm_simt<float>((const float*)A, (const float*)W, M, N, K, e2, s);
+    }
+    Launch L2(ctx, s, ST_PROF_OTHER, 0, 0);
+    swiglu_from_f32(tmp, M, N / 2, (float*)h_out, s);
+  } else {
+    Launch L(ctx, s, ST_PROF_GEMM, flops, bytes);
+    gemm_simt<float>((const float*)A, (const float*)W, M, N, K, ep, s);
+  }
+  CKLAUNCH();
+  return ST_OK;
+}
+
+int rmsnorm(st_ctx* ctx, const float* x, int64_t rows, void* xn, float* inv, cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+  if (c.dtype == ST_BF16) rmsnorm_rows<bf16>(x, rows, c.d, c.eps, (bf16*)xn, inv, s);
+  else rmsnorm_rows<float>(x, rows, c.d, c.eps, (float*)xn, inv, s);
+  CKLAUNCH();
+  return ST_OK;
+}
+
+int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_items,
+              cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  Launch L(ctx, s, ST_PROF_ATTN, 0, 0);
+  if (c.dtype == ST_F32) {
+    attn_simt<float, float>(a, s);
+  } else if (a.mode == 0) {
+    attn_mma_prefill(a, items, n_items, s);
+  } else {
+    attn_mma_eval(a, s);
+  }
+  CKLAUNCH();
+  return ST_OK;
+}
+
+#define RC(x)                       \
+  do {                              \
+    int rc_ = (x);                  \
+    if (rc_ != ST_OK) return rc_;   \
+  } while (0)
+
+}  // namespace
+
+// ================================================================== context
+extern "C" const char* st_version(void) { return "stretto-b300 0.1 (sm_103a)"; }
+
+extern "C" const char* st_last_error(const st_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+extern "C" int st_create(const st_model_cfg* cfg, const void* const* weights, void* stream,
+                         st_ctx** out) {
+  st_ctx* ctx = nullptr;
+  if (!cfg || !weights || !out) return fail(nullptr, ST_EINVAL, "st_create: NULL argument");
+  *out = nullptr;
+  const st_model_cfg& c = *cfg;
+  if (c.layers < 1 || c.d < 128 || c.d % 128 || c.hq < 1 || c.hkv < 1 || c.hq % c.hkv ||
+      c.ffn < 128 || c.ffn % 128 || c.vocab < 2 || c.max_pos < 2 || !(c.eps > 0) ||
+      !(c.rope_theta > 0))
+    return fail(nullptr, ST_EINVAL, "st_create: invalid model shape");
+  if (c.dtype == ST_F32) {
+    if (c.hd != 32 && c.hd != 64) return fail(nullptr, ST_EUNSUPPORTED, "f32 model: hd must be 32 or 64");
+    if (((c.hq + 2 * c.hkv) * c.hd) % (4 * c.hd) || c.d % 128 || (c.hq * c.hd) % 16)
+      return fail(nullptr, ST_EUNSUPPORTED, "f32 model: projection widths not tileable");
+  } else if (c.dtype == ST_BF16) {
+    if (c.hd != 64) return fail(nullptr, ST_EUNSUPPORTED, "bf16 model: hd must be 64");
+    const int nq = (c.hq + 2 * c.hkv) * c.hd;
+    if (!gemm_tc_supported(128, nq, c.d) || !gemm_tc_supported(128, c.d, c.hq * c.hd) ||
+        !gemm_tc_supported(128, 2 * c.ffn, c.d) || !gemm_tc_supported(128, c.d, c.ffn))
+      return fail(nullptr, ST_EUNSUPPORTED, "bf16 model: projection shapes not supported by the tcgen05 GEMM");
+  } else {
+    return fail(nullptr, ST_EINVAL, "st_create: dtype must be ST_F32 or ST_BF16");
+  }
+  ctx = new st_ctx();
+  ctx->cfg = c;
+  ctx->esz = c.dtype == ST_F32 ? 4 : 2;
+  cudaGetDevice(&ctx->device);
+  cudaStream_t s = S(stream);
+  const size_t e = ctx->esz;
+  const size_t d = c.d, qd = (size_t)c.hq * c.hd, kd = (size_t)c.hkv * c.hd, f = c.ffn;
+  auto cleanup_fail = [&](int rc) { st_destroy(ctx); return rc; };
+  auto copy = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+  };
+  int rc;
+  if ((rc = dev_alloc(ctx, &ctx->embed, c.vocab * d * e))) { g_err = ctx->err; return cleanup_fail(rc); }
+  if ((rc = dev_alloc(ctx, &ctx->w_lm, c.vocab * d * e))) { g_err = ctx->err; return cleanup_fail(rc); }
+  copy(ctx->embed, weights[0], c.vocab * d * e);
+  copy(ctx->w_lm, weights[1 + 7 * c.layers], c.vocab * d * e);
+  ctx->layers.resize(c.layers);
+  for (int l = 0; l < c.layers; ++l) {
+    LayerW& L = ctx->layers[l];
+    const void* const* w = weights + 1 + 7 * l;
+    if ((rc = dev_alloc(ctx, &L.wqkv, (qd + 2 * kd) * d * e)) ||
+        (rc = dev_alloc(ctx, &L.wo, d * qd * e)) || (rc = dev_alloc(ctx, &L.wgu, 2 * f * d * e)) ||
+        (rc = dev_alloc(ctx, &L.wd, d * f * e))) {
+      g_err = ctx->err;
+      return cleanup_fail(rc);
+    }
+    copy(L.wqkv, w[0], qd * d * e);
+    copy((char*)L.wqkv + qd * d * e, w[1], kd * d * e);
+    copy((char*)L.wqkv + (qd + kd) * d * e, w[2], kd * d * e);
+    copy(L.wo, w[3], d * qd * e);
+    // gate / up interleaved in blocks of 128 rows: [g0..g127, u0..u127, g128.., u128..]
+    cudaMemcpy2DAsync(L.wgu, 256 * d * e, w[4], 128 * d * e, 128 * d * e, f / 128, cudaMemcpyDefault, s);
+    cudaMemcpy2DAsync((char*)L.wgu + 128 * d * e, 256 * d * e, w[5], 128 * d * e, 128 * d * e,
+                      f / 128, cudaMemcpyDefault, s);
+    copy(L.wd, w[6], d * f * e);
+  }
+  // RoPE table: cos / sin of pos * theta^(-2i/hd), computed in double on the host.
+  const int half = c.hd / 2;
+  std::vector<float2> tab((size_t)c.max_pos * half);
+  for (int p = 0; p < c.max_pos; ++p)
+    for (int i = 0; i < half; ++i) {
+      double ang = (double)p * std::pow((double)c.rope_theta, -2.0 * i / c.hd);
+      tab[(size_t)p * half + i] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  if ((rc = dev_alloc(ctx, (void**)&ctx->rope, tab.size() * sizeof(float2)))) {
+    g_err = ctx->err;
+    return cleanup_fail(rc);
+  }
+  copy(ctx->rope, tab.data(), tab.size() * sizeof(float2));
+  if ((rc = dev_alloc(ctx, (void**)&ctx->dstatus, sizeof(int32_t)))) {
+    g_err = ctx->err;
+    return cleanup_fail(rc);
+  }
+  cudaMemsetAsync(ctx->dstatus, 0, sizeof(int32_t), s);
+  cudaError_t err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) {
+    g_err = std::string("st_create: ") + cudaGetErrorString(err);
+    return cleanup_fail(ST_ECUDA);
+  }
+  *out = ctx;
+  return ST_OK;
+}
+
+extern "C" void st_destroy(st_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  cudaFree(ctx->embed);
+  cudaFree(ctx->w_lm);
+  for (auto& L : ctx->layers) {
+    cudaFree(L.wqkv);
+    cudaFree(L.wo);
+    cudaFree(L.wgu);
+    cudaFree(L.wd);
+  }
+  cudaFree(ctx->rope);
+  cudaFree(ctx->dstatus);
+  cudaFree(ctx->ws_build.p);
+  cudaFree(ctx->ws_eval.p);
+  for (auto& r : ctx->prof.pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->prof.pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+extern "C" int st_reserve(st_ctx* ctx, int64_t build_rows, int64_t eval_rows) {
+  if (!ctx || build_rows < 0 || eval_rows < 0) return fail(ctx, ST_EINVAL, "st_reserve: bad argument");
+  if (build_rows > 0) {
+    ctx->build_rows_cap = build_rows;
+    RC(grow(ctx, ctx->ws_build, build_ws_bytes(ctx, build_rows, build_rows, nullptr, nullptr)));
+  }
+  if (eval_rows > 0) {
+    ctx->eval_rows_cap = eval_rows;
+    RC(grow(ctx, ctx->ws_eval, eval_ws_bytes(ctx, eval_rows, eval_rows, nullptr, nullptr)));
+  }
+  return ST_OK;
+}
+
+// ================================================================== KV caches
+extern "C" int st_kv_alloc(st_ctx* ctx, const int64_t* offsets_host, int32_t T, st_kv** out) {
+  if (!ctx || !offsets_host || !out || T < 1) return fail(ctx, ST_EINVAL, "st_kv_alloc: bad argument");
+  *out = nullptr;
+  const st_model_cfg& c = ctx->cfg;
+  if (offsets_host[0] != 0) return fail(ctx, ST_EINVAL, "st_kv_alloc: offsets[0] must be 0");
+  int64_t max_len = 0, rp = 0;
+  for (int t = 0; t < T; ++t) {
+    int64_t L = offsets_host[t + 1] - offsets_host[t];
+    if (L < 1) return fail(ctx, ST_EINVAL, "st_kv_alloc: every document needs >= 1 token");
+    if (L > c.max_pos - 1) return fail(ctx, ST_EINVAL, "st_kv_alloc: document longer than max_pos - 1");
+    if (L > 16384) return fail(ctx, ST_EUNSUPPORTED, "st_kv_alloc: documents are limited to 16384 tokens");
+    max_len = std::max(max_len, L);
+    rp += (L + 63) & ~63LL;
+  }
+  st_kv* kv = new st_kv();
+  kv->ctx = ctx;
+  kv->T = T;
+  kv->R = offsets_host[T];
+  kv->Rp_cap = rp;
+  kv->max_len = (int32_t)max_len;
+  kv->off_h.assign(offsets_host, offsets_host + T + 1);
+  const size_t e = ctx->esz, LH = (size_t)c.layers * c.hkv;
+  int rc = ST_OK;
+  auto A = [&](void** p, size_t bytes) {
+    if (rc == ST_OK) rc = dev_alloc(ctx, p, bytes);
+  };
+  A((void**)&kv->off, (T + 1) * sizeof(int64_t));
+  A(&kv->K, LH * kv->R * c.hd * e);
+  A(&kv->V, LH * kv->R * c.hd * e);
+  A((void**)&kv->scores, LH * kv->R * sizeof(float));
+  A((void**)&kv->pooled, (size_t)T * c.d * sizeof(float));
+  A((void**)&kv->rank, LH * kv->R * sizeof(int32_t));
+  A(&kv->Kr, LH * rp * c.hd * e);
+  A(&kv->Vr, LH * rp * c.hd * e);
+  A((void**)&kv->scales, LH * (rp / 64) * 2 * sizeof(float));
+  A((void**)&kv->offp, (T + 1) * sizeof(int64_t));
+  A((void**)&kv->nkeep, T * sizeof(int32_t));
+  A((void**)&kv->status, sizeof(int32_t));
+  if (rc != ST_OK) {
+    st_kv_free(kv);
+    return rc;
+  }
+  cudaMemcpy(kv->off, offsets_host, (T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaMemset(kv->status, 0, sizeof(int32_t));
+  cudaError_t err = cudaDeviceSynchronize();
+  if (err != cudaSuccess) {
+    st_kv_free(kv);
+    return fail(ctx, ST_ECUDA, std::string("st_kv_alloc: ") + cudaGetErrorString(err));
+  }
+  // prefill work items for the tensor-core attention: (tuple, 32-position query block)
+  const int qb = 128 / (c.hq / c.hkv);   // document positions per 128-row query block
+  std::vector<int32_t> items;
+  for (int t = 0; t < T; ++t) {
+    int64_t L = offsets_host[t + 1] - offsets_host[t];
+    for (int64_t j = 0; j < L; j += qb) {
+      items.push_back(t);
+      items.push_back((int32_t)j);
+    }
+  }
+  kv->n_items = (int64_t)items.size() / 2;
+  rc = dev_alloc(ctx, (void**)&kv->items, items.size() * sizeof(int32_t));
+  if (rc != ST_OK) {
+    st_kv_free(kv);
+    return rc;
+  }
+  cudaMemcpy(kv->items, items.data(), items.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  // item ranges per tuple, for chunked builds
+  kv->item_start.resize(T + 1);
+  int64_t acc = 0;
+  for (int t = 0; t < T; ++t) {
+    kv->item_start[t] = acc;
+    acc += (offsets_host[t + 1] - offsets_host[t] + qb - 1) / qb;
+  }
+  kv->item_start[T] = acc;
+  *out = kv;
+  return ST_OK;
+}
+
+extern "C" void st_kv_free(st_kv* kv) {
+  if (!kv) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {kv->off, kv->K, kv->V, kv->scores, kv->pooled, kv->rank, kv->Kr, kv->Vr,
+                  kv->scales, kv->offp, kv->nkeep, kv->status, kv->items, kv->tok, kv->iota};
+  for (void* p : ptrs) cudaFree(p);
+  delete kv;
+}
+
+extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, void* stream) {
+  if (!ctx || !kv || !tokens_dev || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_build: bad argument");
+  const st_model_cfg& c = ctx->cfg;
+  cudaStream_t s = S(stream);
+  const int64_t cap = std::max<int64_t>(ctx->build_rows_cap > 0 ? ctx->build_rows_cap : kDefaultBuildRows,
+                                        kv->max_len);
+  std::vector<Chunk> chunks = plan_chunks(kv->off_h, cap);
+  int64_t max_rows = 0, max_tup = 0;
+  for (auto& ch : chunks) {
+    max_rows = std::max(max_rows, ch.rows);
+    max_tup = std::max<int64_t>(max_tup, ch.t1 - ch.t0);
+  }
+  RC(grow(ctx, ctx->ws_build, build_ws_bytes(ctx, max_rows, max_tup, nullptr, nullptr)));
+  BuildWs w;
+  build_ws_bytes(ctx, max_rows, max_tup, &w, ctx->ws_build.p);
+  const size_t e = ctx->esz;
+  const int qd = c.hq * c.hd, kd = c.hkv * c.hd, nqkv = qd + 2 * kd;
+  for (const Chunk& ch : chunks) {
+    const int M = (int)ch.rows;
+    {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      build_rowinfo(kv->off, ch.t0, ch.t1, ch.r0, ch.rows, w.rowtup, w.pos, s);
+    }
+    {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      if (c.dtype == ST_BF16) embed_rows<bf16>(tokens_dev + ch.r0, ch.rows, (const bf16*)ctx->embed, c.d, w.x, s);
+      else embed_rows<float>(tokens_dev + ch.r0, ch.rows, (const float*)ctx->embed, c.d, w.x, s);
+    }
+    CKLAUNCH();
+    for (int l = 0; l < c.layers; ++l) {
+      const LayerW& LW = ctx->layers[l];
+      char* Kl = (char*)kv->K + (size_t)l * c.hkv * kv->R * c.hd * e;
+      char* Vl = (char*)kv->V + (size_t)l * c.hkv * kv->R * c.hd * e;
+      RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
+      EpiParams ep;
+      ep.mode = EPI_QKV;
+      ep.q = w.q;
+      ep.kbase = Kl + (size_t)ch.r0 * c.hd * e;
+      ep.vbase = Vl + (size_t)ch.r0 * c.hd * e;
+      ep.kv_sg = kv->R * c.hd;
+      ep.kv_sr = c.hd;
+      ep.pos = w.pos;
+      ep.rope = ctx->rope;
+      ep.hq = c.hq;
+      ep.hkv = c.hkv;
+      ep.hd = c.hd;
+      RC(project(ctx, w.xn, LW.wqkv, M, nqkv, c.d, ep, w.tmp, nullptr, s));
+      // causal attention of the document onto itself
+      AttnParams a;
+      a.mode = 0;
+      a.q = w.q;
+      a.o = w.o;
+      a.hq = c.hq;
+      a.hkv = c.hkv;
+      a.hd = c.hd;
+      a.scale = 1.0f / std::sqrt((float)c.hd);
+      a.K = Kl;
+      a.V = Vl;
+      a.R = kv->R;
+      a.off = kv->off;
+      a.rowtup = w.rowtup;
+      a.pos = w.pos;
+      a.r0 = ch.r0;
+      a.rows = ch.rows;
+      const int64_t i0 = kv->item_start[ch.t0], i1 = kv->item_start[ch.t1];
+      RC(attention(ctx, a, kv->items + 2 * i0, (int)(i1 - i0), s));
+      // retention statistics and scores of this layer
+      {
+        Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+        if (c.dtype == ST_BF16) {
+          qstats<bf16>((const bf16*)w.q, kv->off, ch.t0, ch.t1, ch.r0, c.hq, c.hkv, c.hd, w.mu, w.s2, s);
+        } else {
+          qstats<float>((const float*)w.q, kv->off, ch.t0, ch.t1, ch.r0, c.hq, c.hkv, c.hd, w.mu, w.s2, s);
+        }
+      }
+      {
+        Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+        float* sl = kv->scores + (size_t)l * c.hkv * kv->R;
+        if (c.dtype == ST_BF16)
+          ea_scores<bf16>((const bf16*)Kl, (const bf16*)Vl, kv->R, c.hkv, c.hd, ch.r0, ch.rows,
+                          w.rowtup, ch.t0, w.mu, w.s2, sl, s);
+        else
+          ea_scores<float>((const float*)Kl, (const float*)Vl, kv->R, c.hkv, c.hd, ch.r0, ch.rows,
+                           w.rowtup, ch.t0, w.mu, w.s2, sl, s);
+      }
+      CKLAUNCH();
+      EpiParams eo;
+      eo.mode = EPI_RESID;
+      eo.x = w.x;
+      eo.ld = c.d;
+      RC(project(ctx, w.o, LW.wo, M, c.d, qd, eo, w.tmp, nullptr, s));
+      RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
+      EpiParams eg;
+      eg.mode = EPI_SWIGLU;
+      eg.h = w.h;
+      eg.ld = c.ffn;
+      RC(project(ctx, w.xn, LW.wgu, M, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
+      EpiParams ed;
+      ed.mode = EPI_RESID;
+      ed.x = w.x;
+      ed.ld = c.d;
+      RC(project(ctx, w.h, LW.wd, M, c.d, c.ffn, ed, w.tmp, nullptr, s));
+    }
+    // pooled final-normed last-layer document state
+    RC(rmsnorm(ctx, w.x, ch.rows, nullptr, w.inv_rms, s));
+    {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      pool_rows(w.x, w.inv_rms, kv->off, ch.t0, ch.t1, ch.r0, c.d, kv->pooled, s);
+    }
+    CKLAUNCH();
+  }
+  kv->built = true;
+  kv->r = 0.0;
+  return ST_OK;
+}
+
+extern "C" int st_kv_retain(st_ctx* ctx, st_kv* kv, double r, int32_t kv_dtype, void* stream) {
+  if (!ctx || !kv || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_retain: bad argument");
+  if (!(r > 0.0 && r <= 1.0)) return fail(ctx, ST_EINVAL, "st_kv_retain: r must lie in (0, 1]");
+  const st_model_cfg& c = ctx->cfg;
+  if (!(kv_dtype == c.dtype || (kv_dtype == ST_E4M3 && c.dtype == ST_BF16)))
+    return fail(ctx, ST_EINVAL, "st_kv_retain: kv_dtype must be the model dtype or ST_E4M3 (bf16 models)");
+  if (!kv->built) return fail(ctx, ST_EINVAL, "st_kv_retain: cache not built");
+  cudaStream_t s = S(stream);
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    nkeep_offp(kv->off, kv->T, r, kv->nkeep, kv->offp, s);
+  }
+  CKLAUNCH();
+  int64_t rp = 0, kept = 0;
+  for (int t = 0; t < kv->T; ++t) {
+    int n = n_keep_host(kv->off_h[t + 1] - kv->off_h[t], r);
+    kept += n;
+    rp += (n + 63) & ~63;
+  }
+  RetainParams p;
+  p.scores = kv->scores;
+  p.K = kv->K;
+  p.V = kv->V;
+  p.rank = kv->rank;
+  p.Kr = kv->Kr;
+  p.Vr = kv->Vr;
+  p.scales = kv->scales;
+  p.off = kv->off;
+  p.offp = kv->offp;
+  p.nkeep = kv->nkeep;
+  p.status = kv->status;
+  p.T = kv->T;
+  p.layers = c.layers;
+  p.hkv = c.hkv;
+  p.hd = c.hd;
+  p.max_len = kv->max_len;
+  p.R = kv->R;
+  p.Rp_cap = kv->Rp_cap;
+  p.in_dtype = c.dtype;
+  p.out_dtype = kv_dtype;
+  // algorithmic bytes: read scores + the kept K/V rows, write rank + retained K/V (+ scales)
+  const double LH = (double)c.layers * c.hkv;
+  const double out_e = kv_dtype == ST_E4M3 ? 1.0 : (double)ctx->esz;
+  const double bytes = LH * (kv->R * 8.0 + kept * 2.0 * c.hd * ctx->esz + rp * 2.0 * c.hd * out_e);
+  {
+    Launch L(ctx, s, ST_PROF_RETAIN, 0, bytes);
+    int rc = retain(p, s);
+    if (rc != ST_OK) return fail(ctx, rc, "st_kv_retain: unsupported retained dtype for this head dim");
+  }
+  CKLAUNCH();
+  kv->Rp = rp;
+  kv->r = r;
+  kv->kv_dtype = kv_dtype;
+  return ST_OK;
+}
+
+extern "C" int st_kv_status(st_ctx* ctx, st_kv* kv, void* stream) {
+  if (!ctx || !kv) return fail(ctx, ST_EINVAL, "st_kv_status: bad argument");
+  int32_t h = 0;
+  CK(cudaMemcpyAsync(&h, kv->status, sizeof(int32_t), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  CK(cudaMemsetAsync(kv->status, 0, sizeof(int32_t), S(stream)));
+  if (h != ST_OK) return fail(ctx, h, "device status: NaN retention score");
+  return ST_OK;
+}
+
+extern "C" int st_status(st_ctx* ctx, void* stream) {
+  if (!ctx) return fail(nullptr, ST_EINVAL, "st_status: NULL context");
+  int32_t h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int32_t), S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  if (h != ST_OK) return fail(ctx, h, "device status: a bounded wait timed out");
+  return ST_OK;
+}
+
+extern "C" int st_kv_view(const st_kv* kv, int32_t which, void** ptr, size_t* bytes) {
+  if (!kv || !ptr || !bytes) return fail(nullptr, ST_EINVAL, "st_kv_view: bad argument");
+  const st_model_cfg& c = kv->ctx->cfg;
+  const size_t e = kv->ctx->esz, LH = (size_t)c.layers * c.hkv;
+  const size_t re = (kv->kv_dtype == ST_E4M3) ? 1 : e;
+  switch (which) {
+    case ST_VIEW_K: *ptr = kv->K; *bytes = LH * kv->R * c.hd * e; break;
+    case ST_VIEW_V: *ptr = kv->V; *bytes = LH * kv->R * c.hd * e; break;
+    case ST_VIEW_SCORES: *ptr = kv->scores; *bytes = LH * kv->R * 4; break;
+    case ST_VIEW_POOLED: *ptr = kv->pooled; *bytes = (size_t)kv->T * c.d * 4; break;
+    case ST_VIEW_RANK: *ptr = kv->rank; *bytes = LH * kv->R * 4; break;
+    case ST_VIEW_KR: *ptr = kv->Kr; *bytes = LH * kv->Rp_cap * c.hd * re; break;
+    case ST_VIEW_VR: *ptr = kv->Vr; *bytes = LH * kv->Rp_cap * c.hd * re; break;
+    case ST_VIEW_SCALES: *ptr = kv->scales; *bytes = LH * (kv->Rp_cap / 64) * 8; break;
+    case ST_VIEW_OFFP: *ptr = kv->offp; *bytes = (size_t)(kv->T + 1) * 8; break;
+    case ST_VIEW_NKEEP: *ptr = kv->nkeep; *bytes = (size_t)kv->T * 4; break;
+    default: return fail(kv->ctx, ST_EINVAL, "st_kv_view: unknown view");
+  }
+  return ST_OK;
+}
+
+extern "C" int st_kv_read(const st_kv* kv, int32_t which, void* dst_dev, size_t bytes,
+                          void* stream) {
+  if (!kv || !dst_dev) return fail(nullptr, ST_EINVAL, "st_kv_read: bad argument");
+  void* p = nullptr;
+  size_t n = 0;
+  RC(st_kv_view(kv, which, &p, &n));
+  const st_ctx* ctx = kv->ctx;
+  CK(cudaMemcpyAsync(dst_dev, p, std::min(n, bytes), cudaMemcpyDeviceToDevice, S(stream)));
+  return ST_OK;
+}
+
+extern "C" int st_gemm(st_ctx* ctx, const void* A_dev, const void* W_dev, int32_t M, int32_t N,
+                       int32_t K, float* C_dev, void* stream) {
+  if (!ctx || !A_dev || !W_dev || !C_dev || M < 0 || N <= 0 || K <= 0)
+    return fail(ctx, ST_EINVAL, "st_gemm: bad argument");
+  if (ctx->cfg.dtype == ST_BF16 && !gemm_tc_supported(M > 0 ? M : 1, N, K))
+    return fail(ctx, ST_EUNSUPPORTED, "st_gemm: bf16 needs N % 256 == 0 and K % 64 == 0");
+  if (ctx->cfg.dtype == ST_F32 && (N % 128 || K % 16))
+    return fail(ctx, ST_EUNSUPPORTED, "st_gemm: f32 needs N % 128 == 0 and K % 16 == 0");
+  EpiParams ep;
+  ep.mode = EPI_STORE_F32;
+  ep.out = C_dev;
+  ep.ld = N;
+  return project(ctx, A_dev, W_dev, M, N, K, ep, nullptr, nullptr, S(stream));
+}
+
+// ================================================================== operators
+extern "C" int st_op_create(st_ctx* ctx, const st_op* op, st_operator** out) {
+  if (!ctx || !op || !out || !op->prompt || !op->label_ids) return fail(ctx, ST_EINVAL, "st_op_create: bad argument");
+  *out = nullptr;
+  const st_model_cfg& c = ctx->cfg;
+  if (op->P < 1 || op->P > 256) return fail(ctx, ST_EINVAL, "st_op_create: P must be in 1..256");
+  if (op->kind == ST_OP_FILTER ? op->n_labels != 2 : (op->kind != ST_OP_CLASSIFY || op->n_labels < 2 || op->n_labels > 8))
+    return fail(ctx, ST_EINVAL, "st_op_create: filters take 2 labels, classify 2..8");
+  if (!(op->r > 0.0 && op->r <= 1.0)) return fail(ctx, ST_EINVAL, "st_op_create: r must lie in (0, 1]");
+  for (int i = 0; i < op->P; ++i)
+    if (op->prompt[i] < 0 || op->prompt[i] >= c.vocab) return fail(ctx, ST_EINVAL, "st_op_create: prompt id out of range");
+  for (int i = 0; i < op->n_labels; ++i)
+    if (op->label_ids[i] < 0 || op->label_ids[i] >= c.vocab) return fail(ctx, ST_EINVAL, "st_op_create: label id out of range");
+  st_operator* o = new st_operator();
+  o->desc = *op;
+  o->desc.prompt = nullptr;
+  o->desc.label_ids = nullptr;
+  o->desc.bias = nullptr;
+  int rc = ST_OK;
+  if ((rc = dev_alloc(ctx, (void**)&o->prompt, op->P * 4)) ||
+      (rc = dev_alloc(ctx, (void**)&o->labels, op->n_labels * 4)) ||
+      (rc = dev_alloc(ctx, (void**)&o->bias, op->n_labels * 4))) {
+    st_op_free(o);
+    return rc;
+  }
+  std::vector<float> b(op->n_labels, 0.f);
+  if (op->bias) b.assign(op->bias, op->bias + op->n_labels);
+  cudaMemcpy(o->prompt, op->prompt, op->P * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(o->labels, op->label_ids, op->n_labels * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(o->bias, b.data(), op->n_labels * 4, cudaMemcpyHostToDevice);
+  *out = o;
+  return ST_OK;
+}
+
+extern "C" void st_op_free(st_operator* op) {
+  if (!op) return;
+  cudaFree(op->prompt);
+  cudaFree(op->labels);
+  cudaFree(op->bias);
+  delete op;
+}
+
+extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
+                          const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
+                          int32_t* labels_dev, void* stream) {
+  if (!ctx || !kv || !op || kv->ctx != ctx || n < 0) return fail(ctx, ST_EINVAL, "st_op_eval: bad argument");
+  if (n == 0) return ST_OK;
+  if (!tuple_ids_dev || !logits_dev || !labels_dev) return fail(ctx, ST_EINVAL, "st_op_eval: NULL buffer");
+  if (kv->r <= 0.0) return fail(ctx, ST_EINVAL, "st_op_eval: no retained profile (call st_kv_retain)");
+  if (op->desc.r > kv->r) return fail(ctx, ST_EINVAL, "st_op_eval: operator r exceeds the retained profile's r");
+  const st_model_cfg& c = ctx->cfg;
+  if (kv->max_len + op->desc.P > c.max_pos) return fail(ctx, ST_EINVAL, "st_op_eval: document + prompt exceeds max_pos");
+  cudaStream_t s = S(stream);
+  const int P = op->desc.P;
+  const int64_t cap = std::max<int64_t>(ctx->eval_rows_cap > 0 ? ctx->eval_rows_cap : kDefaultEvalRows, P);
+  const int per_chunk = (int)std::min<int64_t>(n, cap / P);
+  RC(grow(ctx, ctx->ws_eval, eval_ws_bytes(ctx, (int64_t)per_chunk * P, per_chunk, nullptr, nullptr)));
+  EvalWs w;
+  eval_ws_bytes(ctx, (int64_t)per_chunk * P, per_chunk, &w, ctx->ws_eval.p);
+  const size_t e = ctx->esz;
+  const int qd = c.hq * c.hd, kd = c.hkv * c.hd, nqkv = qd + 2 * kd;
+  const size_t kr_e = kv->kv_dtype == ST_E4M3 ? 1 : e;
+  for (int i0 = 0; i0 < n; i0 += per_chunk) {
+    const int nc = std::min(per_chunk, n - i0);
+    const int M = nc * P;
+    {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      eval_rowinfo(tuple_ids_dev + i0, nc, P, kv->off, op->desc.r, w.tup, w.len, w.nk, w.pos, s);
+    }
+    {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      embed_prompt(op->prompt, P, M, ctx->embed, c.dtype, c.d, w.x, s);
+    }
+    CKLAUNCH();
+    for (int l = 0; l < c.layers; ++l) {
+      const LayerW& LW = ctx->layers[l];
+      RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
+      EpiParams ep;
+      ep.mode = EPI_QKV;
+      ep.q = w.q;
+      ep.kbase = w.kp;
+      ep.vbase = w.vp;
+      ep.kv_sg = c.hd;
+      ep.kv_sr = kd;
+      ep.pos = w.pos;
+      ep.rope = ctx->rope;
+      ep.hq = c.hq;
+      ep.hkv = c.hkv;
+      ep.hd = c.hd;
+      RC(project(ctx, w.xn, LW.wqkv, M, nqkv, c.d, ep, w.tmp, nullptr, s));
+      AttnParams a;
+      a.mode = 1;
+      a.q = w.q;
+      a.o = w.o;
+      a.hq = c.hq;
+      a.hkv = c.hkv;
+      a.hd = c.hd;
+      a.scale = 1.0f / std::sqrt((float)c.hd);
+      a.Kr = (const char*)kv->Kr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
+      a.Vr = (const char*)kv->Vr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
+      a.scales = kv->scales + (size_t)l * c.hkv * (kv->Rp_cap / 64) * 2;
+      a.Rp_cap = kv->Rp_cap;
+      a.offp = kv->offp;
+      a.tup = w.tup;
+      a.nk = w.nk;
+      a.kp = w.kp;
+      a.vp = w.vp;
+      a.n = nc;
+      a.P = P;
+      a.kv_dtype = kv->kv_dtype;
+      RC(attention(ctx, a, nullptr, 0, s));
+      EpiParams eo;
+      eo.mode = EPI_RESID;
+      eo.x = w.x;
+      eo.ld = c.d;
+      RC(project(ctx, w.o, LW.wo, M, c.d, qd, eo, w.tmp, nullptr, s));
+      RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
+      EpiParams eg;
+      eg.mode = EPI_SWIGLU;
+      eg.h = w.h;
+      eg.ld = c.ffn;
+      RC(project(ctx, w.xn, LW.wgu, M, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
+      EpiParams ed;
+      ed.mode = EPI_RESID;
+      ed.x = w.x;
+      ed.ld = c.d;
+      RC(project(ctx, w.h, LW.wd, M, c.d, c.ffn, ed, w.tmp, nullptr, s));
+    }
+    {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      label_head(w.x, nc, P, c.d, c.eps, ctx->w_lm, c.dtype, op->labels, op->desc.n_labels,
+                 op->bias, op->desc.kind, op->desc.theta_pos, op->desc.theta_neg,
+                 logits_dev + (size_t)i0 * op->desc.n_labels, labels_dev + i0, s);
+    }
+    CKLAUNCH();
+  }
+  return ST_OK;
+}
+
+extern "C" int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,
+                           const int32_t* tokens_host, float* logits_host, int32_t* labels_host,
+                           void* stream) {
+  if (!ctx || !kv || !op || !tokens_host || !logits_host || !labels_host)
+    return fail(ctx, ST_EINVAL, "st_run_host: bad argument");
+  cudaStream_t s = S(stream);
+  const int T = kv->T, nl = op->desc.n_labels;
+  if (!kv->tok) {
+    RC(dev_alloc(ctx, (void**)&kv->tok, (size_t)kv->R * 4));
+    RC(dev_alloc(ctx, (void**)&kv->iota, (size_t)T * 4));
+    std::vector<int32_t> ids(T);
+    for (int t = 0; t < T; ++t) ids[t] = t;
+    CK(cudaMemcpy(kv->iota, ids.data(), (size_t)T * 4, cudaMemcpyHostToDevice));
+    RC(dev_alloc(ctx, (void**)&kv->out_logits, (size_t)T * 8 * 4));
+    RC(dev_alloc(ctx, (void**)&kv->out_labels, (size_t)T * 4));
+  }
+  CK(cudaMemcpyAsync(kv->tok, tokens_host, (size_t)kv->R * 4, cudaMemcpyHostToDevice, s));
+  RC(st_kv_build(ctx, kv, kv->tok, stream));
+  RC(st_kv_retain(ctx, kv, op->desc.r, kv_dtype, stream));
+  RC(st_op_eval(ctx, kv, op, kv->iota, T, kv->out_logits, kv->out_labels, stream));
+  CK(cudaMemcpyAsync(logits_host, kv->out_logits, (size_t)T * nl * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(labels_host, kv->out_labels, (size_t)T * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return ST_OK;
+}
+
+// ================================================================== profiling
+extern "C" int st_prof_enable(st_ctx* ctx, int32_t on) {
+  if (!ctx) return fail(nullptr, ST_EINVAL, "st_prof_enable: NULL context");
+  ctx->prof.on = on != 0;
+  return ST_OK;
+}
+
+extern "C" int st_prof_read(st_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, ST_EINVAL, "st_prof_read: bad argument");
+  for (auto& r : ctx->prof.pending) {
+    CK(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    double* a = ctx->prof.acc[r.family];
+    a[0] += 1;
+    a[1] += ms;
+    a[2] += r.flops;
+    a[3] += r.bytes;
+    ctx->prof.pool.push_back(r.a);
+    ctx->prof.pool.push_back(r.b);
+  }
+  ctx->prof.pending.clear();
+  std::memcpy(out, ctx->prof.acc, sizeof(ctx->prof.acc));
+  return ST_OK;
+}
+
+extern "C" int st_prof_reset(st_ctx* ctx) {
+  if (!ctx) return fail(nullptr, ST_EINVAL, "st_prof_reset: NULL context");
+  double tmp[ST_PROF_N * 4];
+  st_prof_read(ctx, tmp);
+  std::memset(ctx->prof.acc, 0, sizeof(ctx->prof.acc));
+  ctx->launches = 0;
+  return ST_OK;
+}
+
+extern "C" int64_t st_launch_count(const st_ctx* ctx) { return ctx ? ctx->launches : 0; }

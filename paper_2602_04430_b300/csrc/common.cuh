@@ -1,0 +1,155 @@
+// Shared device helpers and internal structures of libstretto (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/stretto.h"
+
+namespace st {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------- conversions
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<bf16>(bf16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ bf16 from_f<bf16>(float v) { return __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Load / store n consecutive elements as float (n a multiple of 4 for float, 8 for bf16).
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  static constexpr int N = 4;
+  __device__ __forceinline__ static void load(const float* p, float* out) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  }
+  __device__ __forceinline__ static void store(float* p, const float* in) {
+    *reinterpret_cast<float4*>(p) = make_float4(in[0], in[1], in[2], in[3]);
+  }
+};
+template <> struct Vec<bf16> {
+  static constexpr int N = 8;
+  __device__ __forceinline__ static void load(const bf16* p, float* out) {
+    uint4 v = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(h[i]);
+      out[2 * i] = f.x; out[2 * i + 1] = f.y;
+    }
+  }
+  __device__ __forceinline__ static void store(bf16* p, const float* in) {
+    uint4 v;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(in[2 * i], in[2 * i + 1]);
+    *reinterpret_cast<uint4*>(p) = v;
+  }
+};
+
+__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)); }
+
+// ---------------------------------------------------------------- host side
+struct LayerW {
+  void* wqkv = nullptr;  // [(hq+2hkv)*hd][d]
+  void* wo = nullptr;    // [d][hq*hd]
+  void* wgu = nullptr;   // [2*ffn][d], gate/up interleaved in blocks of 128 rows
+  void* wd = nullptr;    // [d][ffn]
+};
+
+// A grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ProfRec {
+  int family;
+  double flops, bytes;
+  cudaEvent_t a, b;
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  double acc[ST_PROF_N][4] = {};
+};
+
+}  // namespace st
+
+struct st_ctx {
+  st_model_cfg cfg;
+  int device = 0;
+  size_t esz = 4;                 // bytes per weight / activation element
+  void* embed = nullptr;
+  void* w_lm = nullptr;
+  std::vector<st::LayerW> layers;
+  float2* rope = nullptr;         // [max_pos][hd/2] (cos, sin)
+  // workspaces
+  st::DevBuf ws_build, ws_eval;
+  int64_t build_rows_cap = 0, eval_rows_cap = 0;
+  int32_t* dstatus = nullptr;     // device status word of bounded waits (ST_ETIMEOUT)
+  std::string err;
+  st::Prof prof;
+  int64_t launches = 0;
+};
+
+struct st_kv {
+  st_ctx* ctx = nullptr;
+  int32_t T = 0;
+  int64_t R = 0;                  // total document tokens
+  int64_t Rp_cap = 0;             // capacity of the retained cache in slots (sum of pad64(L))
+  int32_t max_len = 0;
+  std::vector<int64_t> off_h;     // host copy of offsets
+  int64_t* off = nullptr;         // device [T+1]
+  void* K = nullptr;              // [layers][hkv][R][hd]
+  void* V = nullptr;
+  float* scores = nullptr;        // [layers][hkv][R]
+  float* pooled = nullptr;        // [T][d]
+  int32_t* rank = nullptr;        // [layers][hkv][R]
+  void* Kr = nullptr;             // [layers][hkv][Rp_cap][hd]
+  void* Vr = nullptr;
+  float* scales = nullptr;        // [layers][hkv][Rp_cap/64][2]
+  int64_t* offp = nullptr;        // device [T+1]
+  int32_t* nkeep = nullptr;       // device [T]
+  int32_t* status = nullptr;      // device status word
+  int64_t Rp = 0;                 // used retained slots (sum pad64(n))
+  double r = 0.0;                 // retained fraction of the current profile (0 = none)
+  int32_t kv_dtype = -1;
+  bool built = false;
+  int32_t* items = nullptr;       // device [n_items][2] prefill work items (tuple, first position)
+  int64_t n_items = 0;
+  std::vector<int64_t> item_start;  // first item of each tuple (host)
+  int32_t* tok = nullptr;         // device token buffer of st_run_host
+  int32_t* iota = nullptr;        // device 0..T-1 of st_run_host
+  float* out_logits = nullptr;    // device outputs of st_run_host
+  int32_t* out_labels = nullptr;
+};
+
+struct st_operator {
+  st_op desc;
+  int32_t* prompt = nullptr;      // device [P]
+  int32_t* labels = nullptr;      // device [n_labels]
+  float* bias = nullptr;          // device [n_labels]
+  float theta_pos = 0, theta_neg = 0;
+};

@@ -1,0 +1,72 @@
+// Projection epilogues shared by the CUDA-core and tcgen05 GEMMs.
+//
+// A thread holds W consecutive float32 accumulators of one output row.  For the
+// QKV projection W equals the head dim, so a thread owns exactly one head and
+// the RoPE rotation pairs (i, i + hd/2) are register-local.
+#pragma once
+
+#include "kernels.h"
+
+namespace st {
+
+template <typename act_t, int W>
+__device__ __forceinline__ void store_act(act_t* dst, const float (&v)[W]) {
+  constexpr int VN = Vec<act_t>::N;
+#pragma unroll
+  for (int j = 0; j < W; j += VN) Vec<act_t>::store(dst + j, v + j);
+}
+
+template <int W>
+__device__ __forceinline__ void rope_inplace(float (&v)[W], const float2* __restrict__ tab) {
+#pragma unroll
+  for (int i = 0; i < W / 2; ++i) {
+    float2 cs = tab[i];
+    float a = v[i], b = v[i + W / 2];
+    v[i] = a * cs.x - b * cs.y;
+    v[i + W / 2] = b * cs.x + a * cs.y;
+  }
+}
+
+// Apply the epilogue to columns [col0, col0 + W) of output row `row`.
+template <typename act_t, int W>
+__device__ __forceinline__ void epilogue_apply(const EpiParams& ep, int row, int col0,
+                                               float (&v)[W]) {
+  if (ep.mode == EPI_QKV) {
+    const int qcols = ep.hq * W, kcols = ep.hkv * W;
+    if (col0 < qcols + kcols) rope_inplace<W>(v, ep.rope + (int64_t)ep.pos[row] * (W / 2));
+    if (col0 < qcols) {
+      store_act<act_t, W>(reinterpret_cast<act_t*>(ep.q) + (int64_t)row * qcols + col0, v);
+    } else if (col0 < qcols + kcols) {
+      int g = (col0 - qcols) / W;
+      store_act<act_t, W>(reinterpret_cast<act_t*>(ep.kbase) + g * ep.kv_sg + row * ep.kv_sr, v);
+    } else {
+      int g = (col0 - qcols - kcols) / W;
+      store_act<act_t, W>(reinterpret_cast<act_t*>(ep.vbase) + g * ep.kv_sg + row * ep.kv_sr, v);
+    }
+  } else if (ep.mode == EPI_RESID) {
+    float* x = ep.x + (int64_t)row * ep.ld + col0;
+#pragma unroll
+    for (int j = 0; j < W; j += 4) {
+      float4 o = *reinterpret_cast<float4*>(x + j);
+      o.x += v[j]; o.y += v[j + 1]; o.z += v[j + 2]; o.w += v[j + 3];
+      *reinterpret_cast<float4*>(x + j) = o;
+    }
+  } else if (ep.mode == EPI_STORE_F32) {
+    float* o = ep.out + (int64_t)row * ep.ld + col0;
+#pragma unroll
+    for (int j = 0; j < W; j += 4)
+      *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+  }
+}
+
+// SwiGLU: gate accumulators g and up accumulators u of FFN columns [f0, f0 + W).
+template <typename act_t, int W>
+__device__ __forceinline__ void epilogue_swiglu(const EpiParams& ep, int row, int f0,
+                                                const float (&g)[W], const float (&u)[W]) {
+  float hv[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) hv[j] = silu_f(g[j]) * u[j];
+  store_act<act_t, W>(reinterpret_cast<act_t*>(ep.h) + (int64_t)row * ep.ld + f0, hv);
+}
+
+}  // namespace st

@@ -1,0 +1,385 @@
+// Row bookkeeping, embedding, RMSNorm, EA-lite statistics / scores, pooling and
+// the label head.  All of these are bandwidth-bound elementwise or reduction
+// kernels; the projections and attention live in their own files.
+#include "kernels.h"
+
+namespace st {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ int n_keep_dev(int L, double r) {
+  // clamp(floor(r*L + 0.5), 1, L); the product and the sum are rounded separately
+  // (no fused multiply-add) so that host and device agree bit for bit.
+  double rl = __dmul_rn(r, (double)L);
+  double f = floor(__dadd_rn(rl, 0.5));
+  int n = (int)f;
+  return n < 1 ? 1 : (n > L ? L : n);
+}
+
+template <int BLOCK>
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float t = (threadIdx.x < BLOCK / 32) ? red[threadIdx.x] : 0.f;
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  return red[0];
+}
+
+// ------------------------------------------------------------------ row info
+__global__ void k_build_rowinfo(const int64_t* __restrict__ off, int t0, int t1, int64_t r0,
+                                int64_t rows, int32_t* __restrict__ rowtup,
+                                int32_t* __restrict__ pos) {
+  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= rows) return;
+  int64_t g = r0 + m;
+  int lo = t0, hi = t1 - 1;          // last t with off[t] <= g
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  rowtup[m] = lo;
+  pos[m] = (int32_t)(g - off[lo]);
+}
+
+void build_rowinfo(const int64_t* off, int t0, int t1, int64_t r0, int64_t rows, int32_t* rowtup,
+                   int32_t* pos, cudaStream_t s) {
+  if (rows <= 0) return;
+  k_build_rowinfo<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(off, t0, t1, r0, rows, rowtup, pos);
+}
+
+__global__ void k_eval_rowinfo(const int32_t* __restrict__ tuple_ids, int n, int P,
+                               const int64_t* __restrict__ off, double r, int32_t* tup,
+                               int32_t* len, int32_t* nk, int32_t* pos) {
+  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int64_t)n * P) return;
+  int i = (int)(m / P), p = (int)(m % P);
+  int t = tuple_ids[i];
+  int L = (int)(off[t + 1] - off[t]);
+  pos[m] = L + p;
+  if (p == 0) {
+    tup[i] = t;
+    len[i] = L;
+    nk[i] = n_keep_dev(L, r);
+  }
+}
+
+void eval_rowinfo(const int32_t* tuple_ids, int n, int P, const int64_t* off, double r,
+                  int32_t* tup, int32_t* len, int32_t* nk, int32_t* pos, cudaStream_t s) {
+  int64_t rows = (int64_t)n * P;
+  if (rows <= 0) return;
+  k_eval_rowinfo<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(tuple_ids, n, P, off, r, tup, len,
+                                                                 nk, pos);
+}
+
+// Retained counts and padded (64-slot) offsets of every tuple, one block.
+__global__ void k_nkeep_offp(const int64_t* __restrict__ off, int T, double r, int32_t* nkeep,
+                             int64_t* offp) {
+  __shared__ int64_t part[1024];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) { carry = 0; offp[0] = 0; }
+  __syncthreads();
+  for (int base = 0; base < T; base += 1024) {
+    int t = base + threadIdx.x;
+    int64_t v = 0;
+    if (t < T) {
+      int L = (int)(off[t + 1] - off[t]);
+      int n = n_keep_dev(L, r);
+      nkeep[t] = n;
+      v = (n + 63) & ~63;
+    }
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {           // inclusive Hillis-Steele scan
+      int64_t add = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (t < T) offp[t + 1] = carry + part[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+}
+
+void nkeep_offp(const int64_t* off, int T, double r, int32_t* nkeep, int64_t* offp,
+                cudaStream_t s) {
+  k_nkeep_offp<<<1, 1024, 0, s>>>(off, T, r, nkeep, offp);
+}
+
+// ------------------------------------------------------------------ embedding
+template <typename act_t>
+__global__ void k_embed(const int32_t* __restrict__ tok, int P, int64_t rows,
+                        const act_t* __restrict__ E, int d, float* __restrict__ x) {
+  // P > 0: row m reads token tok[m % P] (the prompt, same for every tuple)
+  const int per = d / 4;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * per) return;
+  int64_t m = i / per;
+  int c = (int)(i % per) * 4;
+  int t = P > 0 ? tok[m % P] : tok[m];
+  const act_t* e = E + (int64_t)t * d + c;
+  float4 v = make_float4(to_f(e[0]), to_f(e[1]), to_f(e[2]), to_f(e[3]));
+  *reinterpret_cast<float4*>(x + m * d + c) = v;
+}
+
+template <typename act_t>
+void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, float* x, cudaStream_t s) {
+  int64_t n = rows * (d / 4);
+  if (n <= 0) return;
+  k_embed<act_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tok, 0, rows, E, d, x);
+}
+template void embed_rows<float>(const int32_t*, int64_t, const float*, int, float*, cudaStream_t);
+template void embed_rows<bf16>(const int32_t*, int64_t, const bf16*, int, float*, cudaStream_t);
+
+void embed_prompt(const int32_t* prompt, int P, int64_t rows, const void* E, int dtype, int d,
+                  float* x, cudaStream_t s) {
+  int64_t n = rows * (d / 4);
+  if (n <= 0) return;
+  unsigned g = (unsigned)((n + 255) / 256);
+  if (dtype == ST_BF16)
+    k_embed<bf16><<<g, 256, 0, s>>>(prompt, P, rows, (const bf16*)E, d, x);
+  else
+    k_embed<float><<<g, 256, 0, s>>>(prompt, P, rows, (const float*)E, d, x);
+}
+
+// ------------------------------------------------------------------ RMSNorm
+// One warp per row; x float32 [rows][d] -> xn = x / sqrt(mean(x^2) + eps) (act type).
+template <typename act_t>
+__global__ void k_rmsnorm(const float* __restrict__ x, int64_t rows, int d, float eps,
+                          act_t* __restrict__ xn, float* __restrict__ inv_rms) {
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const float* xr = x + row * d;
+  float ss = 0.f;
+  for (int c = lane * 4; c < d; c += 128) {
+    float4 v = *reinterpret_cast<const float4*>(xr + c);
+    ss += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+  }
+  ss = warp_sum(ss);
+  float inv = 1.0f / sqrtf(ss / (float)d + eps);
+  if (inv_rms != nullptr && lane == 0) inv_rms[row] = inv;
+  if (xn == nullptr) return;
+  act_t* o = xn + row * d;
+  for (int c = lane * 4; c < d; c += 128) {
+    float4 v = *reinterpret_cast<const float4*>(xr + c);
+    o[c] = from_f<act_t>(v.x * inv);
+    o[c + 1] = from_f<act_t>(v.y * inv);
+    o[c + 2] = from_f<act_t>(v.z * inv);
+    o[c + 3] = from_f<act_t>(v.w * inv);
+  }
+}
+
+template <typename act_t>
+void rmsnorm_rows(const float* x, int64_t rows, int d, float eps, act_t* xn, float* inv_rms,
+                  cudaStream_t s) {
+  if (rows <= 0) return;
+  k_rmsnorm<act_t><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(x, rows, d, eps, xn, inv_rms);
+}
+template void rmsnorm_rows<float>(const float*, int64_t, int, float, float*, float*, cudaStream_t);
+template void rmsnorm_rows<bf16>(const float*, int64_t, int, float, bf16*, float*, cudaStream_t);
+
+// ------------------------------------------------------------------ EA-lite statistics
+// Block per (tuple, kv head): mean and population variance over (document
+// position, query head of the group) of every post-RoPE query dimension.
+template <typename act_t>
+__global__ void k_qstats(const act_t* __restrict__ q, const int64_t* __restrict__ off, int t0,
+                         int64_t r0, int hq, int hkv, int hd, float* __restrict__ mu,
+                         float* __restrict__ s2) {
+  __shared__ float red[256];
+  const int t = t0 + blockIdx.x / hkv, g = blockIdx.x % hkv;
+  const int G = hq / hkv;
+  const int64_t row0 = off[t] - r0;
+  const int L = (int)(off[t + 1] - off[t]);
+  const int c = threadIdx.x % hd, rg = threadIdx.x / hd, nrg = blockDim.x / hd;
+  const int64_t items = (int64_t)L * G;
+  float sum = 0.f;
+  for (int64_t it = rg; it < items; it += nrg) {
+    int64_t j = it / G, hh = it % G;
+    sum += to_f(q[(row0 + j) * hq * hd + (int64_t)(g * G + hh) * hd + c]);
+  }
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  float m = 0.f;
+  for (int k = 0; k < nrg; ++k) m += red[k * hd + c];
+  m /= (float)items;
+  __syncthreads();
+  float dev = 0.f;
+  for (int64_t it = rg; it < items; it += nrg) {
+    int64_t j = it / G, hh = it % G;
+    float v = to_f(q[(row0 + j) * hq * hd + (int64_t)(g * G + hh) * hd + c]) - m;
+    dev += v * v;
+  }
+  red[threadIdx.x] = dev;
+  __syncthreads();
+  if (rg == 0) {
+    float v = 0.f;
+    for (int k = 0; k < nrg; ++k) v += red[k * hd + c];
+    int64_t o = ((int64_t)(t - t0) * hkv + g) * hd + c;
+    mu[o] = m;
+    s2[o] = v / (float)items;
+  }
+}
+
+template <typename act_t>
+void qstats(const act_t* q, const int64_t* off, int t0, int t1, int64_t r0, int hq, int hkv,
+            int hd, float* mu, float* s2, cudaStream_t s) {
+  int nb = (t1 - t0) * hkv;
+  if (nb <= 0) return;
+  k_qstats<act_t><<<nb, 256, 0, s>>>(q, off, t0, r0, hq, hkv, hd, mu, s2);
+}
+template void qstats<float>(const float*, const int64_t*, int, int, int64_t, int, int, int, float*,
+                            float*, cudaStream_t);
+template void qstats<bf16>(const bf16*, const int64_t*, int, int, int64_t, int, int, int, float*,
+                           float*, cudaStream_t);
+
+// Thread per (kv head, slot): score = mu.k/sqrt(hd) + sum sigma2 k^2/(2hd) + ln(||v|| + 1e-12).
+template <typename act_t>
+__global__ void k_scores(const act_t* __restrict__ K, const act_t* __restrict__ V, int64_t R,
+                         int hkv, int hd, int64_t r0, int64_t rows,
+                         const int32_t* __restrict__ rowtup, int t0, const float* __restrict__ mu,
+                         const float* __restrict__ s2, float* __restrict__ scores) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * hkv) return;
+  int g = (int)(i / rows);
+  int64_t m = i % rows;
+  int lt = rowtup[m] - t0;
+  const act_t* k = K + ((int64_t)g * R + r0 + m) * hd;
+  const act_t* v = V + ((int64_t)g * R + r0 + m) * hd;
+  const float* mup = mu + ((int64_t)lt * hkv + g) * hd;
+  const float* s2p = s2 + ((int64_t)lt * hkv + g) * hd;
+  float d1 = 0.f, d2 = 0.f, vv = 0.f;
+  constexpr int VN = Vec<act_t>::N;
+  for (int c = 0; c < hd; c += VN) {
+    float kk[VN], vx[VN];
+    Vec<act_t>::load(k + c, kk);
+    Vec<act_t>::load(v + c, vx);
+#pragma unroll
+    for (int e = 0; e < VN; ++e) {
+      d1 += mup[c + e] * kk[e];
+      d2 += s2p[c + e] * kk[e] * kk[e];
+      vv += vx[e] * vx[e];
+    }
+  }
+  scores[(int64_t)g * R + r0 + m] =
+      d1 / sqrtf((float)hd) + d2 / (2.0f * (float)hd) + logf(sqrtf(vv) + 1e-12f);
+}
+
+template <typename act_t>
+void ea_scores(const act_t* K, const act_t* V, int64_t R, int hkv, int hd, int64_t r0,
+               int64_t rows, const int32_t* rowtup, int t0, const float* mu, const float* s2,
+               float* scores, cudaStream_t s) {
+  int64_t n = rows * hkv;
+  if (n <= 0) return;
+  k_scores<act_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(K, V, R, hkv, hd, r0, rows, rowtup,
+                                                              t0, mu, s2, scores);
+}
+template void ea_scores<float>(const float*, const float*, int64_t, int, int, int64_t, int64_t,
+                               const int32_t*, int, const float*, const float*, float*,
+                               cudaStream_t);
+template void ea_scores<bf16>(const bf16*, const bf16*, int64_t, int, int, int64_t, int64_t,
+                              const int32_t*, int, const float*, const float*, float*,
+                              cudaStream_t);
+
+// ------------------------------------------------------------------ pooling
+// Block per tuple: pooled[t] = mean over document rows of the final-normed state.
+__global__ void k_pool(const float* __restrict__ x, const float* __restrict__ inv_rms,
+                       const int64_t* __restrict__ off, int t0, int64_t r0, int d,
+                       float* __restrict__ pooled) {
+  const int t = t0 + blockIdx.x;
+  const int64_t a = off[t] - r0, b = off[t + 1] - r0;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    float acc = 0.f;
+    for (int64_t m = a; m < b; ++m) acc += x[m * d + c] * inv_rms[m];
+    pooled[(int64_t)t * d + c] = acc / (float)(b - a);
+  }
+}
+
+void pool_rows(const float* x, const float* inv_rms, const int64_t* off, int t0, int t1,
+               int64_t r0, int d, float* pooled, cudaStream_t s) {
+  if (t1 <= t0) return;
+  k_pool<<<t1 - t0, 256, 0, s>>>(x, inv_rms, off, t0, r0, d, pooled);
+}
+
+// ------------------------------------------------------------------ label head
+// Block per evaluated tuple: final RMSNorm of the last prompt row, label-token
+// logits, and the decision (filter thresholds or classify argmax).
+template <typename w_t>
+__global__ void k_label_head(const float* __restrict__ x, int P, int d, float eps,
+                             const w_t* __restrict__ w_lm, const int32_t* __restrict__ labels,
+                             int n_labels, const float* __restrict__ bias, int kind,
+                             float theta_pos, float theta_neg, float* __restrict__ logits,
+                             int32_t* __restrict__ out_labels) {
+  __shared__ float red[32];
+  __shared__ float z[8];
+  const int i = blockIdx.x;
+  const float* xr = x + ((int64_t)i * P + P - 1) * d;
+  float ss = 0.f;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) ss += xr[c] * xr[c];
+  ss = block_sum<256>(ss, red);
+  const float inv = 1.0f / sqrtf(ss / (float)d + eps);
+  for (int k = 0; k < n_labels; ++k) {
+    const w_t* wr = w_lm + (int64_t)labels[k] * d;
+    float acc = 0.f;
+    for (int c = threadIdx.x; c < d; c += blockDim.x) acc += xr[c] * to_f(wr[c]);
+    acc = block_sum<256>(acc, red);
+    if (threadIdx.x == 0) z[k] = acc * inv;
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < n_labels; ++k) logits[(int64_t)i * n_labels + k] = z[k];
+    int dec;
+    if (kind == ST_OP_FILTER) {
+      float sc = z[0] - z[1];
+      float a = sc - theta_pos, rj = theta_neg - sc, u = 0.f;
+      dec = (u >= a && u >= rj) ? ST_UNSURE : (rj >= a ? ST_REJECT : ST_ACCEPT);
+    } else {
+      dec = 0;
+      float best = z[0] + (bias ? bias[0] : 0.f);
+      for (int k = 1; k < n_labels; ++k) {
+        float v = z[k] + (bias ? bias[k] : 0.f);
+        if (v > best) { best = v; dec = k; }
+      }
+    }
+    out_labels[i] = dec;
+  }
+}
+
+void label_head(const float* x, int n, int P, int d, float eps, const void* w_lm, int dtype,
+                const int32_t* labels, int n_labels, const float* bias, int kind,
+                float theta_pos, float theta_neg, float* logits, int32_t* out_labels,
+                cudaStream_t s) {
+  if (n <= 0) return;
+  if (dtype == ST_BF16)
+    k_label_head<bf16><<<n, 256, 0, s>>>(x, P, d, eps, (const bf16*)w_lm, labels, n_labels, bias,
+                                         kind, theta_pos, theta_neg, logits, out_labels);
+  else
+    k_label_head<float><<<n, 256, 0, s>>>(x, P, d, eps, (const float*)w_lm, labels, n_labels,
+                                          bias, kind, theta_pos, theta_neg, logits, out_labels);
+}
+
+// ------------------------------------------------------------------ SwiGLU (float32 path)
+// t [rows][2F] with gate/up interleaved in blocks of 128 columns -> h [rows][F].
+__global__ void k_swiglu_f32(const float* __restrict__ t, int64_t rows, int ffn,
+                             float* __restrict__ h) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * ffn) return;
+  int64_t m = i / ffn;
+  int f = (int)(i % ffn);
+  int b = f >> 7, j = f & 127;
+  float g = t[m * 2 * ffn + b * 256 + j];
+  float u = t[m * 2 * ffn + b * 256 + 128 + j];
+  h[i] = silu_f(g) * u;
+}
+
+void swiglu_from_f32(const float* t, int64_t rows, int ffn, float* h, cudaStream_t s) {
+  int64_t n = rows * ffn;
+  if (n <= 0) return;
+  k_swiglu_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, rows, ffn, h);
+}
+
+}  // namespace st

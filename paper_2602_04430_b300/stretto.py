@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libstretto (include/stretto.h).
+
+Argument marshalling only: torch tensors provide device memory and the current
+CUDA stream; every step of the operator runs in the library's CUDA kernels.
+The library must have been built in-tree (``paper_2602_04430_b300.build``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstretto.so")
+
+ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ENAN, ST_EUNSUPPORTED = range(7)
+ST_F32, ST_BF16, ST_E4M3 = 0, 1, 2
+ST_OP_FILTER, ST_OP_CLASSIFY = 0, 1
+ST_REJECT, ST_ACCEPT, ST_UNSURE = 0, 1, 2
+(ST_VIEW_K, ST_VIEW_V, ST_VIEW_SCORES, ST_VIEW_POOLED, ST_VIEW_RANK, ST_VIEW_KR, ST_VIEW_VR,
+ ST_VIEW_SCALES, ST_VIEW_OFFP, ST_VIEW_NKEEP) = range(10)
+PROF_FAMILIES = ("gemm", "attention", "retain", "other")
+
+
+class StrettoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libstretto error {code}: {msg}")
+        self.code = code
+
+
+class ModelCfg(ctypes.Structure):
+    _fields_ = [("layers", ctypes.c_int32), ("d", ctypes.c_int32), ("hq", ctypes.c_int32),
+                ("hkv", ctypes.c_int32), ("hd", ctypes.c_int32), ("ffn", ctypes.c_int32),
+                ("vocab", ctypes.c_int32), ("dtype", ctypes.c_int32), ("max_pos", ctypes.c_int32),
+                ("rope_theta", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+class OpDesc(ctypes.Structure):
+    _fields_ = [("prompt", ctypes.POINTER(ctypes.c_int32)), ("P", ctypes.c_int32),
+                ("label_ids", ctypes.POINTER(ctypes.c_int32)), ("n_labels", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("r", ctypes.c_double), ("theta_pos", ctypes.c_float),
+                ("theta_neg", ctypes.c_float), ("bias", ctypes.POINTER(ctypes.c_float))]
+
+
+_LIB = None
+VP = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load libstretto.so (raises ImportError if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2602_04430_b300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, sz, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+    sigs = {
+        "st_create": (i32, [ctypes.POINTER(ModelCfg), ctypes.POINTER(VP), VP, ctypes.POINTER(VP)]),
+        "st_destroy": (None, [VP]),
+        "st_last_error": (ctypes.c_char_p, [VP]),
+        "st_version": (ctypes.c_char_p, []),
+        "st_reserve": (i32, [VP, i64, i64]),
+        "st_kv_alloc": (i32, [VP, ctypes.POINTER(i64), i32, ctypes.POINTER(VP)]),
+        "st_kv_free": (None, [VP]),
+        "st_kv_build": (i32, [VP, VP, VP, VP]),
+        "st_kv_retain": (i32, [VP, VP, dbl, i32, VP]),
+        "st_kv_status": (i32, [VP, VP, VP]),
+        "st_status": (i32, [VP, VP]),
+        "st_kv_view": (i32, [VP, i32, ctypes.POINTER(VP), ctypes.POINTER(sz)]),
+        "st_kv_read": (i32, [VP, i32, VP, sz, VP]),
+        "st_op_create": (i32, [VP, ctypes.POINTER(OpDesc), ctypes.POINTER(VP)]),
+        "st_op_free": (None, [VP]),
+        "st_op_eval": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
+        "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
+        "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
+        "st_prof_enable": (i32, [VP, i32]),
+        "st_prof_read": (i32, [VP, ctypes.POINTER(dbl)]),
+        "st_prof_reset": (i32, [VP]),
+        "st_launch_count": (i64, [VP]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return VP(s.cuda_stream)
+
+
+def _ptr(t) -> VP:
+    return VP(t.data_ptr())
+
+
+class Model:
+    """A decoder with its weights resident on the device (an ``st_ctx``)."""
+
+    def __init__(self, cfg: synth.ModelConfig, weights: Dict[str, object], max_pos: int = 16640,
+                 device: str = "cuda"):
+        import torch
+        self.cfg = cfg
+        self.L = lib()
+        dt = torch.bfloat16 if cfg.dtype == "bf16" else torch.float32
+        self.torch_dtype = dt
+        arrays = [weights["embed"]]
+        for lw in weights["layers"]:
+            arrays += [lw[k] for k in ("wq", "wk", "wv", "wo", "wg", "wu", "wd")]
+        arrays.append(weights["w_lm"])
+        dev = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device).to(dt)
+               for a in arrays]
+        ptrs = (VP * len(dev))(*[t.data_ptr() for t in dev])
+        c = ModelCfg(cfg.layers, cfg.d, cfg.hq, cfg.hkv, cfg.hd, cfg.ffn, cfg.vocab,
+                     ST_BF16 if cfg.dtype == "bf16" else ST_F32, max_pos, cfg.rope_theta, cfg.eps)
+        self._cfg = c
+        h = VP()
+        rc = self.L.st_create(ctypes.byref(c), ptrs, _stream(), ctypes.byref(h))
+        if rc != ST_OK:
+            raise StrettoError(rc, self.L.st_last_error(None).decode())
+        self.h = h
+        del dev
+
+    def check(self, rc: int):
+        if rc != ST_OK:
+            raise StrettoError(rc, self.L.st_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.st_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, build_rows: int = 0, eval_rows: int = 0):
+        self.check(self.L.st_reserve(self.h, int(build_rows), int(eval_rows)))
+
+    def status(self, stream=None):
+        self.check(self.L.st_status(self.h, _stream(stream)))
+
+    def kv_alloc(self, offsets: np.ndarray) -> "KVCache":
+        return KVCache(self, offsets)
+
+    def operator(self, op: synth.Operator) -> "Operator":
+        return Operator(self, op)
+
+    def gemm(self, A, W, C, stream=None):
+        M, K = A.shape
+        N = W.shape[0]
+        self.check(self.L.st_gemm(self.h, _ptr(A), _ptr(W), M, N, K, _ptr(C), _stream(stream)))
+
+    # ---- profiling
+    def prof_enable(self, on: bool = True):
+        self.check(self.L.st_prof_enable(self.h, 1 if on else 0))
+
+    def prof_reset(self):
+        self.check(self.L.st_prof_reset(self.h))
+
+    def prof_read(self) -> Dict[str, Dict[str, float]]:
+        buf = (ctypes.c_double * 16)()
+        self.check(self.L.st_prof_read(self.h, buf))
+        out = {}
+        for i, name in enumerate(PROF_FAMILIES):
+            out[name] = {"launches": buf[4 * i], "ms": buf[4 * i + 1], "flops": buf[4 * i + 2],
+                         "bytes": buf[4 * i + 3]}
+        return out
+
+    def launch_count(self) -> int:
+        return int(self.L.st_launch_count(self.h))
+
+
+class KVCache:
+    """The caches of one table (an ``st_kv``)."""
+
+    def __init__(self, model: Model, offsets: np.ndarray):
+        self.model = model
+        self.L = model.L
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.offsets = off
+        self.T = len(off) - 1
+        h = VP()
+        model.check(self.L.st_kv_alloc(model.h, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       self.T, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.st_kv_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, tokens, stream=None):
+        self.model.check(self.L.st_kv_build(self.model.h, self.h, _ptr(tokens), _stream(stream)))
+
+    def retain(self, r: float, kv_dtype: Optional[int] = None, stream=None):
+        if kv_dtype is None:
+            kv_dtype = ST_BF16 if self.model.cfg.dtype == "bf16" else ST_F32
+        self.model.check(self.L.st_kv_retain(self.model.h, self.h, float(r), int(kv_dtype),
+                                             _stream(stream)))
+
+    def status(self, stream=None):
+        self.model.check(self.L.st_kv_status(self.model.h, self.h, _stream(stream)))
+
+    def view_bytes(self, which: int) -> int:
+        p, n = VP(), ctypes.c_size_t()
+        self.model.check(self.L.st_kv_view(self.h, which, ctypes.byref(p), ctypes.byref(n)))
+        return int(n.value)
+
+    def read(self, which: int, dtype, shape, stream=None):
+        """Copy a cache view into a new torch tensor of the given dtype and shape."""
+        import torch
+        out = torch.empty(shape, dtype=dtype, device="cuda")
+        nbytes = out.numel() * out.element_size()
+        self.model.check(self.L.st_kv_read(self.h, which, _ptr(out), nbytes, _stream(stream)))
+        return out
+
+
+class Operator:
+    """An operator's prompt / labels / thresholds uploaded once (an ``st_operator``)."""
+
+    def __init__(self, model: Model, op: synth.Operator):
+        self.model = model
+        self.L = model.L
+        self.op = op
+        P = len(op.prompt)
+        nl = len(op.label_ids)
+        self._prompt = (ctypes.c_int32 * P)(*op.prompt)
+        self._labels = (ctypes.c_int32 * nl)(*op.label_ids)
+        self._bias = (ctypes.c_float * nl)(*(op.bias if op.bias is not None else [0.0] * nl))
+        d = OpDesc(ctypes.cast(self._prompt, ctypes.POINTER(ctypes.c_int32)), P,
+                   ctypes.cast(self._labels, ctypes.POINTER(ctypes.c_int32)), nl,
+                   ST_OP_CLASSIFY if op.kind == "classify" else ST_OP_FILTER, float(op.r),
+                   float(op.theta_pos), float(op.theta_neg),
+                   ctypes.cast(self._bias, ctypes.POINTER(ctypes.c_float)))
+        h = VP()
+        model.check(self.L.st_op_create(model.h, ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        self.n_labels = nl
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.st_op_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, kv: KVCache, tuple_ids, logits=None, labels=None, stream=None):
+        """Run the operator on the device tuple ids; returns (logits, labels) device tensors."""
+        import torch
+        n = int(tuple_ids.numel())
+        if logits is None:
+            logits = torch.empty((n, self.n_labels), dtype=torch.float32, device="cuda")
+        if labels is None:
+            labels = torch.empty((n,), dtype=torch.int32, device="cuda")
+        self.model.check(self.L.st_op_eval(self.model.h, kv.h, self.h, _ptr(tuple_ids), n,
+                                           _ptr(logits), _ptr(labels), _stream(stream)))
+        return logits, labels
+
+    def run_host(self, kv: KVCache, tokens_host, logits_host, labels_host, kv_dtype: int,
+                 stream=None):
+        """Whole path from host buffers (pinned torch CPU tensors)."""
+        self.model.check(self.L.st_run_host(self.model.h, kv.h, self.h, int(kv_dtype),
+                                            _ptr(tokens_host), _ptr(logits_host),
+                                            _ptr(labels_host), _stream(stream)))
+
+
+def version() -> str:
+    return lib().st_version().decode()

@@ -1,0 +1,164 @@
+"""BF16 path (tcgen05 projections, tensor-core attention) against the FP64 oracle
+on the config-2 decoder (8 layers, d 1024, 16 q / 4 kv heads x 64, FFN 2816,
+vocab 32000) over a ragged table that spans several 64-slot tiles, ragged tails
+and the length extremes (1 .. 2048 tokens).  Tolerances: logits normwise
+relative error <= 2e-2 (bf16) and <= 5e-2 (E4M3 KV); retention bit-exact on
+the kernel's own scores; E4M3 codes and scales bit-exact against the oracle's
+quantiser run in float32 on the same retained values."""
+import numpy as np
+import pytest
+
+from tests.util import decide_f32, normwise_rel
+
+pytestmark = pytest.mark.gpu
+
+LENGTHS = [1, 2, 63, 64, 65, 130, 257, 600, 1000, 2048]
+
+
+@pytest.fixture(scope="module")
+def run():
+    import torch
+    from oracle import operator as O
+    from paper_2602_04430_b300 import build, stretto, synth
+    build.build()
+    cfg = synth.MODELS["c2_bf16"]
+    w = synth.make_weights(cfg, seed=21)
+    table = synth.make_table_from_lengths(LENGTHS, cfg.vocab, seed=22, ids="zipf")
+    model = stretto.Model(cfg, w, max_pos=4096)
+    kv = model.kv_alloc(table["offsets"])
+    tok = torch.from_numpy(table["tokens"]).cuda()
+    kv.build(tok)
+    torch.cuda.synchronize()
+    model.status()
+    caches = {t: O.kv_build(cfg, w, table["tokens"][table["offsets"][t]:table["offsets"][t + 1]])
+              for t in range(len(LENGTHS))}
+    return dict(cfg=cfg, w=w, table=table, model=model, kv=kv, caches=caches)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1536, 1024), (127, 1536, 1024), (128, 1024, 1024),
+                                   (300, 5632, 1024), (1000, 1024, 2816), (4096, 256, 64)])
+def test_tcgen05_gemm_matches_torch(run, M, N, K):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    W = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda", dtype=torch.float32)
+    run["model"].gemm(A, W, C)
+    torch.cuda.synchronize()
+    run["model"].status()
+    ref = A.double() @ W.double().T
+    assert normwise_rel(C.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
+
+
+def test_cache_matches_oracle(run):
+    import torch
+    from paper_2602_04430_b300 import stretto
+    cfg, off, kv = run["cfg"], run["table"]["offsets"], run["kv"]
+    R = int(off[-1])
+    K = kv.read(stretto.ST_VIEW_K, torch.bfloat16, (cfg.layers, cfg.hkv, R, cfg.hd)).float().cpu().numpy()
+    V = kv.read(stretto.ST_VIEW_V, torch.bfloat16, (cfg.layers, cfg.hkv, R, cfg.hd)).float().cpu().numpy()
+    S = kv.read(stretto.ST_VIEW_SCORES, torch.float32, (cfg.layers, cfg.hkv, R)).cpu().numpy()
+    pooled = kv.read(stretto.ST_VIEW_POOLED, torch.float32, (len(LENGTHS), cfg.d)).cpu().numpy()
+    worst = {"k": 0.0, "v": 0.0, "s": 0.0, "p": 0.0}
+    for t, c in run["caches"].items():
+        a, b = off[t], off[t + 1]
+        for l in range(cfg.layers):
+            for g in range(cfg.hkv):
+                worst["k"] = max(worst["k"], normwise_rel(K[l, g, a:b], c.k[l][g]))
+                worst["v"] = max(worst["v"], normwise_rel(V[l, g, a:b], c.v[l][g]))
+                worst["s"] = max(worst["s"], normwise_rel(S[l, g, a:b], c.scores[l][g]))
+        worst["p"] = max(worst["p"], normwise_rel(pooled[t], c.pooled))
+    print("worst normwise rel err", worst)
+    assert max(worst.values()) <= 2e-2
+
+
+@pytest.mark.parametrize("r", [1.0, 0.5, 0.25, 0.1])
+def test_retention_bit_exact(run, r):
+    import torch
+    from oracle import operator as O
+    from paper_2602_04430_b300 import stretto
+    cfg, off, kv = run["cfg"], run["table"]["offsets"], run["kv"]
+    R = int(off[-1])
+    kv.retain(r)
+    kv.status()
+    S = kv.read(stretto.ST_VIEW_SCORES, torch.float32, (cfg.layers, cfg.hkv, R)).cpu().numpy()
+    rank = kv.read(stretto.ST_VIEW_RANK, torch.int32, (cfg.layers, cfg.hkv, R)).cpu().numpy()
+    K = kv.read(stretto.ST_VIEW_K, torch.bfloat16, (cfg.layers, cfg.hkv, R, cfg.hd)).float().cpu().numpy()
+    T = len(LENGTHS)
+    offp = kv.read(stretto.ST_VIEW_OFFP, torch.int64, (T + 1,)).cpu().numpy()
+    rp_cap = kv.view_bytes(stretto.ST_VIEW_KR) // (2 * cfg.layers * cfg.hkv * cfg.hd)
+    Kr = kv.read(stretto.ST_VIEW_KR, torch.bfloat16, (cfg.layers, cfg.hkv, rp_cap, cfg.hd)).float().cpu().numpy()
+    for t in range(T):
+        a, b = off[t], off[t + 1]
+        n = O.n_keep(b - a, r)
+        for l in range(cfg.layers):
+            for g in range(cfg.hkv):
+                assert rank[l, g, a:b].tolist() == O.rank_order(S[l, g, a:b]).tolist()
+                idx = rank[l, g, a:a + n]
+                np.testing.assert_array_equal(Kr[l, g, offp[t]:offp[t] + n], K[l, g, a + idx])
+                np.testing.assert_array_equal(Kr[l, g, offp[t] + n:offp[t + 1]], 0.0)
+
+
+def _oracle_logits(run, r, rank, kv_fp8=False):
+    from oracle import operator as O
+    cfg, w, off = run["cfg"], run["w"], run["table"]["offsets"]
+    out = []
+    for t, c in run["caches"].items():
+        n = O.n_keep(c.L, r)
+        idx = [[rank[l, g, off[t]:off[t] + n] for g in range(cfg.hkv)] for l in range(cfg.layers)]
+        Kg, Vg, _ = O.retained_kv(c, r, idx=idx, kv_fp8=kv_fp8)
+        out.append(O.op_eval(cfg, w, c.L, Kg, Vg, run["op"].prompt, run["op"].label_ids))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("r,kv_dtype,tol", [(1.0, "bf16", 2e-2), (0.25, "bf16", 2e-2),
+                                            (1.0, "e4m3", 5e-2), (0.25, "e4m3", 5e-2)])
+def test_op_eval_matches_oracle(run, r, kv_dtype, tol):
+    import torch
+    from oracle import operator as O
+    from paper_2602_04430_b300 import stretto, synth
+    cfg, off, kv, model = run["cfg"], run["table"]["offsets"], run["kv"], run["model"]
+    op = synth.make_prompt(32, cfg.vocab, seed=23, label_ids=(1, 0), r=r)
+    run["op"] = op
+    kv.retain(r, stretto.ST_E4M3 if kv_dtype == "e4m3" else stretto.ST_BF16)
+    R = int(off[-1])
+    rank = kv.read(stretto.ST_VIEW_RANK, torch.int32, (cfg.layers, cfg.hkv, R)).cpu().numpy()
+    opr = model.operator(op)
+    ids = torch.arange(len(LENGTHS), dtype=torch.int32, device="cuda")
+    logits, labels = opr.eval(kv, ids)
+    torch.cuda.synchronize()
+    model.status()
+    z = logits.cpu().numpy()
+    np.testing.assert_array_equal(labels.cpu().numpy(), decide_f32(z, op.theta_pos, op.theta_neg))
+    zo = _oracle_logits(run, r, rank, kv_fp8=(kv_dtype == "e4m3"))
+    err = normwise_rel(z, zo)
+    print(f"r={r} kv={kv_dtype}: normwise rel err of label logits {err:.3e}")
+    assert np.isfinite(z).all()
+    assert err <= tol
+
+
+def test_e4m3_codes_bit_exact(run):
+    import torch
+    from oracle import fp8 as F
+    from paper_2602_04430_b300 import stretto
+    cfg, off, kv = run["cfg"], run["table"]["offsets"], run["kv"]
+    T = len(LENGTHS)
+    r = 0.5
+    kv.retain(r, stretto.ST_BF16)
+    rp_cap = kv.view_bytes(stretto.ST_VIEW_KR) // (2 * cfg.layers * cfg.hkv * cfg.hd)
+    shp = (cfg.layers, cfg.hkv, rp_cap, cfg.hd)
+    Kb = kv.read(stretto.ST_VIEW_KR, torch.bfloat16, shp).float().cpu().numpy()
+    Vb = kv.read(stretto.ST_VIEW_VR, torch.bfloat16, shp).float().cpu().numpy()
+    kv.retain(r, stretto.ST_E4M3)
+    K8 = kv.read(stretto.ST_VIEW_KR, torch.uint8, shp).cpu().numpy()
+    V8 = kv.read(stretto.ST_VIEW_VR, torch.uint8, shp).cpu().numpy()
+    sc = kv.read(stretto.ST_VIEW_SCALES, torch.float32, (cfg.layers, cfg.hkv, rp_cap // 64, 2)).cpu().numpy()
+    offp = kv.read(stretto.ST_VIEW_OFFP, torch.int64, (T + 1,)).cpu().numpy()
+    for t in range(T):
+        a, b = offp[t], offp[t + 1]
+        for l in range(cfg.layers):
+            for g in range(cfg.hkv):
+                for src, codes, which in ((Kb, K8, 0), (Vb, V8, 1)):
+                    c_ref, s_ref, _ = F.quantize_blocks(src[l, g, a:b], "f32")
+                    np.testing.assert_array_equal(codes[l, g, a:b], c_ref)
+                    np.testing.assert_array_equal(sc[l, g, a // 64:b // 64, which], s_ref)
