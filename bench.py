@@ -1,0 +1,343 @@
+"""Benchmark of the KV-cache semantic operator path on B300.
+
+One step = one pass of the whole path over one synthetic table: offline KV-cache
+creation (prefill of every document), query-agnostic retention to r, and the
+online evaluation of a binary filter operator (label logits + decisions) over
+every tuple.  Default workload: the BF16 decoder with 8 layers, d 1024, 16 q / 4
+kv heads x 64, SwiGLU 2816, vocab 32000 (random init); 4096 tuples with
+lognormal document lengths (median 512, sigma 0.6, clipped to 64..2048) and
+Zipf(1.1) token ids; a 32-token prompt; r = 0.5.
+
+Prints one JSON line.  Under torchrun each rank runs its own shard (a table of
+the same size drawn with a rank-specific seed): no collective on the data path,
+weak scaling; rank 0 prints the whole-job throughput (sum of tuples / max time).
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tuples/s: proxy+FP8 vs plain BF16 at >=99% label agreement; % HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tuples", type=int, default=None, help="override the table size")
+    ap.add_argument("--r", type=float, default=0.5)
+    ap.add_argument("--kv-dtype", default="bf16", choices=["bf16", "e4m3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the per-r op_eval sweep")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_2602_04430_b300 import synth
+    cfg = synth.MODELS["c2_bf16"]
+    tcfg = synth.TABLES["c2"]
+    T = args.tuples or tcfg.n_tuples
+    table = synth.make_table(tcfg, cfg.vocab, seed=1000 + 17 * rank, n_tuples=T)
+    op = synth.make_prompt(32, cfg.vocab, seed=77, label_ids=(1, 0), r=args.r)
+    return cfg, tcfg, table, op
+
+
+def config_dict(args, cfg, table, op):
+    L = table["lengths"]
+    return {
+        "workload": "plain BF16 KV-cache filter operator, full path per step: kv_build (prefill) "
+                    f"+ kv_retain(r={args.r}) + op_eval; decoder 8L d1024 16q/4kv x64 F2816 V32000 "
+                    f"random-init; {len(L)} tuples, lognormal(512, 0.6) lengths clipped 64..2048, "
+                    "Zipf(1.1) ids; 32-token prompt",
+        "tuples": int(len(L)), "doc_tokens": int(L.sum()), "mean_len": float(L.mean()),
+        "prompt_len": len(op.prompt), "r": args.r, "kv_dtype": args.kv_dtype,
+        "l2": "inputs larger than L2 (full KV cache %.1f GB per step)" % (
+            8 * 4 * 64 * 2 * 2 * float(L.sum()) / 1e9),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows
+                                    if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def cpu_oracle_rate(args, cfg, table, op, seconds):
+    """The FP64 oracle (as it stands) on a bounded sample of the same table:
+    full path per tuple (kv_build, retention, op_eval, decision)."""
+    from oracle import operator as O
+    from paper_2602_04430_b300 import synth
+    w = synth.make_weights(cfg, seed=4242)
+    rng = np.random.Generator(np.random.PCG64(11))
+    order = list(rng.permutation(len(table["lengths"])))
+    done, t0 = 0, time.perf_counter()
+    tokens = 0
+    while done < len(order):
+        t = int(order[done])
+        a, b = table["offsets"][t], table["offsets"][t + 1]
+        c = O.kv_build(cfg, w, table["tokens"][a:b])
+        Kr, Vr, _ = O.retained_kv(c, op.r)
+        z = O.op_eval(cfg, w, c.L, Kr, Vr, op.prompt, op.label_ids)
+        O.decide(op, z)
+        done += 1
+        tokens += int(b - a)
+        if time.perf_counter() - t0 >= seconds and done >= 2:
+            break
+    el = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([int(i.get("num_threads", 1)) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": done / el, "unit": "tuples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} random tuples of the same table ({tokens} document tokens), full "
+                      f"path per tuple in float64 numpy, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg, tcfg, table, op = workload(args)
+    res = cpu_oracle_rate(args, cfg, table, op, args.cpu_seconds)
+    per_step = max(1, round(res["value"] * 5.0))
+    ms = 1000.0 * per_step / res["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "tuples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, cfg, table, op),
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "tuples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def attention_bytes(cfg, lengths, r, kv_esz):
+    """Algorithmic HBM bytes of the operator's attention over retained KV (all layers):
+    retained K and V once, plus the E4M3 block scales."""
+    from oracle.operator import n_keep  # host arithmetic only: the retained counts
+    n = np.array([n_keep(int(L), r) for L in lengths], dtype=np.float64)
+    kv = 2.0 * cfg.layers * cfg.hkv * cfg.hd * kv_esz * n.sum()
+    scales = 0.0 if kv_esz == 2 else 2.0 * 4 * cfg.layers * cfg.hkv * np.ceil(n / 64).sum()
+    return kv + scales
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2602_04430_b300 import stretto, synth
+    from paper_2602_04430_b300 import build as _b
+    _b.build()
+    cfg, tcfg, table, op = workload(args, rank)
+    w = synth.make_weights(cfg, seed=4242)
+    model = stretto.Model(cfg, w, max_pos=2048 + 64)
+    del w
+    kv = model.kv_alloc(table["offsets"])
+    T = len(table["lengths"])
+    kvd = stretto.ST_E4M3 if args.kv_dtype == "e4m3" else stretto.ST_BF16
+    opr = model.operator(op)
+    tok = torch.from_numpy(table["tokens"]).cuda()
+    ids = torch.arange(T, dtype=torch.int32, device="cuda")
+    logits = torch.empty((T, 2), dtype=torch.float32, device="cuda")
+    labels = torch.empty((T,), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        kv.build(tok)
+        kv.retain(op.r, kvd)
+        opr.eval(kv, ids, logits, labels)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    model.status()
+    kv.status()
+    model.prof_reset()
+    model.prof_enable(True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    model.prof_enable(False)
+    prof = model.prof_read()
+    launches = model.launch_count()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    total_tuples = T * world * args.steps
+    value = total_tuples / (ms_max / 1000.0)
+    clocks = clk.summary()
+    model.status()
+
+    # ---- per-kernel roofline: the tcgen05 GEMM (dominant) and the eval attention
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    tf_peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "measured" if peaks else "fallback"
+    g = prof["gemm"]
+    gemm_tf = g["flops"] / (g["ms"] / 1000.0) / 1e12 if g["ms"] > 0 else 0.0
+    roofline = {"kernel": "k_gemm_tc (tcgen05 BF16 projection GEMM)", "bound": "tensor",
+                "achieved": gemm_tf, "peak": tf_peak, "unit": "TFLOP/s",
+                "frac": gemm_tf / tf_peak, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "traffic": None, "launches": int(g["launches"]),
+                "share_of_step": g["ms"] / ms if ms > 0 else None}
+    out = {}
+    if not args.no_extra and rank == 0:
+        # op_eval alone at every r of the ladder (KV resident), CUDA events, after warm-up
+        kv_esz = 1 if args.kv_dtype == "e4m3" else 2
+        for r in (1.0, 0.5, 0.25, 0.1):
+            kv.retain(r, kvd)
+            opr_r = model.operator(synth.make_prompt(32, cfg.vocab, seed=77, label_ids=(1, 0), r=r))
+            for _ in range(2):
+                opr_r.eval(kv, ids, logits, labels)
+            torch.cuda.synchronize()
+            model.prof_reset()
+            model.prof_enable(True)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            reps = 3
+            for _ in range(reps):
+                opr_r.eval(kv, ids, logits, labels)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            model.prof_enable(False)
+            pr = model.prof_read()
+            e_ms = a0.elapsed_time(a1) / reps
+            at = pr["attention"]
+            ab = attention_bytes(cfg, table["lengths"], r, kv_esz)
+            gbs = ab / (at["ms"] / reps / 1000.0) / 1e9 if at["ms"] > 0 else 0.0
+            gg = pr["gemm"]
+            out[str(r)] = {"tuples_per_s": T / (e_ms / 1000.0), "ms": e_ms,
+                           "attention_ms": at["ms"] / reps, "attention_GBps": gbs,
+                           "attention_hbm_frac": gbs / hbm_peak,
+                           "gemm_ms": gg["ms"] / reps,
+                           "gemm_TFLOPs": gg["flops"] / (gg["ms"] / 1000.0) / 1e12 if gg["ms"] else 0}
+        kv.retain(op.r, kvd)
+    e2e = None
+    if not args.no_e2e:
+        tok_h = torch.from_numpy(table["tokens"]).pin_memory()
+        lg_h = torch.empty((T, 2), dtype=torch.float32).pin_memory()
+        lb_h = torch.empty((T,), dtype=torch.int32).pin_memory()
+        opr.run_host(kv, tok_h, lg_h, lb_h, kvd)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            opr.run_host(kv, tok_h, lg_h, lb_h, kvd)
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": total_tuples / float(te.item()), "unit": "tuples/s",
+               "h2d_bytes_per_step": int(tok_h.numel() * 4),
+               "d2h_bytes_per_step": int(T * 2 * 4 + T * 4),
+               "path": "st_run_host: pinned host tokens -> device, kv_build, kv_retain, op_eval, "
+                       "logits + labels -> pinned host, synchronised every step"}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_rate(args, cfg, table, op, args.cpu_seconds)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "data": "synthetic (seeded random-init weights and token tables)",
+                "config": config_dict(args, cfg, table, op), "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+                "per_family_ms": {k: v["ms"] for k, v in prof.items()},
+                "op_eval": out}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
