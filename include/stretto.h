@@ -207,6 +207,37 @@ int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
                const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
                int32_t* labels_dev, void* stream);
 
+/* ---- operator evaluation without device allocation ----
+ *
+ * The paper has no counterpart to this entry; it exists for callers that
+ * cannot let the library allocate device memory: a query executor that keeps
+ * several streams busy cannot afford the implicit device synchronisation of
+ * cudaFree (and at times cudaMalloc), and a process whose GPU memory is already
+ * claimed by another framework's caching allocator can see a fresh cudaMalloc
+ * fail although that allocator holds free blocks.
+ *
+ * st_op_eval_noalloc computes exactly what st_op_eval computes (same kernels,
+ * same order) but never allocates: its activations live in one file-scope
+ * device array of ST_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the
+ * library holds until the process exits.  The caller still passes the inputs
+ * (context, caches, operator, DEVICE tuple ids) and the outputs (DEVICE logits
+ * float32 [n][n_labels], labels int32 [n]).
+ *   - Size limit: n * P prompt rows must fit the array (about 16.9 KB per row
+ *     for the config-2 decoder: 62 tuples with a 32-token prompt); larger n is
+ *     rejected with ST_EINVAL and a message giving the bytes needed.
+ *   - The first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents (nothing
+ *     in it needs to start at zero).  Calls whose work overlaps on the GPU (two
+ *     streams or two host threads) race on it: serialise them.
+ *   - No profiling events are recorded for this entry (st_prof_read omits it);
+ *     its launches are counted by st_launch_count. */
+#define ST_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operator* op,
+                       const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
+                       int32_t* labels_dev, void* stream);
+
 /* The whole path from HOST buffers: copy tokens_host (int32 [offsets[T]]) to
  * the device, st_kv_build, st_kv_retain(op->r, kv_dtype), st_op_eval over all
  * T tuples, and copy logits (float32 [T][n_labels]) and labels (int32 [T]) back

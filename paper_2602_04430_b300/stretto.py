@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
         "st_op_create": (i32, [VP, ctypes.POINTER(OpDesc), ctypes.POINTER(VP)]),
         "st_op_free": (None, [VP]),
         "st_op_eval": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
+        "st_op_eval_noalloc": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
         "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
         "st_prof_enable": (i32, [VP, i32]),
@@ -275,6 +276,14 @@ class Operator:
             labels = torch.empty((n,), dtype=torch.int32, device="cuda")
         self.model.check(self.L.st_op_eval(self.model.h, kv.h, self.h, _ptr(tuple_ids), n,
                                            _ptr(logits), _ptr(labels), _stream(stream)))
+        return logits, labels
+
+    def eval_noalloc(self, kv: KVCache, tuple_ids, logits, labels, stream=None):
+        """Same as ``eval`` through the entry that allocates no device memory (its
+        activations live in the library's fixed-size static scratch array)."""
+        n = int(tuple_ids.numel())
+        self.model.check(self.L.st_op_eval_noalloc(self.model.h, kv.h, self.h, _ptr(tuple_ids), n,
+                                                   _ptr(logits), _ptr(labels), _stream(stream)))
         return logits, labels
 
     def run_host(self, kv: KVCache, tokens_host, logits_host, labels_host, kv_dtype: int,
