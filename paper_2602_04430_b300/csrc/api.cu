@@ -230,17 +230,20 @@ int rmsnorm(st_ctx* ctx, const float* x, int64_t rows, void* xn, float* inv, cud
   return ST_OK;
 }
 
-int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_items,
-              cudaStream_t s) {
+int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_items, cudaStream_t s) {
   const st_model_cfg& c = ctx->cfg;
   Launch L(ctx, s, ST_PROF_ATTN, 0, 0);
+  int rc = ST_OK;
   if (c.dtype == ST_F32) {
     attn_simt<float, float>(a, s);
   } else if (a.mode == 0) {
-    attn_mma_prefill(a, items, n_items, s);
-  } else {
+    rc = attn_tc_prefill(a, items, n_items, ctx->dstatus, s);
+  } else if (a.kv_dtype == ST_E4M3) {
     attn_mma_eval(a, s);
+  } else {
+    rc = attn_tc_eval(a, ctx->dstatus, s);
   }
+  if (rc != ST_OK) return fail(ctx, rc, "tcgen05 attention: unsupported shape or tensor-map encoding failed");
   CKLAUNCH();
   return ST_OK;
 }
@@ -457,6 +460,15 @@ extern "C" int st_kv_alloc(st_ctx* ctx, const int64_t* offsets_host, int32_t T, 
     acc += (offsets_host[t + 1] - offsets_host[t] + qb - 1) / qb;
   }
   kv->item_start[T] = acc;
+  // the retained cache starts zeroed: tiles that run past a tuple's padded segment
+  // (into unused capacity) then read finite values, which the masks discard
+  cudaMemset(kv->Kr, 0, LH * rp * c.hd * e);
+  cudaMemset(kv->Vr, 0, LH * rp * c.hd * e);
+  err = cudaDeviceSynchronize();
+  if (err != cudaSuccess) {
+    st_kv_free(kv);
+    return fail(ctx, ST_ECUDA, std::string("st_kv_alloc: ") + cudaGetErrorString(err));
+  }
   *out = kv;
   return ST_OK;
 }
@@ -465,7 +477,8 @@ extern "C" void st_kv_free(st_kv* kv) {
   if (!kv) return;
   cudaDeviceSynchronize();
   void* ptrs[] = {kv->off, kv->K, kv->V, kv->scores, kv->pooled, kv->rank, kv->Kr, kv->Vr,
-                  kv->scales, kv->offp, kv->nkeep, kv->status, kv->items, kv->tok, kv->iota};
+                  kv->scales, kv->offp, kv->nkeep, kv->status, kv->items, kv->tok, kv->iota,
+                  kv->out_logits, kv->out_labels};
   for (void* p : ptrs) cudaFree(p);
   delete kv;
 }

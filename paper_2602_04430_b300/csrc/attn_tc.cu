@@ -1,0 +1,523 @@
+// Attention on the 5th-generation tensor cores (tcgen05) for one kv head and
+// 128 query rows per CTA: all G query heads of the group share every key/value
+// tile staged in shared memory.
+//
+//   S = Q K^T   tcgen05.mma M128 N128 K16 x4, Q and K K-major (128-byte swizzle),
+//               f32 accumulator in TMEM (two 128-column buffers).
+//   softmax     4 warps, one thread per query row: the row is that thread's TMEM
+//               lane, so max / exp2 / sum need no shuffles; P is written as bf16
+//               to shared memory in the MMA's K-major swizzled layout.
+//   O += P V    tcgen05.mma M128 N64 K16 x8, V read MN-major straight from its
+//               [key][dim] tile; the per-tile partial lands in TMEM (two
+//               64-column buffers) and is folded into the thread's registers with
+//               the online-softmax rescale.
+//   loads       one thread issues TMA for 128-key K and V tiles (two stages).
+//
+// Modes: prefill (the document's own keys, causal) and eval (the tuple's
+// retained slots, all visible, then the prompt's keys, causal).
+// Every mbarrier wait is bounded; a timeout sets the status word.
+#include <cudaTypedefs.h>
+
+#include "kernels.h"
+#include "ptx.cuh"
+
+namespace st {
+namespace {
+
+constexpr int HD = 64;
+constexpr int TK = 128;          // keys per tile
+constexpr int ROWS = 128;        // query rows per work item
+constexpr int NKV = 3;           // K/V stages
+constexpr int NT = 224;          // warps 0-3 softmax, 4 K/V loads, 5 MMA, 6 Q loads
+constexpr int OFF_Q = 0;                           // 2 x 16 KB
+constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // NKV x 16 KB
+constexpr int OFF_V = OFF_K + NKV * TK * 128;      // NKV x 16 KB
+constexpr int OFF_P = OFF_V + NKV * TK * 128;      // 2 x 32 KB (two 64-key sub-tiles each)
+constexpr int OFF_BAR = OFF_P + 2 * ROWS * TK * 2;
+constexpr size_t SMEM = OFF_BAR + 256 + 1024;
+constexpr uint32_t TMEM_COLS = 512;              // S: [0,256), PV: [256,384)
+
+struct Bars {
+  uint64_t kv_full[NKV], kv_empty[NKV], s_full[2], s_free[2], p_full[2], pv_full[2], pv_free[2];
+  uint64_t q_full[2], q_empty[2];
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ uint32_t swz(int row, int chunk) {
+  return (uint32_t)(row * 128 + ((chunk ^ (row & 7)) << 4));
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// 2^x on the special-function unit (flushes subnormal results to zero, which a
+// softmax probability can afford).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+// MN-major operand with the 128-byte swizzle: 64 elements (128 B) along N per
+// row, 8 K-rows per 1024-byte atom; consecutive 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(1024 >> 4) << 16;   // leading byte offset (one 64-wide N atom: unused)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset between 8-row K groups
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+struct TileInfo {
+  bool prompt;
+  int key0, count;
+};
+
+// One work item: 128 query rows of one kv head of one tuple.
+template <int MODE>
+struct Work {
+  int g, G, rows, row_base, n_tiles, n_doc_tiles;
+  int i, n_doc, P;          // eval
+  int t, j0, L;             // prefill
+  int64_t doc_row0, prompt_row0, qrow0;
+
+  __device__ void decode(const AttnParams& a, const int32_t* items, int w, int zb_count) {
+    G = a.hq / a.hkv;
+    if (MODE == 1) {
+      const int zb = w % zb_count;
+      const int rest = w / zb_count;
+      g = rest % a.hkv;
+      i = rest / a.hkv;
+      P = a.P;
+      row_base = zb * ROWS;
+      rows = min(ROWS, a.P * G - row_base);
+      const int tt = a.tup[i];
+      n_doc = a.nk[i];
+      doc_row0 = (int64_t)g * a.Rp_cap + a.offp[tt];
+      prompt_row0 = (int64_t)i * a.P;
+      qrow0 = (int64_t)i * a.P + row_base / G;
+      n_doc_tiles = (n_doc + TK - 1) / TK;
+      n_tiles = n_doc_tiles + (a.P + TK - 1) / TK;
+    } else {
+      const int it = w / a.hkv;
+      g = w % a.hkv;
+      t = items[2 * it];
+      j0 = items[2 * it + 1];
+      L = (int)(a.off[t + 1] - a.off[t]);
+      row_base = 0;
+      rows = ROWS;
+      doc_row0 = (int64_t)g * a.R + a.off[t];
+      qrow0 = a.off[t] - a.r0 + j0;
+      const int last = min(j0 + ROWS / G, L) - 1;
+      n_doc_tiles = last / TK + 1;
+      n_tiles = n_doc_tiles;
+    }
+  }
+  __device__ TileInfo tile(int ti) const {
+    TileInfo T;
+    if (MODE == 1 && ti >= n_doc_tiles) {
+      T.prompt = true;
+      T.key0 = (ti - n_doc_tiles) * TK;
+      T.count = min(TK, P - T.key0);
+    } else {
+      T.prompt = false;
+      T.key0 = ti * TK;
+      T.count = min(TK, (MODE == 1 ? n_doc : L) - T.key0);
+    }
+    return T;
+  }
+};
+
+// Persistent: CTA b processes work items b, b + gridDim.x, ...; the load, MMA
+// and softmax roles each walk the same sequence, connected by mbarrier rings
+// (Q: 2 buffers, K/V: 3 stages, S and PV accumulators: 2 TMEM buffers each,
+// P: 2 shared-memory tiles), so the next item's loads overlap this item's math.
+template <int MODE>
+__global__ void __launch_bounds__(NT, 1)
+    k_attn_tc(AttnParams a, const int32_t* __restrict__ items, int n_work, int zb_count,
+              const __grid_constant__ CUtensorMap tmQ,
+              const __grid_constant__ CUtensorMap tmK, const __grid_constant__ CUtensorMap tmV,
+              const __grid_constant__ CUtensorMap tmKp, const __grid_constant__ CUtensorMap tmVp,
+              int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  Bars* bars = reinterpret_cast<Bars*>(smem + OFF_BAR);
+  const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
+  const uint32_t sK0 = ptx::smem_u32(smem + OFF_K), sV0 = ptx::smem_u32(smem + OFF_V);
+  const uint32_t sP0 = ptx::smem_u32(smem + OFF_P);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NKV; ++s) {
+      ptx::mbar_init(&bars->kv_full[s], 1);
+      ptx::mbar_init(&bars->kv_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      ptx::mbar_init(&bars->s_full[s], 1);
+      ptx::mbar_init(&bars->s_free[s], 128);
+      ptx::mbar_init(&bars->p_full[s], 128);
+      ptx::mbar_init(&bars->pv_full[s], 1);
+      ptx::mbar_init(&bars->pv_free[s], 128);
+      ptx::mbar_init(&bars->q_full[s], 1);
+      ptx::mbar_init(&bars->q_empty[s], 129);   // the MMA's commit + 128 softmax threads
+    }
+    ptx::fence_mbar_init();
+  }
+  if (warp == 5) {
+    ptx::tmem_alloc(&bars->tmem, TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = bars->tmem;
+
+  if (warp == 6) {
+    // ------------------------------------------------------------ TMA: Q, up to 2 items ahead
+    if (lane == 0) {
+      ptx::tma_prefetch_desc(&tmQ);
+      int last_q[2] = {-1, -1};
+      uint32_t qc = 0;
+      for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++qc) {
+        Work<MODE> W;
+        W.decode(a, items, w, zb_count);
+        const int qb = qc & 1;
+        if (!ptx::mbar_wait(&bars->q_empty[qb], ((qc >> 1) & 1) ^ 1)) {
+          atomicExch(status, ST_ETIMEOUT);
+          break;
+        }
+        ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
+        ptx::tma_load_3d(smem + OFF_Q + qb * ROWS * 128, &tmQ, &bars->q_full[qb], 0, W.g * W.G,
+                         (int)W.qrow0);
+        last_q[qb] = (int)((qc >> 1) & 1);
+      }
+      for (int s = 0; s < 2; ++s)
+        if (last_q[s] >= 0) ptx::mbar_wait(&bars->q_full[s], (uint32_t)last_q[s], 100000000LL);
+    }
+  } else if (warp == 4) {
+    // ------------------------------------------------------------ TMA: K/V tiles
+    if (lane == 0) {
+      ptx::tma_prefetch_desc(&tmK);
+      ptx::tma_prefetch_desc(&tmV);
+      int last_kv[NKV];
+      for (int s = 0; s < NKV; ++s) last_kv[s] = -1;
+      bool ok = true;
+      uint32_t c = 0;   // tile counter of this CTA
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+        Work<MODE> W;
+        W.decode(a, items, w, zb_count);
+        for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
+          const int s = c % NKV;
+          const uint32_t u = c / NKV;
+          if (!ptx::mbar_wait(&bars->kv_empty[s], (u & 1) ^ 1)) { ok = false; break; }
+          const TileInfo T = W.tile(ti);
+          ptx::mbar_arrive_expect_tx(&bars->kv_full[s], 2 * TK * 128);
+          uint8_t* dk = smem + OFF_K + s * TK * 128;
+          uint8_t* dv = smem + OFF_V + s * TK * 128;
+          if (T.prompt) {
+            const int y = (int)(W.prompt_row0 + T.key0);
+            ptx::tma_load_2d(dk, &tmKp, &bars->kv_full[s], W.g * HD, y);
+            ptx::tma_load_2d(dv, &tmVp, &bars->kv_full[s], W.g * HD, y);
+          } else {
+            const int y = (int)(W.doc_row0 + T.key0);
+            ptx::tma_load_2d(dk, &tmK, &bars->kv_full[s], 0, y);
+            ptx::tma_load_2d(dv, &tmV, &bars->kv_full[s], 0, y);
+          }
+          last_kv[s] = (int)(u & 1);
+        }
+      }
+      if (!ok) atomicExch(status, ST_ETIMEOUT);
+      for (int s = 0; s < NKV; ++s)
+        if (last_kv[s] >= 0) ptx::mbar_wait(&bars->kv_full[s], (uint32_t)last_kv[s], 100000000LL);
+    }
+  } else if (warp == 5) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t idS = ptx::idesc_bf16_f32(ROWS, TK);
+      constexpr uint32_t idPV = ptx::idesc_bf16_f32(ROWS, HD) | (1u << 16);   // B MN-major
+      bool ok = true;
+      uint32_t c = 0, qc = 0;
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
+        Work<MODE> W;
+        W.decode(a, items, w, zb_count);
+        const int qb = qc & 1;
+        if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t sQ = sQ0 + qb * ROWS * 128;
+        const uint32_t base = c;
+        auto issue_s = [&](uint32_t cc) -> bool {
+          const int s = cc % NKV, b = cc & 1;
+          if (!ptx::mbar_wait(&bars->kv_full[s], (cc / NKV) & 1)) return false;
+          if (!ptx::mbar_wait(&bars->s_free[b], ((cc >> 1) & 1) ^ 1)) return false;
+          ptx::tc_fence_after();
+          const uint32_t kb = sK0 + s * TK * 128;
+#pragma unroll
+          for (int k = 0; k < HD / 16; ++k)
+            ptx::mma_f16(tmem + b * TK, ptx::desc_kmajor_sw128(sQ + k * 32),
+                         ptx::desc_kmajor_sw128(kb + k * 32), idS, k > 0);
+          ptx::mma_commit(&bars->s_full[b]);
+          return true;
+        };
+        if (!(ok = issue_s(base))) break;
+        for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
+          if (ti + 1 < W.n_tiles && !(ok = issue_s(c + 1))) break;
+          const int b = c & 1;
+          const uint32_t u = c >> 1;
+          if (!ptx::mbar_wait(&bars->p_full[b], u & 1)) { ok = false; break; }
+          if (!ptx::mbar_wait(&bars->pv_free[b], (u & 1) ^ 1)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t pb = sP0 + b * ROWS * TK * 2;
+          const uint32_t vb = sV0 + (c % NKV) * TK * 128;
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk)
+            ptx::mma_f16(tmem + 2 * TK + b * HD,
+                         ptx::desc_kmajor_sw128(pb + (kk >> 2) * (ROWS * 128) + (kk & 3) * 32),
+                         desc_mnmajor_sw128(vb + kk * 2048), idPV, kk > 0);
+          ptx::mma_commit(&bars->pv_full[b]);
+          ptx::mma_commit(&bars->kv_empty[c % NKV]);
+        }
+        if (!ok) break;
+        ptx::mma_commit(&bars->q_empty[qb]);
+      }
+      if (!ok) atomicExch(status, ST_ETIMEOUT);
+      // every commit of this thread has landed once the last stages are released
+      if (ok)
+        for (uint32_t cc = c >= NKV ? c - NKV : 0; cc < c; ++cc)
+          ptx::mbar_wait(&bars->kv_empty[cc % NKV], (cc / NKV) & 1, 100000000LL);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ softmax warps
+    const int r = threadIdx.x;                 // query row == TMEM lane
+    const float sl2 = a.scale * 1.4426950408889634f;
+    const uint32_t lane_base = (uint32_t)((warp * 32) << 16);
+    bf16* og = reinterpret_cast<bf16*>(a.o);
+    const bf16* qg = reinterpret_cast<const bf16*>(a.q);
+    bool ok = true;
+    uint32_t c = 0, qc = 0;
+    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
+      Work<MODE> W;
+      W.decode(a, items, w, zb_count);
+      const int qb = qc & 1;
+      const int rr = W.row_base + r;
+      const int pos = rr / W.G, hh = rr % W.G;
+      bool row_ok = r < W.rows;
+      if (MODE == 0) row_ok = row_ok && (W.j0 + pos) < W.L;
+      ptx::mbar_arrive(&bars->q_empty[qb]);
+
+      float m = -INFINITY, l = 0.f, alpha_prev = 0.f;
+      float o[HD];
+#pragma unroll
+      for (int e = 0; e < HD; ++e) o[e] = 0.f;
+      const int lim = MODE == 0 ? W.j0 + pos : pos;   // causal limit of this row
+      auto fold_pv = [&](uint32_t cj) {
+        const int b = cj & 1;
+        if (!ptx::mbar_wait(&bars->pv_full[b], (cj >> 1) & 1)) { ok = false; return; }
+        ptx::tc_fence_after();
+        uint32_t v0[32], v1[32];
+        ST_TMEM_LD32(tmem + lane_base + 2 * TK + b * HD, v0);
+        ST_TMEM_LD32(tmem + lane_base + 2 * TK + b * HD + 32, v1);
+        ptx::tmem_wait_ld();
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(&bars->pv_free[b]);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          o[e] = fmaf(o[e], alpha_prev, __uint_as_float(v0[e]));
+          o[32 + e] = fmaf(o[32 + e], alpha_prev, __uint_as_float(v1[e]));
+        }
+      };
+      for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
+        const int b = c & 1;
+        const TileInfo T = W.tile(ti);
+        const bool causal = (MODE == 0) || T.prompt;
+        if (!ptx::mbar_wait(&bars->s_full[b], (c >> 1) & 1)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t sb = tmem + lane_base + b * TK;
+        // the whole S row into registers with one wait, then release the TMEM buffer
+        uint32_t v[TK];
+        ST_TMEM_LD32(sb, v);
+        ST_TMEM_LD32(sb + 32, (v + 32));
+        ST_TMEM_LD32(sb + 64, (v + 64));
+        ST_TMEM_LD32(sb + 96, (v + 96));
+        ptx::tmem_wait_ld();
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(&bars->s_free[b]);
+        // invisible keys of this row (ragged tail, causal limit) become -inf
+        int nvis = T.count;
+        if (causal) nvis = min(nvis, lim - T.key0 + 1);
+        if (nvis < TK) {
+#pragma unroll
+          for (int k = 0; k < TK; ++k)
+            if (k >= nvis) v[k] = 0xFF800000u;
+        }
+        float mx4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+        for (int k = 0; k < TK; ++k) mx4[k & 3] = fmaxf(mx4[k & 3], __uint_as_float(v[k]));
+        const float mx = fmaxf(fmaxf(mx4[0], mx4[1]), fmaxf(mx4[2], mx4[3])) * sl2;
+        const float mn = fmaxf(m, mx);
+        const float base = mn == -INFINITY ? 0.f : mn;
+        const float alpha = ex2(m - base);
+        // probabilities -> bf16 P tile (K-major, 128-byte swizzle)
+        float rs4[4] = {0.f, 0.f, 0.f, 0.f};
+        uint8_t* prow = smem + OFF_P + b * (ROWS * TK * 2);
+#pragma unroll
+        for (int k8 = 0; k8 < TK; k8 += 8) {
+          uint32_t pk[4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            const float p0 = ex2(fmaf(__uint_as_float(v[k8 + e]), sl2, -base));
+            const float p1 = ex2(fmaf(__uint_as_float(v[k8 + e + 1]), sl2, -base));
+            rs4[e >> 1] += p0 + p1;
+            pk[e >> 1] = pack_bf16(p0, p1);
+          }
+          *reinterpret_cast<uint4*>(prow + (k8 >> 6) * (ROWS * 128) + swz(r, (k8 & 63) >> 3)) =
+              make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        const float rs = (rs4[0] + rs4[1]) + (rs4[2] + rs4[3]);
+        fence_proxy_async();
+        ptx::mbar_arrive(&bars->p_full[b]);
+        l = l * alpha + rs;
+        if (ti >= 1) fold_pv(c - 1);
+        alpha_prev = alpha;
+        m = mn;
+      }
+      if (!ok) break;
+      fold_pv(c - 1);
+      if (!ok) break;
+      if (row_ok) {
+        const float inv = l > 0.f ? 1.f / l : 0.f;
+        int64_t orow;
+        if (MODE == 1) orow = ((int64_t)W.i * a.P + pos) * a.hq + (int64_t)W.g * W.G + hh;
+        else orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
+        uint4* dst = reinterpret_cast<uint4*>(og + orow * HD);
+#pragma unroll
+        for (int e = 0; e < HD; e += 8)
+          dst[e / 8] = make_uint4(pack_bf16(o[e] * inv, o[e + 1] * inv),
+                                  pack_bf16(o[e + 2] * inv, o[e + 3] * inv),
+                                  pack_bf16(o[e + 4] * inv, o[e + 5] * inv),
+                                  pack_bf16(o[e + 6] * inv, o[e + 7] * inv));
+      }
+    }
+    if (!ok) atomicExch(status, ST_ETIMEOUT);
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return false;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {(cuuint32_t)HD, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool map_q(CUtensorMap* m, const void* q, int hq, uint64_t rows, int G) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) !=
+            cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess)
+      return false;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  // q [rows][hq][64] bf16 viewed as (dim, head, row); a box is 128/G rows x G heads x 64 dims,
+  // i.e. 128 smem lines ordered (row, head of the group).
+  cuuint64_t dims[3] = {(cuuint64_t)HD, (cuuint64_t)hq, rows};
+  cuuint64_t strides[2] = {(cuuint64_t)HD * 2, (cuuint64_t)hq * HD * 2};
+  cuuint32_t box[3] = {(cuuint32_t)HD, (cuuint32_t)G, (cuuint32_t)(ROWS / G)};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(q), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return n;
+}
+
+template <int MODE>
+void set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_attn_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    done = true;
+  }
+}
+
+}  // namespace
+
+bool attn_tc_supported(int hq, int hkv, int hd) {
+  const int G = hq / hkv;
+  return hd == HD && G >= 1 && G <= ROWS && ROWS % G == 0;
+}
+
+int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
+  if (a.n <= 0) return ST_OK;
+  if (!attn_tc_supported(a.hq, a.hkv, a.hd) || a.kv_dtype != ST_BF16) return ST_EUNSUPPORTED;
+  const int G = a.hq / a.hkv;
+  CUtensorMap mq, mk, mv, mkp, mvp;
+  const uint64_t planes = (uint64_t)a.hkv * a.Rp_cap;
+  const uint64_t prow = (uint64_t)a.n * a.P;
+  if (!map_q(&mq, a.q, a.hq, prow, G) || !map2d(&mk, a.Kr, HD, planes, TK) ||
+      !map2d(&mv, a.Vr, HD, planes, TK) || !map2d(&mkp, a.kp, (uint64_t)a.hkv * HD, prow, TK) ||
+      !map2d(&mvp, a.vp, (uint64_t)a.hkv * HD, prow, TK))
+    return ST_ECUDA;
+  set_smem_attr<1>();
+  const int zb = (a.P * G + ROWS - 1) / ROWS;
+  const int n_work = a.n * a.hkv * zb;
+  const int grid = n_work < sm_count() ? n_work : sm_count();
+  k_attn_tc<1><<<grid, NT, SMEM, s>>>(a, nullptr, n_work, zb, mq, mk, mv, mkp, mvp, status);
+  return ST_OK;
+}
+
+int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int* status,
+                    cudaStream_t s) {
+  if (n_items <= 0) return ST_OK;
+  if (!attn_tc_supported(a.hq, a.hkv, a.hd)) return ST_EUNSUPPORTED;
+  const int G = a.hq / a.hkv;
+  CUtensorMap mq, mk, mv;
+  const uint64_t planes = (uint64_t)a.hkv * a.R;
+  if (!map_q(&mq, a.q, a.hq, (uint64_t)a.rows, G) || !map2d(&mk, a.K, HD, planes, TK) ||
+      !map2d(&mv, a.V, HD, planes, TK))
+    return ST_ECUDA;
+  set_smem_attr<0>();
+  const int n_work = n_items * a.hkv;
+  const int grid = n_work < sm_count() ? n_work : sm_count();
+  k_attn_tc<0><<<grid, NT, SMEM, s>>>(a, items, n_work, 1, mq, mk, mv, mk, mv, status);
+  return ST_OK;
+}
+
+}  // namespace st

@@ -110,6 +110,10 @@ struct AttnParams {
 template <typename act_t, typename kv_t>
 void attn_simt(const AttnParams& a, cudaStream_t s);
 void attn_mma_eval(const AttnParams& a, cudaStream_t s);
+bool attn_tc_supported(int hq, int hkv, int hd);
+int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s);
+int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int* status,
+                    cudaStream_t s);
 void attn_mma_prefill(const AttnParams& a, const int32_t* items, int n_items, cudaStream_t s);
 
 // ---- retention (retain.cu) ----

@@ -148,6 +148,15 @@ void embed_prompt(const int32_t* prompt, int P, int64_t rows, const void* E, int
 }
 
 // ------------------------------------------------------------------ RMSNorm
+__device__ __forceinline__ void store4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void store4(bf16* p, float4 v) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t*>(&a);
+  u.y = *reinterpret_cast<uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
 // One warp per row; x float32 [rows][d] -> xn = x / sqrt(mean(x^2) + eps) (act type).
 template <typename act_t>
 __global__ void k_rmsnorm(const float* __restrict__ x, int64_t rows, int d, float eps,
@@ -168,10 +177,7 @@ __global__ void k_rmsnorm(const float* __restrict__ x, int64_t rows, int d, floa
   act_t* o = xn + row * d;
   for (int c = lane * 4; c < d; c += 128) {
     float4 v = *reinterpret_cast<const float4*>(xr + c);
-    o[c] = from_f<act_t>(v.x * inv);
-    o[c + 1] = from_f<act_t>(v.y * inv);
-    o[c + 2] = from_f<act_t>(v.z * inv);
-    o[c + 3] = from_f<act_t>(v.w * inv);
+    store4(o + c, make_float4(v.x * inv, v.y * inv, v.z * inv, v.w * inv));
   }
 }
 
@@ -187,42 +193,59 @@ template void rmsnorm_rows<bf16>(const float*, int64_t, int, float, bf16*, float
 // ------------------------------------------------------------------ EA-lite statistics
 // Block per (tuple, kv head): mean and population variance over (document
 // position, query head of the group) of every post-RoPE query dimension.
+// One pass, shifted by the group's first query vector for stability:
+// mean = shift + S1/N, var = S2/N - (S1/N)^2 with S1 = sum(q - shift),
+// S2 = sum((q - shift)^2).  Each thread reads 16-byte vectors (VN dims) of
+// consecutive (position, head) items, so a warp reads whole rows.
 template <typename act_t>
-__global__ void k_qstats(const act_t* __restrict__ q, const int64_t* __restrict__ off, int t0,
-                         int64_t r0, int hq, int hkv, int hd, float* __restrict__ mu,
-                         float* __restrict__ s2) {
-  __shared__ float red[256];
+__global__ void __launch_bounds__(256) k_qstats(const act_t* __restrict__ q,
+                                                const int64_t* __restrict__ off, int t0, int64_t r0,
+                                                int hq, int hkv, int hd, float* __restrict__ mu,
+                                                float* __restrict__ s2) {
+  constexpr int VN = Vec<act_t>::N;           // dims per 16-byte vector
+  __shared__ float red[2][256][VN];
   const int t = t0 + blockIdx.x / hkv, g = blockIdx.x % hkv;
   const int G = hq / hkv;
   const int64_t row0 = off[t] - r0;
   const int L = (int)(off[t + 1] - off[t]);
-  const int c = threadIdx.x % hd, rg = threadIdx.x / hd, nrg = blockDim.x / hd;
+  const int chunks = hd / VN;                  // threads per item
+  const int lanes = blockDim.x / chunks;       // items in flight per iteration
+  const int ch = threadIdx.x % chunks, il = threadIdx.x / chunks;
   const int64_t items = (int64_t)L * G;
-  float sum = 0.f;
-  for (int64_t it = rg; it < items; it += nrg) {
-    int64_t j = it / G, hh = it % G;
-    sum += to_f(q[(row0 + j) * hq * hd + (int64_t)(g * G + hh) * hd + c]);
+  const act_t* base = q + row0 * hq * hd + (int64_t)g * G * hd + ch * VN;
+  float shift[VN], a1[VN], a2[VN], v[VN];
+  Vec<act_t>::load(base, shift);               // the group's first query vector
+#pragma unroll
+  for (int e = 0; e < VN; ++e) a1[e] = a2[e] = 0.f;
+  for (int64_t it = il; it < items; it += lanes) {
+    const int64_t j = it / G, hh = it % G;
+    Vec<act_t>::load(base + j * hq * hd + hh * hd, v);
+#pragma unroll
+    for (int e = 0; e < VN; ++e) {
+      const float dv = v[e] - shift[e];
+      a1[e] += dv;
+      a2[e] = fmaf(dv, dv, a2[e]);
+    }
   }
-  red[threadIdx.x] = sum;
-  __syncthreads();
-  float m = 0.f;
-  for (int k = 0; k < nrg; ++k) m += red[k * hd + c];
-  m /= (float)items;
-  __syncthreads();
-  float dev = 0.f;
-  for (int64_t it = rg; it < items; it += nrg) {
-    int64_t j = it / G, hh = it % G;
-    float v = to_f(q[(row0 + j) * hq * hd + (int64_t)(g * G + hh) * hd + c]) - m;
-    dev += v * v;
+#pragma unroll
+  for (int e = 0; e < VN; ++e) {
+    red[0][threadIdx.x][e] = a1[e];
+    red[1][threadIdx.x][e] = a2[e];
   }
-  red[threadIdx.x] = dev;
   __syncthreads();
-  if (rg == 0) {
-    float v = 0.f;
-    for (int k = 0; k < nrg; ++k) v += red[k * hd + c];
-    int64_t o = ((int64_t)(t - t0) * hkv + g) * hd + c;
-    mu[o] = m;
-    s2[o] = v / (float)items;
+  if (il == 0) {
+#pragma unroll
+    for (int e = 0; e < VN; ++e) {
+      float s1 = 0.f, sq = 0.f;
+      for (int k = 0; k < lanes; ++k) {
+        s1 += red[0][k * chunks + ch][e];
+        sq += red[1][k * chunks + ch][e];
+      }
+      const float m1 = s1 / (float)items;
+      const int64_t o = ((int64_t)(t - t0) * hkv + g) * hd + ch * VN + e;
+      mu[o] = shift[e] + m1;
+      s2[o] = fmaxf(sq / (float)items - m1 * m1, 0.f);
+    }
   }
 }
 

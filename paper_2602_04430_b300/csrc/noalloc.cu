@@ -217,8 +217,11 @@ extern "C" int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operato
     a.kv_dtype = kv->kv_dtype;
     {
       Count L(ctx);
+      int rc = ST_OK;
       if (c.dtype == ST_F32) attn_simt<float, float>(a, s);
-      else attn_mma_eval(a, s);
+      else if (a.kv_dtype == ST_E4M3) attn_mma_eval(a, s);
+      else rc = attn_tc_eval(a, ctx->dstatus, s);
+      if (rc != ST_OK) return na_fail(ctx, rc, "tcgen05 attention: unsupported shape or tensor-map encoding failed");
     }
     NA_RC(launched(ctx));
     EpiParams eo;
