@@ -834,22 +834,49 @@ extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
       a.P = P;
       a.kv_dtype = kv->kv_dtype;
       RC(attention(ctx, a, nullptr, 0, s));
+      // In the last layer only each tuple's last prompt row feeds the label head:
+      // the output projection, the FFN and their norms run on those nc rows
+      // (rows i*P + P-1 of the stream), read in place through a row stride.
+      const bool last = (l == c.layers - 1) && P > 1;
+      const int Mr = last ? nc : M;
       EpiParams eo;
       eo.mode = EPI_RESID;
       eo.x = w.x;
       eo.ld = c.d;
-      RC(project(ctx, w.o, LW.wo, M, c.d, qd, eo, w.tmp, nullptr, s));
-      RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
+      const void* o_in = w.o;
+      if (last) {
+        eo.a_ld = (int64_t)P * qd;
+        eo.row_mul = P;
+        eo.row_add = P - 1;
+        o_in = (const char*)w.o + (size_t)(P - 1) * qd * ctx->esz;
+      }
+      RC(project(ctx, o_in, LW.wo, Mr, c.d, qd, eo, w.tmp, nullptr, s));
+      if (last) {
+        Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+        if (c.dtype == ST_BF16)
+          rmsnorm_rows<bf16>(w.x + (size_t)(P - 1) * c.d, nc, c.d, c.eps, (bf16*)w.xn, nullptr, s,
+                             (int64_t)P * c.d);
+        else
+          rmsnorm_rows<float>(w.x + (size_t)(P - 1) * c.d, nc, c.d, c.eps, (float*)w.xn, nullptr, s,
+                              (int64_t)P * c.d);
+        CKLAUNCH();
+      } else {
+        RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
+      }
       EpiParams eg;
       eg.mode = EPI_SWIGLU;
       eg.h = w.h;
       eg.ld = c.ffn;
-      RC(project(ctx, w.xn, LW.wgu, M, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
+      RC(project(ctx, w.xn, LW.wgu, Mr, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
       EpiParams ed;
       ed.mode = EPI_RESID;
       ed.x = w.x;
       ed.ld = c.d;
-      RC(project(ctx, w.h, LW.wd, M, c.d, c.ffn, ed, w.tmp, nullptr, s));
+      if (last) {
+        ed.row_mul = P;
+        ed.row_add = P - 1;
+      }
+      RC(project(ctx, w.h, LW.wd, Mr, c.d, c.ffn, ed, w.tmp, nullptr, s));
     }
     {
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);

@@ -44,7 +44,7 @@ __device__ __forceinline__ void epilogue_apply(const EpiParams& ep, int row, int
       store_act<act_t, W>(reinterpret_cast<act_t*>(ep.vbase) + g * ep.kv_sg + row * ep.kv_sr, v);
     }
   } else if (ep.mode == EPI_RESID) {
-    float* x = ep.x + (int64_t)row * ep.ld + col0;
+    float* x = ep.x + ((int64_t)row * ep.row_mul + ep.row_add) * ep.ld + col0;
 #pragma unroll
     for (int j = 0; j < W; j += 4) {
       float4 o = *reinterpret_cast<float4*>(x + j);

@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(128) k_gemm_simt(const act_t* __restrict__ A,
   __shared__ float Bs[BK][BN + 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int64_t lda = ep.a_ld > 0 ? ep.a_ld : K;
   float acc[W];
 #pragma unroll
   for (int j = 0; j < W; ++j) acc[j] = 0.f;
@@ -23,7 +24,7 @@ __global__ void __launch_bounds__(128) k_gemm_simt(const act_t* __restrict__ A,
     for (int e = threadIdx.x; e < BM * BK; e += 128) {
       int r = e / BK, k = e % BK;
       int gr = m0 + r;
-      As[k][r] = gr < M ? to_f(A[(int64_t)gr * K + k0 + k]) : 0.f;
+      As[k][r] = gr < M ? to_f(A[(int64_t)gr * lda + k0 + k]) : 0.f;
     }
     for (int e = threadIdx.x; e < BN * BK; e += 128) {
       int n = e / BK, k = e % BK;

@@ -210,11 +210,12 @@ int num_sms() {
   return n;
 }
 
-bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_outer,
+              uint64_t row_stride = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {inner * 2};
+  cuuint64_t strides[1] = {(row_stride ? row_stride : inner) * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, box_outer};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
@@ -233,7 +234,8 @@ int gemm_tc(const bf16* A, const bf16* W, int M, int N, int K, const EpiParams& 
   if (M <= 0) return ST_OK;
   if (!gemm_tc_supported(M, N, K)) return ST_EUNSUPPORTED;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, BM) || !make_map(&mb, W, (uint64_t)K, (uint64_t)N, BN))
+  if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, BM, (uint64_t)ep.a_ld) ||
+      !make_map(&mb, W, (uint64_t)K, (uint64_t)N, BN))
     return ST_ECUDA;
   static bool attr = false;
   if (!attr) {

@@ -11,6 +11,8 @@ enum EpiMode { EPI_QKV = 0, EPI_RESID = 1, EPI_SWIGLU = 2, EPI_STORE_F32 = 3 };
 struct EpiParams {
   int mode = EPI_STORE_F32;
   int M = 0, N = 0;
+  int64_t a_ld = 0;               // row stride of A in elements (0: K)
+  int64_t row_mul = 1, row_add = 0;   // EPI_RESID writes stream row (row*row_mul + row_add)
   // EPI_QKV: columns [0, hq*hd) are queries, then hkv*hd keys, then hkv*hd values.
   void* q = nullptr;              // act [M][hq*hd]
   void* kbase = nullptr;          // key of (row, kv head g, dim c) at kbase + g*kv_sg + row*kv_sr + c
@@ -46,7 +48,7 @@ void embed_prompt(const int32_t* prompt, int P, int64_t rows, const void* E, int
                   float* x, cudaStream_t s);
 template <typename act_t>
 void rmsnorm_rows(const float* x, int64_t rows, int d, float eps, act_t* xn, float* inv_rms,
-                  cudaStream_t s);
+                  cudaStream_t s, int64_t x_ld = 0);
 void build_rowinfo(const int64_t* off, int t0, int t1, int64_t r0, int64_t rows, int32_t* rowtup,
                    int32_t* pos, cudaStream_t s);
 void eval_rowinfo(const int32_t* tuple_ids, int n, int P, const int64_t* off, double r,

@@ -160,11 +160,11 @@ __device__ __forceinline__ void store4(bf16* p, float4 v) {
 // One warp per row; x float32 [rows][d] -> xn = x / sqrt(mean(x^2) + eps) (act type).
 template <typename act_t>
 __global__ void k_rmsnorm(const float* __restrict__ x, int64_t rows, int d, float eps,
-                          act_t* __restrict__ xn, float* __restrict__ inv_rms) {
+                          act_t* __restrict__ xn, float* __restrict__ inv_rms, int64_t x_ld) {
   int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  const float* xr = x + row * d;
+  const float* xr = x + row * x_ld;
   float ss = 0.f;
   for (int c = lane * 4; c < d; c += 128) {
     float4 v = *reinterpret_cast<const float4*>(xr + c);
@@ -183,12 +183,15 @@ __global__ void k_rmsnorm(const float* __restrict__ x, int64_t rows, int d, floa
 
 template <typename act_t>
 void rmsnorm_rows(const float* x, int64_t rows, int d, float eps, act_t* xn, float* inv_rms,
-                  cudaStream_t s) {
+                  cudaStream_t s, int64_t x_ld) {
   if (rows <= 0) return;
-  k_rmsnorm<act_t><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(x, rows, d, eps, xn, inv_rms);
+  k_rmsnorm<act_t><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(x, rows, d, eps, xn, inv_rms,
+                                                              x_ld > 0 ? x_ld : d);
 }
-template void rmsnorm_rows<float>(const float*, int64_t, int, float, float*, float*, cudaStream_t);
-template void rmsnorm_rows<bf16>(const float*, int64_t, int, float, bf16*, float*, cudaStream_t);
+template void rmsnorm_rows<float>(const float*, int64_t, int, float, float*, float*, cudaStream_t,
+                                  int64_t);
+template void rmsnorm_rows<bf16>(const float*, int64_t, int, float, bf16*, float*, cudaStream_t,
+                                 int64_t);
 
 // ------------------------------------------------------------------ EA-lite statistics
 // Block per (tuple, kv head): mean and population variance over (document
