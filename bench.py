@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the per-r op_eval sweep")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-proxy", action="store_true", help="skip the proxy+FP8 cascade arm")
+    ap.add_argument("--proxy-train-tables", type=int, default=8)
+    ap.add_argument("--proxy-epochs", type=int, default=12)
     return ap.parse_args()
 
 
@@ -184,6 +187,106 @@ def attention_bytes(cfg, lengths, r, kv_esz):
     return kv + scales
 
 
+def proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch):
+    """The learned proxy + FP8 KV cascade against the plain BF16 operator.
+
+    Training data: fresh tables with the bench table's lengths (different token
+    ids), each prefilled and evaluated by the full FP8-KV operator; labels are
+    its decisions at the calibrated threshold (median margin).  Held out: the
+    bench table.  Timed (CUDA events, KV resident): plain BF16 op_eval of every
+    tuple vs proxy eval + compaction + FP8 op_eval of the unsure tuples + merge.
+    """
+    T = len(table["lengths"])
+    r = args.r
+    op = synth.make_prompt(32, cfg.vocab, seed=77, label_ids=(1, 0), r=r)
+    opr = model.operator(op)
+    ids = torch.arange(T, dtype=torch.int32, device="cuda")
+    logits = torch.empty((T, 2), dtype=torch.float32, device="cuda")
+    labels = torch.empty((T,), dtype=torch.int32, device="cuda")
+    xs, ms = [], []
+    for c in range(args.proxy_train_tables):
+        tb = synth.make_table_from_lengths(table["lengths"], cfg.vocab, seed=5000 + c, ids="zipf")
+        kv.build(torch.from_numpy(tb["tokens"]).cuda())
+        kv.retain(r, stretto.ST_E4M3)
+        opr.eval(kv, ids, logits, labels)
+        xs.append(kv.read(stretto.ST_VIEW_POOLED, torch.float32, (T, cfg.d)))
+        ms.append(logits[:, 0] - logits[:, 1])
+    x_tr = torch.cat(xs)
+    m_tr = torch.cat(ms)
+    theta = float(m_tr.median().item())          # calibrated threshold (balanced labels)
+    y_tr = (m_tr > theta).to(torch.int32)
+    n_tr = int(x_tr.shape[0])
+    px = stretto.Proxy(model, synth.make_proxy_weights(cfg.d, 512, 128, seed=777))
+    batches = synth.minibatches(n_tr, 512, args.proxy_epochs, seed=778)
+    bt = torch.from_numpy(np.stack(batches)).cuda()
+    t0 = time.perf_counter()
+    for i in range(len(batches)):
+        px.train_step(x_tr, y_tr, bt[i], lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # held-out: the bench table
+    opf = model.operator(synth.make_prompt(32, cfg.vocab, seed=77, label_ids=(1, 0), r=r,
+                                           theta_pos=theta, theta_neg=theta))
+    kv.build(torch.from_numpy(table["tokens"]).cuda())
+    x_ho = kv.read(stretto.ST_VIEW_POOLED, torch.float32, (T, cfg.d))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+
+    kv.retain(r, stretto.ST_BF16)
+    lab_plain = torch.empty(T, dtype=torch.int32, device="cuda")
+    ms_plain = timed(lambda: opf.eval(kv, ids, logits, lab_plain))
+    lab_plain_h = lab_plain.cpu().numpy()
+    kv.retain(r, stretto.ST_E4M3)
+    lab_fp8 = torch.empty(T, dtype=torch.int32, device="cuda")
+    ms_fp8 = timed(lambda: opf.eval(kv, ids, logits, lab_fp8))
+    agree_fp8 = float((lab_fp8.cpu().numpy() == lab_plain_h).mean())
+    conf, plab = px.eval(x_ho)
+    acc_proxy = float((plab.cpu().numpy() == lab_plain_h).mean())
+    conf_h = conf.cpu().numpy()
+    pos = torch.empty(T, dtype=torch.int32, device="cuda")
+    tid = torch.empty(T, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cnt2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    full_lab = torch.empty(T, dtype=torch.int32, device="cuda")
+    final = torch.empty(T, dtype=torch.int32, device="cuda")
+    sweep = []
+    for frac in (0.05, 0.1, 0.2, 0.3, 0.4, 0.5, 0.7, 1.0):
+        tau = float(np.quantile(conf_h, frac)) if frac < 1.0 else 2.0
+
+        def cascade():
+            px.eval(x_ho, conf=conf, label=plab)
+            stretto.cascade_compact(model, conf, tau, out=pos, count=cnt)
+            stretto.cascade_compact(model, conf, tau, ids=ids, out=tid, count=cnt2)
+            k = int(cnt.item())
+            if k:
+                opf.eval(kv, tid[:k], logits[:k], full_lab[:k])
+            stretto.cascade_merge(model, plab, pos, cnt, full_lab, out=final)
+
+        ms_c = timed(cascade)
+        agree = float((final.cpu().numpy() == lab_plain_h).mean())
+        sweep.append({"fallback": float(int(cnt.item()) / T), "tau": tau, "agreement": agree,
+                      "tuples_per_s": T / (ms_c / 1000.0)})
+    ok = [s_ for s_ in sweep if s_["agreement"] >= 0.99]
+    best = max(ok, key=lambda s_: s_["tuples_per_s"]) if ok else None
+    return {"plain_bf16_tuples_per_s": T / (ms_plain / 1000.0),
+            "fp8_only_tuples_per_s": T / (ms_fp8 / 1000.0), "fp8_only_agreement": agree_fp8,
+            "proxy_holdout_accuracy": acc_proxy, "train_tuples": n_tr,
+            "train_steps": len(batches), "train_seconds": train_s, "theta": theta, "r": r,
+            "best_at_99": best,
+            "gain_at_99": (best["tuples_per_s"] / (T / (ms_plain / 1000.0))) if best else None,
+            "sweep": sweep}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -300,6 +403,11 @@ def main():
                            "gemm_ms": gg["ms"] / reps,
                            "gemm_TFLOPs": gg["flops"] / (gg["ms"] / 1000.0) / 1e12 if gg["ms"] else 0}
         kv.retain(op.r, kvd)
+    proxy = None
+    if not args.no_proxy and rank == 0:
+        proxy = proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch)
+        kv.build(tok)
+        kv.retain(op.r, kvd)
     e2e = None
     if not args.no_e2e:
         tok_h = torch.from_numpy(table["tokens"]).pin_memory()
@@ -332,7 +440,7 @@ def main():
                 "config": config_dict(args, cfg, table, op), "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                 "per_family_ms": {k: v["ms"] for k, v in prof.items()},
-                "op_eval": out}
+                "op_eval": out, "proxy_fp8": proxy}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -246,6 +246,49 @@ int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,
                 const int32_t* tokens_host, float* logits_host, int32_t* labels_host,
                 void* stream);
 
+/* ---- learned proxy and two-stage cascade ----
+ *
+ * A cheap first stage in front of the operator (the cascade of Sec. 4.1: a
+ * stage accepts or rejects a tuple, or marks it unsure and passes it on to the
+ * next, more expensive stage).  The proxy is an MLP
+ *   Linear(d_in, h1) - GELU(erf) - Linear(h1, h2) - GELU - Linear(h2, 2)
+ * over each tuple's pooled last-layer document state (ST_VIEW_POOLED of
+ * st_kv_build), trained with softmax cross-entropy and Adam (beta 0.9 / 0.999,
+ * eps 1e-8, bias-corrected) against the full operator's labels (0 reject,
+ * 1 accept).  float32 parameters, activations and accumulation. */
+typedef struct st_proxy st_proxy;
+#define ST_PROXY_PARAMS 0   /* w1 [h1][d_in], b1 [h1], w2 [h2][h1], b2 [h2], w3 [2][h2], b3 [2] */
+#define ST_PROXY_GRADS 1    /* the same layout: gradients of the last train step */
+#define ST_PROXY_ADAM_M 2
+#define ST_PROXY_ADAM_V 3
+/* init_host: 6 HOST float32 arrays in the ST_PROXY_PARAMS order (copied). */
+int st_proxy_create(st_ctx* ctx, int32_t d_in, int32_t h1, int32_t h2,
+                    const float* const* init_host, st_proxy** out);
+void st_proxy_free(st_proxy* p);
+/* One Adam step on the mini-batch x_dev[batch_dev[b]] (DEVICE float32 [n][d_in]
+ * rows, int32 labels y_dev indexed like x); loss_dev (DEVICE float32 [1], or
+ * NULL) receives the batch's mean cross-entropy. */
+int st_proxy_train_step(st_ctx* ctx, st_proxy* p, const float* x_dev, const int32_t* y_dev,
+                        const int32_t* batch_dev, int32_t B, float lr, float* loss_dev,
+                        void* stream);
+/* Proxy decision for rows x_dev[rows_dev[i]] (rows_dev NULL: rows 0..n-1):
+ * conf_dev (float32 [n]) = max softmax probability, label_dev (int32 [n]) =
+ * argmax (ties to 0). */
+int st_proxy_eval(st_ctx* ctx, st_proxy* p, const float* x_dev, const int32_t* rows_dev, int32_t n,
+                  float* conf_dev, int32_t* label_dev, void* stream);
+/* Cascade routing: the positions i (or ids_dev[i] when ids_dev is not NULL)
+ * with conf_dev[i] < tau, in increasing order, into unsure_dev; their number
+ * into count_dev (DEVICE int32 [1]).  One block; n <= 2^31-1. */
+int st_cascade_compact(st_ctx* ctx, const float* conf_dev, const int32_t* ids_dev, int32_t n,
+                       float tau, int32_t* unsure_dev, int32_t* count_dev, void* stream);
+/* Cascade merge: out_dev[i] = proxy_label_dev[i], then
+ * out_dev[unsure_pos_dev[j]] = full_label_dev[j] for j < *count_dev. */
+int st_cascade_merge(st_ctx* ctx, const int32_t* proxy_label_dev, int32_t n,
+                     const int32_t* unsure_pos_dev, const int32_t* count_dev,
+                     const int32_t* full_label_dev, int32_t* out_dev, void* stream);
+/* Copy one of the ST_PROXY_* buffers (float32, ST_PROXY_PARAMS layout) to DEVICE memory. */
+int st_proxy_read(const st_proxy* p, int32_t which, void* dst_dev, size_t bytes, void* stream);
+
 /* ---- kernel self-test entry ---- */
 
 /* The projection GEMM of the context's precision with a plain store epilogue:

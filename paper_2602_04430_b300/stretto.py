@@ -25,6 +25,8 @@ ST_REJECT, ST_ACCEPT, ST_UNSURE = 0, 1, 2
 (ST_VIEW_K, ST_VIEW_V, ST_VIEW_SCORES, ST_VIEW_POOLED, ST_VIEW_RANK, ST_VIEW_KR, ST_VIEW_VR,
  ST_VIEW_SCALES, ST_VIEW_OFFP, ST_VIEW_NKEEP) = range(10)
 PROF_FAMILIES = ("gemm", "attention", "retain", "other")
+ST_PROXY_PARAMS, ST_PROXY_GRADS, ST_PROXY_ADAM_M, ST_PROXY_ADAM_V = range(4)
+PROXY_ORDER = ("w1", "b1", "w2", "b2", "w3", "b3")
 
 
 class StrettoError(RuntimeError):
@@ -80,6 +82,13 @@ def lib() -> ctypes.CDLL:
         "st_op_eval_noalloc": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
         "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
+        "st_proxy_create": (i32, [VP, i32, i32, i32, ctypes.POINTER(VP), ctypes.POINTER(VP)]),
+        "st_proxy_free": (None, [VP]),
+        "st_proxy_train_step": (i32, [VP, VP, VP, VP, VP, i32, ctypes.c_float, VP, VP]),
+        "st_proxy_eval": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
+        "st_cascade_compact": (i32, [VP, VP, VP, i32, ctypes.c_float, VP, VP, VP]),
+        "st_cascade_merge": (i32, [VP, VP, i32, VP, VP, VP, VP, VP]),
+        "st_proxy_read": (i32, [VP, i32, VP, sz, VP]),
         "st_prof_enable": (i32, [VP, i32]),
         "st_prof_read": (i32, [VP, ctypes.POINTER(dbl)]),
         "st_prof_reset": (i32, [VP]),
@@ -292,6 +301,80 @@ class Operator:
         self.model.check(self.L.st_run_host(self.model.h, kv.h, self.h, int(kv_dtype),
                                             _ptr(tokens_host), _ptr(logits_host),
                                             _ptr(labels_host), _stream(stream)))
+
+
+class Proxy:
+    """The learned proxy MLP (an ``st_proxy``) and the cascade routing kernels."""
+
+    def __init__(self, model: Model, params: Dict[str, np.ndarray]):
+        self.model = model
+        self.L = model.L
+        self.h1, self.d = params["w1"].shape
+        self.h2 = params["w2"].shape[0]
+        self._init = [np.ascontiguousarray(params[k], dtype=np.float32) for k in PROXY_ORDER]
+        arr = (VP * 6)(*[a.ctypes.data for a in self._init])
+        h = VP()
+        model.check(self.L.st_proxy_create(model.h, self.d, self.h1, self.h2, arr, ctypes.byref(h)))
+        self.h = h
+        self.sizes = [a.size for a in self._init]
+        self.shapes = [a.shape for a in self._init]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.st_proxy_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train_step(self, x, y, batch, lr: float, loss=None, stream=None):
+        self.model.check(self.L.st_proxy_train_step(
+            self.model.h, self.h, _ptr(x), _ptr(y), _ptr(batch), int(batch.numel()),
+            float(lr), _ptr(loss) if loss is not None else None, _stream(stream)))
+
+    def eval(self, x, rows=None, n=None, conf=None, label=None, stream=None):
+        import torch
+        n = int(rows.numel()) if rows is not None else (int(x.shape[0]) if n is None else n)
+        conf = torch.empty(n, dtype=torch.float32, device="cuda") if conf is None else conf
+        label = torch.empty(n, dtype=torch.int32, device="cuda") if label is None else label
+        self.model.check(self.L.st_proxy_eval(self.model.h, self.h, _ptr(x),
+                                              _ptr(rows) if rows is not None else None, n,
+                                              _ptr(conf), _ptr(label), _stream(stream)))
+        return conf, label
+
+    def read(self, which: int) -> Dict[str, np.ndarray]:
+        import torch
+        out = torch.empty(sum(self.sizes), dtype=torch.float32, device="cuda")
+        self.model.check(self.L.st_proxy_read(self.h, which, _ptr(out), out.numel() * 4,
+                                              _stream()))
+        flat = out.cpu().numpy()
+        res, o = {}, 0
+        for k, sz, shp in zip(PROXY_ORDER, self.sizes, self.shapes):
+            res[k] = flat[o:o + sz].reshape(shp)
+            o += sz
+        return res
+
+
+def cascade_compact(model: Model, conf, tau: float, ids=None, out=None, count=None, stream=None):
+    import torch
+    n = int(conf.numel())
+    out = torch.empty(max(n, 1), dtype=torch.int32, device="cuda") if out is None else out
+    count = torch.zeros(1, dtype=torch.int32, device="cuda") if count is None else count
+    model.check(model.L.st_cascade_compact(model.h, _ptr(conf), _ptr(ids) if ids is not None else None,
+                                           n, float(tau), _ptr(out), _ptr(count), _stream(stream)))
+    return out, count
+
+
+def cascade_merge(model: Model, proxy_label, unsure_pos, count, full_label, out=None, stream=None):
+    import torch
+    n = int(proxy_label.numel())
+    out = torch.empty(n, dtype=torch.int32, device="cuda") if out is None else out
+    model.check(model.L.st_cascade_merge(model.h, _ptr(proxy_label), n, _ptr(unsure_pos),
+                                         _ptr(count), _ptr(full_label), _ptr(out), _stream(stream)))
+    return out
 
 
 def version() -> str:

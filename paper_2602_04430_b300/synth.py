@@ -143,6 +143,27 @@ def make_weights(cfg: ModelConfig, seed: int = 1234, std: float = 0.02) -> Dict[
     return out
 
 
+def make_proxy_weights(d_in: int, h1: int = 512, h2: int = 128, seed: int = 777) -> Dict[str, np.ndarray]:
+    """Initial parameters of the proxy MLP: W ~ N(0, 1/fan_in), b = 0 (float32)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for name, (o, i) in (("1", (h1, d_in)), ("2", (h2, h1)), ("3", (2, h2))):
+        out["w" + name] = (rng.standard_normal((o, i), dtype=np.float32) / np.float32(np.sqrt(i)))
+        out["b" + name] = np.zeros(o, dtype=np.float32)
+    return out
+
+
+def minibatches(n: int, batch: int, epochs: int, seed: int = 778):
+    """Shuffled mini-batch index arrays (the proxy's training order is an input)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(epochs):
+        perm = rng.permutation(n).astype(np.int32)
+        for i in range(0, n - batch + 1, batch):
+            out.append(perm[i:i + batch])
+    return out
+
+
 def lognormal_lengths(rng: np.random.Generator, n: int, median: float, sigma: float,
                       lo: int, hi: int) -> np.ndarray:
     x = rng.lognormal(mean=math.log(median), sigma=sigma, size=n)
