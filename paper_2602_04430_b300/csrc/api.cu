@@ -238,8 +238,6 @@ int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_item
     attn_simt<float, float>(a, s);
   } else if (a.mode == 0) {
     rc = attn_tc_prefill(a, items, n_items, ctx->dstatus, s);
-  } else if (a.kv_dtype == ST_E4M3) {
-    attn_mma_eval(a, s);
   } else {
     rc = attn_tc_eval(a, ctx->dstatus, s);
   }
@@ -464,6 +462,7 @@ extern "C" int st_kv_alloc(st_ctx* ctx, const int64_t* offsets_host, int32_t T, 
   // (into unused capacity) then read finite values, which the masks discard
   cudaMemset(kv->Kr, 0, LH * rp * c.hd * e);
   cudaMemset(kv->Vr, 0, LH * rp * c.hd * e);
+  cudaMemset(kv->scales, 0, LH * (rp / 64) * 2 * sizeof(float));
   err = cudaDeviceSynchronize();
   if (err != cudaSuccess) {
     st_kv_free(kv);
@@ -812,6 +811,7 @@ extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
       ep.hq = c.hq;
       ep.hkv = c.hkv;
       ep.hd = c.hd;
+      ep.qkv_f16 = kv->kv_dtype == ST_E4M3 ? 1 : 0;
       RC(project(ctx, w.xn, LW.wqkv, M, nqkv, c.d, ep, w.tmp, nullptr, s));
       AttnParams a;
       a.mode = 1;

@@ -11,7 +11,12 @@
 //               [key][dim] tile; the per-tile partial lands in TMEM (two
 //               64-column buffers) and is folded into the thread's registers with
 //               the online-softmax rescale.
-//   loads       one thread issues TMA for 128-key K and V tiles (two stages).
+//   loads       one thread issues TMA for 128-key K and V tiles (three stages);
+//               the MMA thread TMA-loads each next item's Q (3-D box).
+//   E4M3 KV     raw code tiles land in two raw stages; two warps widen them
+//               exactly to f16 into the swizzled K/V stage; Q and the prompt's
+//               K/V arrive in f16, both products run as f16 MMAs, the K block
+//               scale multiplies the f32 scores and the V block scale P.
 //
 // Modes: prefill (the document's own keys, causal) and eval (the tuple's
 // retained slots, all visible, then the prompt's keys, causal).
@@ -28,18 +33,22 @@ constexpr int HD = 64;
 constexpr int TK = 128;          // keys per tile
 constexpr int ROWS = 128;        // query rows per work item
 constexpr int NKV = 3;           // K/V stages
-constexpr int NT = 224;          // warps 0-3 softmax, 4 K/V loads, 5 MMA, 6 Q loads
+// warps 0-3 softmax, 4 K/V loads, 5 MMA issue + Q loads, (E4M3 KV) 6-7 widen codes to bf16
+constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
 constexpr int OFF_Q = 0;                           // 2 x 16 KB
 constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // NKV x 16 KB
 constexpr int OFF_V = OFF_K + NKV * TK * 128;      // NKV x 16 KB
 constexpr int OFF_P = OFF_V + NKV * TK * 128;      // 2 x 32 KB (two 64-key sub-tiles each)
-constexpr int OFF_BAR = OFF_P + 2 * ROWS * TK * 2;
-constexpr size_t SMEM = OFF_BAR + 256 + 1024;
+constexpr int OFF_RAW = OFF_P + 2 * ROWS * TK * 2; // (E4M3) 2 x (K + V codes, 8 KB each)
+constexpr int RAW_BYTES = 2 * TK * HD;
+constexpr int off_bar(bool fp8) { return OFF_RAW + (fp8 ? 2 * RAW_BYTES : 0); }
+constexpr size_t smem_bytes(bool fp8) { return (size_t)off_bar(fp8) + 256 + 1024; }
 constexpr uint32_t TMEM_COLS = 512;              // S: [0,256), PV: [256,384)
 
 struct Bars {
   uint64_t kv_full[NKV], kv_empty[NKV], s_full[2], s_free[2], p_full[2], pv_full[2], pv_free[2];
   uint64_t q_full[2], q_empty[2];
+  uint64_t kvc_full[NKV], raw_full[2], raw_empty[2];   // E4M3: widened stages, raw code stages
   uint32_t tmem;
 };
 
@@ -58,6 +67,10 @@ __device__ __forceinline__ float ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
+  __half2 v = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
 }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -136,11 +149,12 @@ struct Work {
 };
 
 // Persistent: CTA b processes work items b, b + gridDim.x, ...; the load, MMA
-// and softmax roles each walk the same sequence, connected by mbarrier rings
+// (which also loads each next item's Q) and softmax roles each walk the same
+// sequence, connected by mbarrier rings
 // (Q: 2 buffers, K/V: 3 stages, S and PV accumulators: 2 TMEM buffers each,
 // P: 2 shared-memory tiles), so the next item's loads overlap this item's math.
-template <int MODE>
-__global__ void __launch_bounds__(NT, 1)
+template <int MODE, bool FP8>
+__global__ void __launch_bounds__(nthreads(FP8), 1)
     k_attn_tc(AttnParams a, const int32_t* __restrict__ items, int n_work, int zb_count,
               const __grid_constant__ CUtensorMap tmQ,
               const __grid_constant__ CUtensorMap tmK, const __grid_constant__ CUtensorMap tmV,
@@ -149,7 +163,7 @@ __global__ void __launch_bounds__(NT, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  Bars* bars = reinterpret_cast<Bars*>(smem + OFF_BAR);
+  Bars* bars = reinterpret_cast<Bars*>(smem + off_bar(FP8));
   const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
   const uint32_t sK0 = ptx::smem_u32(smem + OFF_K), sV0 = ptx::smem_u32(smem + OFF_V);
   const uint32_t sP0 = ptx::smem_u32(smem + OFF_P);
@@ -159,6 +173,11 @@ __global__ void __launch_bounds__(NT, 1)
     for (int s = 0; s < NKV; ++s) {
       ptx::mbar_init(&bars->kv_full[s], 1);
       ptx::mbar_init(&bars->kv_empty[s], 1);
+      ptx::mbar_init(&bars->kvc_full[s], 64);
+    }
+    for (int s = 0; s < 2; ++s) {
+      ptx::mbar_init(&bars->raw_full[s], 1);
+      ptx::mbar_init(&bars->raw_empty[s], 64);
     }
     for (int s = 0; s < 2; ++s) {
       ptx::mbar_init(&bars->s_full[s], 1);
@@ -180,45 +199,41 @@ __global__ void __launch_bounds__(NT, 1)
   ptx::tc_fence_after();
   const uint32_t tmem = bars->tmem;
 
-  if (warp == 6) {
-    // ------------------------------------------------------------ TMA: Q, up to 2 items ahead
-    if (lane == 0) {
-      ptx::tma_prefetch_desc(&tmQ);
-      int last_q[2] = {-1, -1};
-      uint32_t qc = 0;
-      for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++qc) {
-        Work<MODE> W;
-        W.decode(a, items, w, zb_count);
-        const int qb = qc & 1;
-        if (!ptx::mbar_wait(&bars->q_empty[qb], ((qc >> 1) & 1) ^ 1)) {
-          atomicExch(status, ST_ETIMEOUT);
-          break;
-        }
-        ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
-        ptx::tma_load_3d(smem + OFF_Q + qb * ROWS * 128, &tmQ, &bars->q_full[qb], 0, W.g * W.G,
-                         (int)W.qrow0);
-        last_q[qb] = (int)((qc >> 1) & 1);
-      }
-      for (int s = 0; s < 2; ++s)
-        if (last_q[s] >= 0) ptx::mbar_wait(&bars->q_full[s], (uint32_t)last_q[s], 100000000LL);
-    }
-  } else if (warp == 4) {
+  if (warp == 4) {
     // ------------------------------------------------------------ TMA: K/V tiles
     if (lane == 0) {
       ptx::tma_prefetch_desc(&tmK);
       ptx::tma_prefetch_desc(&tmV);
       int last_kv[NKV];
-      for (int s = 0; s < NKV; ++s) last_kv[s] = -1;
+      uint32_t n_tma[NKV];      // TMA fills of each stage (its kv_full completions)
+      for (int s = 0; s < NKV; ++s) {
+        last_kv[s] = -1;
+        n_tma[s] = 0;
+      }
       bool ok = true;
-      uint32_t c = 0;   // tile counter of this CTA
+      uint32_t c = 0, dc = 0;   // tile counter / E4M3 document-tile counter of this CTA
+      int last_raw[2] = {-1, -1};
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
         Work<MODE> W;
         W.decode(a, items, w, zb_count);
         for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
           const int s = c % NKV;
           const uint32_t u = c / NKV;
-          if (!ptx::mbar_wait(&bars->kv_empty[s], (u & 1) ^ 1)) { ok = false; break; }
           const TileInfo T = W.tile(ti);
+          if (FP8 && !T.prompt) {
+            // raw codes into a raw stage; the widening warps fill K/V stage s
+            const int rs = dc & 1;
+            if (!ptx::mbar_wait(&bars->raw_empty[rs], ((dc >> 1) & 1) ^ 1)) { ok = false; break; }
+            ptx::mbar_arrive_expect_tx(&bars->raw_full[rs], RAW_BYTES);
+            uint8_t* dr = smem + OFF_RAW + rs * RAW_BYTES;
+            const int y = (int)(W.doc_row0 + T.key0);
+            ptx::tma_load_2d(dr, &tmK, &bars->raw_full[rs], 0, y);
+            ptx::tma_load_2d(dr + TK * HD, &tmV, &bars->raw_full[rs], 0, y);
+            last_raw[rs] = (int)((dc >> 1) & 1);
+            ++dc;
+            continue;
+          }
+          if (!ptx::mbar_wait(&bars->kv_empty[s], (u & 1) ^ 1)) { ok = false; break; }
           ptx::mbar_arrive_expect_tx(&bars->kv_full[s], 2 * TK * 128);
           uint8_t* dk = smem + OFF_K + s * TK * 128;
           uint8_t* dv = smem + OFF_V + s * TK * 128;
@@ -231,31 +246,61 @@ __global__ void __launch_bounds__(NT, 1)
             ptx::tma_load_2d(dk, &tmK, &bars->kv_full[s], 0, y);
             ptx::tma_load_2d(dv, &tmV, &bars->kv_full[s], 0, y);
           }
-          last_kv[s] = (int)(u & 1);
+          last_kv[s] = (int)(n_tma[s] & 1);
+          ++n_tma[s];
         }
       }
-      if (!ok) atomicExch(status, ST_ETIMEOUT);
+      // let every load this CTA issued land before it can exit
       for (int s = 0; s < NKV; ++s)
-        if (last_kv[s] >= 0) ptx::mbar_wait(&bars->kv_full[s], (uint32_t)last_kv[s], 100000000LL);
+        if (last_kv[s] >= 0 && !ptx::mbar_wait(&bars->kv_full[s], (uint32_t)last_kv[s], 100000000LL))
+          ok = false;
+      for (int s = 0; s < 2; ++s)
+        if (last_raw[s] >= 0 && !ptx::mbar_wait(&bars->raw_full[s], (uint32_t)last_raw[s], 100000000LL))
+          ok = false;
+      if (!ok) atomicExch(status, ST_ETIMEOUT);
     }
   } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      constexpr uint32_t idS = ptx::idesc_bf16_f32(ROWS, TK);
-      constexpr uint32_t idPV = ptx::idesc_bf16_f32(ROWS, HD) | (1u << 16);   // B MN-major
+      // E4M3 KV runs the products in f16 (codes widen exactly; scales act in f32)
+      constexpr uint32_t idS = FP8 ? ptx::idesc_f16_f32(ROWS, TK) : ptx::idesc_bf16_f32(ROWS, TK);
+      constexpr uint32_t idPV =
+          (FP8 ? ptx::idesc_f16_f32(ROWS, HD) : ptx::idesc_bf16_f32(ROWS, HD)) | (1u << 16);
       bool ok = true;
       uint32_t c = 0, qc = 0;
+      uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};
+      ptx::tma_prefetch_desc(&tmQ);
+      // Q of item qn into buffer qn & 1 once the item two back has released it
+      auto load_q = [&](int wq, uint32_t qn) -> bool {
+        Work<MODE> WQ;
+        WQ.decode(a, items, wq, zb_count);
+        const int qb = qn & 1;
+        if (!ptx::mbar_wait(&bars->q_empty[qb], ((qn >> 1) & 1) ^ 1)) return false;
+        ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
+        ptx::tma_load_3d(smem + OFF_Q + qb * ROWS * 128, &tmQ, &bars->q_full[qb], 0, WQ.g * WQ.G,
+                         (int)WQ.qrow0);
+        return true;
+      };
+      if (blockIdx.x < n_work) ok = load_q(blockIdx.x, 0);
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
         Work<MODE> W;
         W.decode(a, items, w, zb_count);
         const int qb = qc & 1;
         if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
+        if (w + (int)gridDim.x < n_work && !(ok = load_q(w + gridDim.x, qc + 1))) break;
         ptx::tc_fence_after();
         const uint32_t sQ = sQ0 + qb * ROWS * 128;
         const uint32_t base = c;
         auto issue_s = [&](uint32_t cc) -> bool {
           const int s = cc % NKV, b = cc & 1;
-          if (!ptx::mbar_wait(&bars->kv_full[s], (cc / NKV) & 1)) return false;
+          const int ti_local = (int)(cc - base);
+          const bool widened = FP8 && !W.tile(ti_local).prompt;
+          // each stage's two "full" barriers complete once per use of their kind
+          uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->kv_full[s];
+          uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
+          const uint32_t par = nuse & 1;
+          ++nuse;
+          if (!ptx::mbar_wait(fb, par)) return false;
           if (!ptx::mbar_wait(&bars->s_free[b], ((cc >> 1) & 1) ^ 1)) return false;
           ptx::tc_fence_after();
           const uint32_t kb = sK0 + s * TK * 128;
@@ -291,10 +336,71 @@ __global__ void __launch_bounds__(NT, 1)
       // every commit of this thread has landed once the last stages are released
       if (ok)
         for (uint32_t cc = c >= NKV ? c - NKV : 0; cc < c; ++cc)
-          ptx::mbar_wait(&bars->kv_empty[cc % NKV], (cc / NKV) & 1, 100000000LL);
+          if (!ptx::mbar_wait(&bars->kv_empty[cc % NKV], (cc / NKV) & 1, 100000000LL))
+            atomicExch(status, ST_ETIMEOUT);
     }
     __syncwarp();
-  } else {
+  } else if (FP8 && warp >= 6) {
+    // ------------------------------------------------------------ widen E4M3 -> bf16
+    // 64 threads; thread tc widens rows tc and tc + 64 of the K and V code tiles
+    // (value * block scale, rounded to bf16) into the swizzled MMA stage.
+    const int tc = threadIdx.x - 192;
+    bool ok = true;
+    uint32_t c = 0, dc = 0;
+    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+      Work<MODE> W;
+      W.decode(a, items, w, zb_count);
+      for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
+        const TileInfo T = W.tile(ti);
+        if (T.prompt) continue;
+        const int s = c % NKV, rs = dc & 1;
+        if (!ptx::mbar_wait(&bars->raw_full[rs], (dc >> 1) & 1)) { ok = false; break; }
+        if (!ptx::mbar_wait(&bars->kv_empty[s], ((c / NKV) & 1) ^ 1)) { ok = false; break; }
+        const uint8_t* raw = smem + OFF_RAW + rs * RAW_BYTES;
+#pragma unroll
+        for (int kv = 0; kv < 2; ++kv) {
+          uint8_t* dst = smem + (kv == 0 ? OFF_K : OFF_V) + s * TK * 128;
+#pragma unroll
+          for (int hrow = 0; hrow < 2; ++hrow) {
+            const int row = tc + hrow * 64;
+            if (row >= T.count) {
+              // past the tuple's retained slots: exact zeros (their block, and
+              // its scale, may not exist)
+#pragma unroll
+              for (int ch = 0; ch < 8; ++ch)
+                *reinterpret_cast<uint4*>(dst + swz(row, ch)) = make_uint4(0, 0, 0, 0);
+              continue;
+            }
+            const uint4* src = reinterpret_cast<const uint4*>(raw + kv * TK * HD + row * HD);
+#pragma unroll
+            for (int q16 = 0; q16 < 4; ++q16) {
+              const uint4 cw = src[q16];
+              const uint32_t words[4] = {cw.x, cw.y, cw.z, cw.w};
+              uint32_t out[8];
+#pragma unroll
+              for (int wd = 0; wd < 4; ++wd) {
+#pragma unroll
+                for (int hw = 0; hw < 2; ++hw) {
+                  const uint16_t pair = (uint16_t)(words[wd] >> (16 * hw));
+                  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(out[2 * wd + hw]) : "h"(pair));
+                }
+              }
+              // 16 codes -> 32 bytes of f16 = chunks 2*q16, 2*q16+1 of the row
+              *reinterpret_cast<uint4*>(dst + swz(row, 2 * q16)) =
+                  make_uint4(out[0], out[1], out[2], out[3]);
+              *reinterpret_cast<uint4*>(dst + swz(row, 2 * q16 + 1)) =
+                  make_uint4(out[4], out[5], out[6], out[7]);
+            }
+          }
+        }
+        fence_proxy_async();
+        ptx::mbar_arrive(&bars->raw_empty[rs]);
+        ptx::mbar_arrive(&bars->kvc_full[s]);
+        ++dc;
+      }
+    }
+    if (!ok) atomicExch(status, ST_ETIMEOUT);
+  } else if (warp < 4) {
     // ------------------------------------------------------------ softmax warps
     const int r = threadIdx.x;                 // query row == TMEM lane
     const float sl2 = a.scale * 1.4426950408889634f;
@@ -358,9 +464,21 @@ __global__ void __launch_bounds__(NT, 1)
           for (int k = 0; k < TK; ++k)
             if (k >= nvis) v[k] = 0xFF800000u;
         }
+        // E4M3 document tiles: one K and one V scale per 64-slot half of the tile
+        float ks[2] = {1.f, 1.f}, vs[2] = {1.f, 1.f};
+        if (FP8 && !T.prompt) {
+          const float* scp = a.scales + ((W.doc_row0 + T.key0) >> 6) * 2;
+          ks[0] = scp[0];
+          vs[0] = scp[1];
+          if (T.count > 64) {
+            ks[1] = scp[2];
+            vs[1] = scp[3];
+          }
+        }
         float mx4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
-        for (int k = 0; k < TK; ++k) mx4[k & 3] = fmaxf(mx4[k & 3], __uint_as_float(v[k]));
+        for (int k = 0; k < TK; ++k)
+          mx4[k & 3] = fmaxf(mx4[k & 3], __uint_as_float(v[k]) * ks[k >> 6]);
         const float mx = fmaxf(fmaxf(mx4[0], mx4[1]), fmaxf(mx4[2], mx4[3])) * sl2;
         const float mn = fmaxf(m, mx);
         const float base = mn == -INFINITY ? 0.f : mn;
@@ -371,12 +489,13 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int k8 = 0; k8 < TK; k8 += 8) {
           uint32_t pk[4];
+          const float mul = sl2 * ks[k8 >> 6], vsc = vs[k8 >> 6];
 #pragma unroll
           for (int e = 0; e < 8; e += 2) {
-            const float p0 = ex2(fmaf(__uint_as_float(v[k8 + e]), sl2, -base));
-            const float p1 = ex2(fmaf(__uint_as_float(v[k8 + e + 1]), sl2, -base));
+            const float p0 = ex2(fmaf(__uint_as_float(v[k8 + e]), mul, -base));
+            const float p1 = ex2(fmaf(__uint_as_float(v[k8 + e + 1]), mul, -base));
             rs4[e >> 1] += p0 + p1;
-            pk[e >> 1] = pack_bf16(p0, p1);
+            pk[e >> 1] = FP8 ? pack_f16(p0 * vsc, p1 * vsc) : pack_bf16(p0, p1);
           }
           *reinterpret_cast<uint4*>(prow + (k8 >> 6) * (ROWS * 128) + swz(r, (k8 & 63) >> 3)) =
               make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -416,7 +535,8 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
-bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_outer,
+           CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -431,12 +551,13 @@ bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uin
   cuuint64_t strides[1] = {inner * 2};
   cuuint32_t box[2] = {(cuuint32_t)HD, box_outer};
   cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool map_q(CUtensorMap* m, const void* q, int hq, uint64_t rows, int G) {
+bool map_q(CUtensorMap* m, const void* q, int hq, uint64_t rows, int G,
+           CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -453,7 +574,7 @@ bool map_q(CUtensorMap* m, const void* q, int hq, uint64_t rows, int G) {
   cuuint64_t strides[2] = {(cuuint64_t)HD * 2, (cuuint64_t)hq * HD * 2};
   cuuint32_t box[3] = {(cuuint32_t)HD, (cuuint32_t)G, (cuuint32_t)(ROWS / G)};
   cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(q), dims, strides, box, es,
+  return fn(m, dt, 3, const_cast<void*>(q), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -468,11 +589,32 @@ int sm_count() {
   return n;
 }
 
-template <int MODE>
+bool map2d_u8(CUtensorMap* m, const void* base, uint64_t outer, uint32_t box_outer) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return false;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)HD, outer};
+  cuuint64_t strides[1] = {(cuuint64_t)HD};
+  cuuint32_t box[2] = {(cuuint32_t)HD, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE, bool FP8>
 void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_attn_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaFuncSetAttribute(k_attn_tc<MODE, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_bytes(FP8));
     done = true;
   }
 }
@@ -486,20 +628,32 @@ bool attn_tc_supported(int hq, int hkv, int hd) {
 
 int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   if (a.n <= 0) return ST_OK;
-  if (!attn_tc_supported(a.hq, a.hkv, a.hd) || a.kv_dtype != ST_BF16) return ST_EUNSUPPORTED;
+  if (!attn_tc_supported(a.hq, a.hkv, a.hd) || (a.kv_dtype != ST_BF16 && a.kv_dtype != ST_E4M3))
+    return ST_EUNSUPPORTED;
+  const bool fp8 = a.kv_dtype == ST_E4M3;
   const int G = a.hq / a.hkv;
   CUtensorMap mq, mk, mv, mkp, mvp;
   const uint64_t planes = (uint64_t)a.hkv * a.Rp_cap;
   const uint64_t prow = (uint64_t)a.n * a.P;
-  if (!map_q(&mq, a.q, a.hq, prow, G) || !map2d(&mk, a.Kr, HD, planes, TK) ||
-      !map2d(&mv, a.Vr, HD, planes, TK) || !map2d(&mkp, a.kp, (uint64_t)a.hkv * HD, prow, TK) ||
-      !map2d(&mvp, a.vp, (uint64_t)a.hkv * HD, prow, TK))
-    return ST_ECUDA;
-  set_smem_attr<1>();
+  const CUtensorMapDataType qt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  bool ok = map_q(&mq, a.q, a.hq, prow, G, qt) &&
+            map2d(&mkp, a.kp, (uint64_t)a.hkv * HD, prow, TK, qt) &&
+            map2d(&mvp, a.vp, (uint64_t)a.hkv * HD, prow, TK, qt);
+  if (fp8) ok = ok && map2d_u8(&mk, a.Kr, planes, TK) && map2d_u8(&mv, a.Vr, planes, TK);
+  else ok = ok && map2d(&mk, a.Kr, HD, planes, TK) && map2d(&mv, a.Vr, HD, planes, TK);
+  if (!ok) return ST_ECUDA;
   const int zb = (a.P * G + ROWS - 1) / ROWS;
   const int n_work = a.n * a.hkv * zb;
   const int grid = n_work < sm_count() ? n_work : sm_count();
-  k_attn_tc<1><<<grid, NT, SMEM, s>>>(a, nullptr, n_work, zb, mq, mk, mv, mkp, mvp, status);
+  if (fp8) {
+    set_smem_attr<1, true>();
+    k_attn_tc<1, true><<<grid, nthreads(true), smem_bytes(true), s>>>(a, nullptr, n_work, zb, mq, mk,
+                                                                      mv, mkp, mvp, status);
+  } else {
+    set_smem_attr<1, false>();
+    k_attn_tc<1, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, nullptr, n_work, zb, mq,
+                                                                         mk, mv, mkp, mvp, status);
+  }
   return ST_OK;
 }
 
@@ -513,10 +667,11 @@ int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int*
   if (!map_q(&mq, a.q, a.hq, (uint64_t)a.rows, G) || !map2d(&mk, a.K, HD, planes, TK) ||
       !map2d(&mv, a.V, HD, planes, TK))
     return ST_ECUDA;
-  set_smem_attr<0>();
+  set_smem_attr<0, false>();
   const int n_work = n_items * a.hkv;
   const int grid = n_work < sm_count() ? n_work : sm_count();
-  k_attn_tc<0><<<grid, NT, SMEM, s>>>(a, items, n_work, 1, mq, mk, mv, mk, mv, status);
+  k_attn_tc<0, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, items, n_work, 1, mq, mk,
+                                                                       mv, mk, mv, status);
   return ST_OK;
 }
 

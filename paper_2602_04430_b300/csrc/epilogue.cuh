@@ -17,6 +17,18 @@ __device__ __forceinline__ void store_act(act_t* dst, const float (&v)[W]) {
 }
 
 template <int W>
+__device__ __forceinline__ void store_half(__half* dst, const float (&v)[W]) {
+#pragma unroll
+  for (int j = 0; j < W; j += 8) {
+    uint4 u;
+    __half2* h = reinterpret_cast<__half2*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(v[j + 2 * i], v[j + 2 * i + 1]);
+    *reinterpret_cast<uint4*>(dst + j) = u;
+  }
+}
+
+template <int W>
 __device__ __forceinline__ void rope_inplace(float (&v)[W], const float2* __restrict__ tab) {
 #pragma unroll
   for (int i = 0; i < W / 2; ++i) {
@@ -34,15 +46,20 @@ __device__ __forceinline__ void epilogue_apply(const EpiParams& ep, int row, int
   if (ep.mode == EPI_QKV) {
     const int qcols = ep.hq * W, kcols = ep.hkv * W;
     if (col0 < qcols + kcols) rope_inplace<W>(v, ep.rope + (int64_t)ep.pos[row] * (W / 2));
+    int64_t off;
+    void* base;
     if (col0 < qcols) {
-      store_act<act_t, W>(reinterpret_cast<act_t*>(ep.q) + (int64_t)row * qcols + col0, v);
+      base = ep.q;
+      off = (int64_t)row * qcols + col0;
     } else if (col0 < qcols + kcols) {
-      int g = (col0 - qcols) / W;
-      store_act<act_t, W>(reinterpret_cast<act_t*>(ep.kbase) + g * ep.kv_sg + row * ep.kv_sr, v);
+      base = ep.kbase;
+      off = ((col0 - qcols) / W) * ep.kv_sg + row * ep.kv_sr;
     } else {
-      int g = (col0 - qcols - kcols) / W;
-      store_act<act_t, W>(reinterpret_cast<act_t*>(ep.vbase) + g * ep.kv_sg + row * ep.kv_sr, v);
+      base = ep.vbase;
+      off = ((col0 - qcols - kcols) / W) * ep.kv_sg + row * ep.kv_sr;
     }
+    if (ep.qkv_f16) store_half<W>(reinterpret_cast<__half*>(base) + off, v);
+    else store_act<act_t, W>(reinterpret_cast<act_t*>(base) + off, v);
   } else if (ep.mode == EPI_RESID) {
     float* x = ep.x + ((int64_t)row * ep.row_mul + ep.row_add) * ep.ld + col0;
 #pragma unroll

@@ -124,10 +124,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
       }
-      if (!ok) atomicExch(status, ST_ETIMEOUT);
       // let every load this CTA issued land before the CTA can exit
       for (int s = 0; s < STAGES; ++s)
-        if (last_par[s] >= 0) ptx::mbar_wait(&bars->full[s], (uint32_t)last_par[s], 100000000LL);
+        if (last_par[s] >= 0 && !ptx::mbar_wait(&bars->full[s], (uint32_t)last_par[s], 100000000LL))
+          ok = false;
+      if (!ok) atomicExch(status, ST_ETIMEOUT);
     }
   } else if (warp == 1) {
     if (lane == 0) {

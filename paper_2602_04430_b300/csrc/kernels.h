@@ -12,6 +12,7 @@ struct EpiParams {
   int mode = EPI_STORE_F32;
   int M = 0, N = 0;
   int64_t a_ld = 0;               // row stride of A in elements (0: K)
+  int qkv_f16 = 0;                // EPI_QKV: store q / k / v as IEEE half instead of the act type
   int64_t row_mul = 1, row_add = 0;   // EPI_RESID writes stream row (row*row_mul + row_add)
   // EPI_QKV: columns [0, hq*hd) are queries, then hkv*hd keys, then hkv*hd values.
   void* q = nullptr;              // act [M][hq*hd]

@@ -194,6 +194,7 @@ extern "C" int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operato
     ep.hq = c.hq;
     ep.hkv = c.hkv;
     ep.hd = c.hd;
+    ep.qkv_f16 = kv->kv_dtype == ST_E4M3 ? 1 : 0;
     NA_RC(gemm(ctx, w.xn, LW.wqkv, (int)M, nqkv, c.d, ep, w.tmp, nullptr, s));
     AttnParams a;
     a.mode = 1;
@@ -219,7 +220,6 @@ extern "C" int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operato
       Count L(ctx);
       int rc = ST_OK;
       if (c.dtype == ST_F32) attn_simt<float, float>(a, s);
-      else if (a.kv_dtype == ST_E4M3) attn_mma_eval(a, s);
       else rc = attn_tc_eval(a, ctx->dstatus, s);
       if (rc != ST_OK) return na_fail(ctx, rc, "tcgen05 attention: unsupported shape or tensor-map encoding failed");
     }
