@@ -67,7 +67,8 @@ template <> struct Vec<bf16> {
   }
 };
 
-__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)); }
+// x * sigmoid(x) with the fast reciprocal-based divide (about 2 ulp)
+__device__ __forceinline__ float silu_f(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
 
 // ---------------------------------------------------------------- host side
 struct LayerW {

@@ -9,9 +9,10 @@
 //               128-byte swizzle, mbarrier transaction counts.
 //   warp 1      TMEM allocator (512 columns = two 128x256 f32 accumulators) and,
 //               on one lane, the tcgen05.mma issuer (M=128, N=256, K=16 steps).
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator rows (warp w reads TMEM
-//               lanes 32*(w%4) ..), fused epilogue (RoPE + Q/K/V scatter,
-//               residual add, SwiGLU) straight from registers to global memory.
+//   warps 2-9   epilogue: tcgen05.ld of the accumulator rows (warp w reads TMEM
+//               lanes 32*(w%4) .., warps w and w+4 split the tile's columns),
+//               fused epilogue (RoPE + Q/K/V scatter, residual add, SwiGLU)
+//               straight from registers to global memory.
 // The two accumulators let the epilogue of tile i overlap the main loop of
 // tile i+1.  Every mbarrier wait is bounded; a timeout sets the status word.
 #include <cudaTypedefs.h>
@@ -24,7 +25,7 @@ namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NUM_THREADS = 192;
+constexpr int NUM_THREADS = 320;   // producer, MMA, 8 epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 
@@ -33,12 +34,14 @@ struct Bars {
   uint32_t tmem_base;
 };
 
+// Columns [half * BN/2, (half + 1) * BN/2) of the tile for one accumulator row
+// (SwiGLU: gate columns [half*64, half*64 + 64) with their up columns).
 __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int n0,
-                                              uint32_t taddr, int M) {
+                                              uint32_t taddr, int M, int half) {
   if (ep.mode == EPI_SWIGLU) {
     // columns [0,128) are gate, [128,256) the matching up projections
 #pragma unroll 1
-    for (int j = 0; j < BN / 2; j += 32) {
+    for (int j = half * (BN / 4); j < (half + 1) * (BN / 4); j += 32) {
       uint32_t g[32], u[32];
       ST_TMEM_LD32(taddr + j, g);
       ST_TMEM_LD32(taddr + BN / 2 + j, u);
@@ -55,7 +58,7 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int 
     }
   } else {
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 64) {
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 64) {
       uint32_t r[64];
       uint32_t* r2 = r + 32;
       ST_TMEM_LD32(taddr + c, r);
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&bars->tfull[b], 1);
-      ptx::mbar_init(&bars->tempty[b], 128);
+      ptx::mbar_init(&bars->tempty[b], 256);
     }
     ptx::fence_mbar_init();
     ptx::tma_prefetch_desc(&tmA);
@@ -162,7 +165,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     __syncwarp();
   } else {
-    const int quarter = warp & 3;
+    const int quarter = warp & 3;          // TMEM lanes 32*quarter .. (warp % 4 rule)
+    const int half = (warp - 2) >> 2;      // which half of the tile's columns
     int it = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
       const int buf = it & 1;
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int mb = tile / n_blocks, nb = tile % n_blocks;
       const int row = mb * BM + quarter * 32 + lane;
       const uint32_t taddr = tmem + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
-      epilogue_tile(ep, row, nb * BN, taddr, M);
+      epilogue_tile(ep, row, nb * BN, taddr, M, half);
       ptx::tc_fence_before();
       ptx::mbar_arrive(&bars->tempty[buf]);
     }
