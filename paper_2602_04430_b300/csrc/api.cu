@@ -97,7 +97,7 @@ std::vector<Chunk> plan_chunks(const std::vector<int64_t>& off, int64_t cap) {
 }
 
 struct BuildWs {
-  float *x, *inv_rms, *mu, *s2, *tmp;
+  float *x, *inv_rms, *mu, *s2, *tmp, *ssq;
   void *xn, *q, *o, *h;
   int32_t *rowtup, *pos;
 };
@@ -116,35 +116,9 @@ size_t build_ws_bytes(const st_ctx* ctx, int64_t rows, int64_t tuples, BuildWs* 
   ws.o = cv.take<char>(rows * c.hq * c.hd * e);
   ws.h = cv.take<char>(rows * c.ffn * e);
   ws.tmp = c.dtype == ST_F32 ? cv.take<float>(rows * 2 * c.ffn) : nullptr;
+  ws.ssq = cv.take<float>(rows * (c.d / 128));
   ws.rowtup = cv.take<int32_t>(rows);
   ws.pos = cv.take<int32_t>(rows);
-  if (w) *w = ws;
-  return cv.off + 256;
-}
-
-struct EvalWs {
-  float *x, *tmp;
-  void *xn, *q, *kp, *vp, *o, *h;
-  int32_t *pos, *tup, *len, *nk;
-};
-
-size_t eval_ws_bytes(const st_ctx* ctx, int64_t rows, int64_t tuples, EvalWs* w, void* base) {
-  const st_model_cfg& c = ctx->cfg;
-  Carve cv(base ? base : (void*)0);
-  const size_t e = ctx->esz;
-  EvalWs ws;
-  ws.x = cv.take<float>(rows * c.d);
-  ws.xn = cv.take<char>(rows * c.d * e);
-  ws.q = cv.take<char>(rows * c.hq * c.hd * e);
-  ws.kp = cv.take<char>(rows * c.hkv * c.hd * e);
-  ws.vp = cv.take<char>(rows * c.hkv * c.hd * e);
-  ws.o = cv.take<char>(rows * c.hq * c.hd * e);
-  ws.h = cv.take<char>(rows * c.ffn * e);
-  ws.tmp = c.dtype == ST_F32 ? cv.take<float>(rows * 2 * c.ffn) : nullptr;
-  ws.pos = cv.take<int32_t>(rows);
-  ws.tup = cv.take<int32_t>(tuples);
-  ws.len = cv.take<int32_t>(tuples);
-  ws.nk = cv.take<int32_t>(tuples);
   if (w) *w = ws;
   return cv.off + 256;
 }
@@ -251,6 +225,19 @@ int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_item
     int rc_ = (x);                  \
     if (rc_ != ST_OK) return rc_;   \
   } while (0)
+
+// The projection reads bf16(x) and scales its rows by 1/rms from `ssq`.
+void set_norm_in(EpiParams& ep, const float* ssq, const st_model_cfg& c) {
+  ep.ssq_in = ssq;
+  ep.ssq_parts = c.d / 128;
+  ep.norm_d = c.d;
+  ep.eps = c.eps;
+}
+// The residual epilogue also writes bf16(x) to xb and the partial sums of squares.
+void set_norm_out(EpiParams& ep, void* xb, float* ssq) {
+  ep.xb = xb;
+  ep.ssq_out = ssq;
+}
 
 }  // namespace
 
@@ -378,7 +365,7 @@ extern "C" int st_reserve(st_ctx* ctx, int64_t build_rows, int64_t eval_rows) {
   }
   if (eval_rows > 0) {
     ctx->eval_rows_cap = eval_rows;
-    RC(grow(ctx, ctx->ws_eval, eval_ws_bytes(ctx, eval_rows, eval_rows, nullptr, nullptr)));
+    RC(grow(ctx, ctx->ws_eval, eval_bufs(ctx, eval_rows, eval_rows, nullptr, nullptr)));
   }
   return ST_OK;
 }
@@ -511,12 +498,17 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
       else embed_rows<float>(tokens_dev + ch.r0, ch.rows, (const float*)ctx->embed, c.d, w.x, s);
     }
     CKLAUNCH();
+    // bf16 path: only layer 0 runs a standalone RMSNorm; afterwards every residual
+    // epilogue leaves bf16(x) and the row's partial sums of squares, and the next
+    // projection applies 1/rms in its epilogue.
+    const bool fused = c.dtype == ST_BF16;
     for (int l = 0; l < c.layers; ++l) {
       const LayerW& LW = ctx->layers[l];
       char* Kl = (char*)kv->K + (size_t)l * c.hkv * kv->R * c.hd * e;
       char* Vl = (char*)kv->V + (size_t)l * c.hkv * kv->R * c.hd * e;
-      RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
+      if (!fused || l == 0) RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
       EpiParams ep;
+      if (fused && l > 0) set_norm_in(ep, w.ssq, c);
       ep.mode = EPI_QKV;
       ep.q = w.q;
       ep.kbase = Kl + (size_t)ch.r0 * c.hd * e;
@@ -572,17 +564,20 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
       eo.mode = EPI_RESID;
       eo.x = w.x;
       eo.ld = c.d;
+      if (fused) set_norm_out(eo, w.xn, w.ssq);
       RC(project(ctx, w.o, LW.wo, M, c.d, qd, eo, w.tmp, nullptr, s));
-      RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
+      if (!fused) RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
       EpiParams eg;
       eg.mode = EPI_SWIGLU;
       eg.h = w.h;
       eg.ld = c.ffn;
+      if (fused) set_norm_in(eg, w.ssq, c);
       RC(project(ctx, w.xn, LW.wgu, M, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
       EpiParams ed;
       ed.mode = EPI_RESID;
       ed.x = w.x;
       ed.ld = c.d;
+      if (fused && l + 1 < c.layers) set_norm_out(ed, w.xn, w.ssq);
       RC(project(ctx, w.h, LW.wd, M, c.d, c.ffn, ed, w.tmp, nullptr, s));
     }
     // pooled final-normed last-layer document state
@@ -764,6 +759,147 @@ extern "C" void st_op_free(st_operator* op) {
   delete op;
 }
 
+namespace st {
+
+size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t tuples, char* base, EvalBufs* w) {
+  const st_model_cfg& c = ctx->cfg;
+  const size_t e = ctx->esz;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    char* p = base + off;
+    off += bytes;
+    return (void*)p;
+  };
+  EvalBufs b;
+  b.x = (float*)take(rows * c.d * 4);
+  b.xn = take(rows * c.d * e);
+  b.q = take(rows * c.hq * c.hd * e);
+  b.kp = take(rows * c.hkv * c.hd * e);
+  b.vp = take(rows * c.hkv * c.hd * e);
+  b.o = take(rows * c.hq * c.hd * e);
+  b.h = take(rows * c.ffn * e);
+  b.tmp = c.dtype == ST_F32 ? (float*)take(rows * 2 * c.ffn * 4) : nullptr;
+  b.ssq = (float*)take(rows * (c.d / 128) * 4);
+  b.pos = (int32_t*)take(rows * 4);
+  b.tup = (int32_t*)take(tuples * 4);
+  b.len = (int32_t*)take(tuples * 4);
+  b.nk = (int32_t*)take(tuples * 4);
+  if (w) *w = b;
+  return off + 256;
+}
+
+int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_t* tuple_ids,
+               int nc, const EvalBufs& w, float* logits, int32_t* labels, cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  const int P = op->desc.P;
+  const int M = nc * P;
+  const int qd = c.hq * c.hd, kd = c.hkv * c.hd, nqkv = qd + 2 * kd;
+  const size_t kr_e = kv->kv_dtype == ST_E4M3 ? 1 : ctx->esz;
+  const bool fused = c.dtype == ST_BF16;
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    eval_rowinfo(tuple_ids, nc, P, kv->off, op->desc.r, w.tup, w.len, w.nk, w.pos, s);
+  }
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    embed_prompt(op->prompt, P, M, ctx->embed, c.dtype, c.d, w.x, s);
+  }
+  CKLAUNCH();
+  for (int l = 0; l < c.layers; ++l) {
+    const LayerW& LW = ctx->layers[l];
+    if (!fused || l == 0) RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
+    EpiParams ep;
+    if (fused && l > 0) set_norm_in(ep, w.ssq, c);
+    ep.mode = EPI_QKV;
+    ep.q = w.q;
+    ep.kbase = w.kp;
+    ep.vbase = w.vp;
+    ep.kv_sg = c.hd;
+    ep.kv_sr = kd;
+    ep.pos = w.pos;
+    ep.rope = ctx->rope;
+    ep.hq = c.hq;
+    ep.hkv = c.hkv;
+    ep.hd = c.hd;
+    ep.qkv_f16 = kv->kv_dtype == ST_E4M3 ? 1 : 0;
+    RC(project(ctx, w.xn, LW.wqkv, M, nqkv, c.d, ep, w.tmp, nullptr, s));
+    AttnParams a;
+    a.mode = 1;
+    a.q = w.q;
+    a.o = w.o;
+    a.hq = c.hq;
+    a.hkv = c.hkv;
+    a.hd = c.hd;
+    a.scale = 1.0f / std::sqrt((float)c.hd);
+    a.Kr = (const char*)kv->Kr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
+    a.Vr = (const char*)kv->Vr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
+    a.scales = kv->scales + (size_t)l * c.hkv * (kv->Rp_cap / 64) * 2;
+    a.Rp_cap = kv->Rp_cap;
+    a.offp = kv->offp;
+    a.tup = w.tup;
+    a.nk = w.nk;
+    a.kp = w.kp;
+    a.vp = w.vp;
+    a.n = nc;
+    a.P = P;
+    a.kv_dtype = kv->kv_dtype;
+    RC(attention(ctx, a, nullptr, 0, s));
+    // In the last layer only each tuple's last prompt row feeds the label head:
+    // the output projection, the FFN and their norms run on those nc rows
+    // (rows i*P + P-1 of the stream), read in place through a row stride.
+    const bool last = (l == c.layers - 1) && P > 1;
+    const int Mr = last ? nc : M;
+    EpiParams eo;
+    eo.mode = EPI_RESID;
+    eo.x = w.x;
+    eo.ld = c.d;
+    if (fused) set_norm_out(eo, w.xn, w.ssq);
+    const void* o_in = w.o;
+    if (last) {
+      eo.a_ld = (int64_t)P * qd;
+      eo.row_mul = P;
+      eo.row_add = P - 1;
+      o_in = (const char*)w.o + (size_t)(P - 1) * qd * ctx->esz;
+    }
+    RC(project(ctx, o_in, LW.wo, Mr, c.d, qd, eo, w.tmp, nullptr, s));
+    if (!fused) {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      if (last)
+        rmsnorm_rows<float>(w.x + (size_t)(P - 1) * c.d, nc, c.d, c.eps, (float*)w.xn, nullptr, s,
+                            (int64_t)P * c.d);
+      else
+        rmsnorm_rows<float>(w.x, M, c.d, c.eps, (float*)w.xn, nullptr, s);
+      CKLAUNCH();
+    }
+    EpiParams eg;
+    eg.mode = EPI_SWIGLU;
+    eg.h = w.h;
+    eg.ld = c.ffn;
+    if (fused) set_norm_in(eg, w.ssq, c);
+    RC(project(ctx, w.xn, LW.wgu, Mr, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
+    EpiParams ed;
+    ed.mode = EPI_RESID;
+    ed.x = w.x;
+    ed.ld = c.d;
+    if (fused && !last) set_norm_out(ed, w.xn, w.ssq);
+    if (last) {
+      ed.row_mul = P;
+      ed.row_add = P - 1;
+    }
+    RC(project(ctx, w.h, LW.wd, Mr, c.d, c.ffn, ed, w.tmp, nullptr, s));
+  }
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    label_head(w.x, nc, P, c.d, c.eps, ctx->w_lm, c.dtype, op->labels, op->desc.n_labels, op->bias,
+               op->desc.kind, op->desc.theta_pos, op->desc.theta_neg, logits, labels, s);
+  }
+  CKLAUNCH();
+  return ST_OK;
+}
+
+}  // namespace st
+
 extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
                           const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
                           int32_t* labels_dev, void* stream) {
@@ -778,113 +914,13 @@ extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
   const int P = op->desc.P;
   const int64_t cap = std::max<int64_t>(ctx->eval_rows_cap > 0 ? ctx->eval_rows_cap : kDefaultEvalRows, P);
   const int per_chunk = (int)std::min<int64_t>(n, cap / P);
-  RC(grow(ctx, ctx->ws_eval, eval_ws_bytes(ctx, (int64_t)per_chunk * P, per_chunk, nullptr, nullptr)));
-  EvalWs w;
-  eval_ws_bytes(ctx, (int64_t)per_chunk * P, per_chunk, &w, ctx->ws_eval.p);
-  const size_t e = ctx->esz;
-  const int qd = c.hq * c.hd, kd = c.hkv * c.hd, nqkv = qd + 2 * kd;
-  const size_t kr_e = kv->kv_dtype == ST_E4M3 ? 1 : e;
+  RC(grow(ctx, ctx->ws_eval, eval_bufs(ctx, (int64_t)per_chunk * P, per_chunk, nullptr, nullptr)));
+  EvalBufs w;
+  eval_bufs(ctx, (int64_t)per_chunk * P, per_chunk, (char*)ctx->ws_eval.p, &w);
   for (int i0 = 0; i0 < n; i0 += per_chunk) {
     const int nc = std::min(per_chunk, n - i0);
-    const int M = nc * P;
-    {
-      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      eval_rowinfo(tuple_ids_dev + i0, nc, P, kv->off, op->desc.r, w.tup, w.len, w.nk, w.pos, s);
-    }
-    {
-      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      embed_prompt(op->prompt, P, M, ctx->embed, c.dtype, c.d, w.x, s);
-    }
-    CKLAUNCH();
-    for (int l = 0; l < c.layers; ++l) {
-      const LayerW& LW = ctx->layers[l];
-      RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
-      EpiParams ep;
-      ep.mode = EPI_QKV;
-      ep.q = w.q;
-      ep.kbase = w.kp;
-      ep.vbase = w.vp;
-      ep.kv_sg = c.hd;
-      ep.kv_sr = kd;
-      ep.pos = w.pos;
-      ep.rope = ctx->rope;
-      ep.hq = c.hq;
-      ep.hkv = c.hkv;
-      ep.hd = c.hd;
-      ep.qkv_f16 = kv->kv_dtype == ST_E4M3 ? 1 : 0;
-      RC(project(ctx, w.xn, LW.wqkv, M, nqkv, c.d, ep, w.tmp, nullptr, s));
-      AttnParams a;
-      a.mode = 1;
-      a.q = w.q;
-      a.o = w.o;
-      a.hq = c.hq;
-      a.hkv = c.hkv;
-      a.hd = c.hd;
-      a.scale = 1.0f / std::sqrt((float)c.hd);
-      a.Kr = (const char*)kv->Kr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
-      a.Vr = (const char*)kv->Vr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
-      a.scales = kv->scales + (size_t)l * c.hkv * (kv->Rp_cap / 64) * 2;
-      a.Rp_cap = kv->Rp_cap;
-      a.offp = kv->offp;
-      a.tup = w.tup;
-      a.nk = w.nk;
-      a.kp = w.kp;
-      a.vp = w.vp;
-      a.n = nc;
-      a.P = P;
-      a.kv_dtype = kv->kv_dtype;
-      RC(attention(ctx, a, nullptr, 0, s));
-      // In the last layer only each tuple's last prompt row feeds the label head:
-      // the output projection, the FFN and their norms run on those nc rows
-      // (rows i*P + P-1 of the stream), read in place through a row stride.
-      const bool last = (l == c.layers - 1) && P > 1;
-      const int Mr = last ? nc : M;
-      EpiParams eo;
-      eo.mode = EPI_RESID;
-      eo.x = w.x;
-      eo.ld = c.d;
-      const void* o_in = w.o;
-      if (last) {
-        eo.a_ld = (int64_t)P * qd;
-        eo.row_mul = P;
-        eo.row_add = P - 1;
-        o_in = (const char*)w.o + (size_t)(P - 1) * qd * ctx->esz;
-      }
-      RC(project(ctx, o_in, LW.wo, Mr, c.d, qd, eo, w.tmp, nullptr, s));
-      if (last) {
-        Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-        if (c.dtype == ST_BF16)
-          rmsnorm_rows<bf16>(w.x + (size_t)(P - 1) * c.d, nc, c.d, c.eps, (bf16*)w.xn, nullptr, s,
-                             (int64_t)P * c.d);
-        else
-          rmsnorm_rows<float>(w.x + (size_t)(P - 1) * c.d, nc, c.d, c.eps, (float*)w.xn, nullptr, s,
-                              (int64_t)P * c.d);
-        CKLAUNCH();
-      } else {
-        RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
-      }
-      EpiParams eg;
-      eg.mode = EPI_SWIGLU;
-      eg.h = w.h;
-      eg.ld = c.ffn;
-      RC(project(ctx, w.xn, LW.wgu, Mr, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
-      EpiParams ed;
-      ed.mode = EPI_RESID;
-      ed.x = w.x;
-      ed.ld = c.d;
-      if (last) {
-        ed.row_mul = P;
-        ed.row_add = P - 1;
-      }
-      RC(project(ctx, w.h, LW.wd, Mr, c.d, c.ffn, ed, w.tmp, nullptr, s));
-    }
-    {
-      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      label_head(w.x, nc, P, c.d, c.eps, ctx->w_lm, c.dtype, op->labels, op->desc.n_labels,
-                 op->bias, op->desc.kind, op->desc.theta_pos, op->desc.theta_neg,
-                 logits_dev + (size_t)i0 * op->desc.n_labels, labels_dev + i0, s);
-    }
-    CKLAUNCH();
+    RC(eval_chunk(ctx, kv, op, tuple_ids_dev + i0, nc, w, logits_dev + (size_t)i0 * op->desc.n_labels,
+                  labels_dev + i0, s));
   }
   return ST_OK;
 }

@@ -39,10 +39,25 @@ __device__ __forceinline__ void rope_inplace(float (&v)[W], const float2* __rest
   }
 }
 
-// Apply the epilogue to columns [col0, col0 + W) of output row `row`.
+// 1 / rms of output row `row` from the partial sums of squares of the previous
+// residual epilogue (1 when the A operand is already normalised).
+__device__ __forceinline__ float row_inv_rms(const EpiParams& ep, int row) {
+  if (ep.ssq_in == nullptr) return 1.f;
+  float s = 0.f;
+  for (int k = 0; k < ep.ssq_parts; ++k) s += ep.ssq_in[(int64_t)row * ep.ssq_parts + k];
+  return 1.0f / sqrtf(s / (float)ep.norm_d + ep.eps);
+}
+
+// Apply the epilogue to columns [col0, col0 + W) of output row `row`; `scale`
+// multiplies the accumulators first.  Returns, for EPI_RESID, the sum of the
+// squares of the new stream values (0 otherwise).
 template <typename act_t, int W>
-__device__ __forceinline__ void epilogue_apply(const EpiParams& ep, int row, int col0,
-                                               float (&v)[W]) {
+__device__ __forceinline__ float epilogue_apply(const EpiParams& ep, int row, int col0,
+                                                float (&v)[W], float scale = 1.f) {
+  if (scale != 1.f) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) v[j] *= scale;
+  }
   if (ep.mode == EPI_QKV) {
     const int qcols = ep.hq * W, kcols = ep.hkv * W;
     if (col0 < qcols + kcols) rope_inplace<W>(v, ep.rope + (int64_t)ep.pos[row] * (W / 2));
@@ -62,18 +77,25 @@ __device__ __forceinline__ void epilogue_apply(const EpiParams& ep, int row, int
     else store_act<act_t, W>(reinterpret_cast<act_t*>(base) + off, v);
   } else if (ep.mode == EPI_RESID) {
     float* x = ep.x + ((int64_t)row * ep.row_mul + ep.row_add) * ep.ld + col0;
+    float ss = 0.f;
 #pragma unroll
     for (int j = 0; j < W; j += 4) {
       float4 o = *reinterpret_cast<float4*>(x + j);
       o.x += v[j]; o.y += v[j + 1]; o.z += v[j + 2]; o.w += v[j + 3];
       *reinterpret_cast<float4*>(x + j) = o;
+      v[j] = o.x; v[j + 1] = o.y; v[j + 2] = o.z; v[j + 3] = o.w;
+      ss += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
     }
+    if (ep.xb != nullptr)
+      store_act<bf16, W>(reinterpret_cast<bf16*>(ep.xb) + (int64_t)row * ep.N + col0, v);
+    return ss;
   } else if (ep.mode == EPI_STORE_F32) {
     float* o = ep.out + (int64_t)row * ep.ld + col0;
 #pragma unroll
     for (int j = 0; j < W; j += 4)
       *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
   }
+  return 0.f;
 }
 
 // SwiGLU: gate accumulators g and up accumulators u of FFN columns [f0, f0 + W).

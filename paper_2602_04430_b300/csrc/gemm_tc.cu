@@ -38,6 +38,7 @@ struct Bars {
 // (SwiGLU: gate columns [half*64, half*64 + 64) with their up columns).
 __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int n0,
                                               uint32_t taddr, int M, int half) {
+  const float inv = row < M ? row_inv_rms(ep, row) : 1.f;
   if (ep.mode == EPI_SWIGLU) {
     // columns [0,128) are gate, [128,256) the matching up projections
 #pragma unroll 1
@@ -50,13 +51,14 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int 
         float gf[32], uf[32];
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
-          gf[e] = __uint_as_float(g[e]);
-          uf[e] = __uint_as_float(u[e]);
+          gf[e] = __uint_as_float(g[e]) * inv;
+          uf[e] = __uint_as_float(u[e]) * inv;
         }
         epilogue_swiglu<bf16, 32>(ep, row, n0 / 2 + j, gf, uf);
       }
     }
   } else {
+    float ss = 0.f;
 #pragma unroll 1
     for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 64) {
       uint32_t r[64];
@@ -68,9 +70,11 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int 
         float v[64];
 #pragma unroll
         for (int e = 0; e < 64; ++e) v[e] = __uint_as_float(r[e]);
-        epilogue_apply<bf16, 64>(ep, row, n0 + c, v);
+        ss += epilogue_apply<bf16, 64>(ep, row, n0 + c, v, inv);
       }
     }
+    if (ep.mode == EPI_RESID && ep.ssq_out != nullptr && row < M)
+      ep.ssq_out[(int64_t)row * (ep.N / 128) + (n0 + half * (BN / 2)) / 128] = ss;
   }
 }
 

@@ -13,6 +13,16 @@ struct EpiParams {
   int M = 0, N = 0;
   int64_t a_ld = 0;               // row stride of A in elements (0: K)
   int qkv_f16 = 0;                // EPI_QKV: store q / k / v as IEEE half instead of the act type
+  // Fused RMSNorm (tensor-core path).  EPI_RESID also writes xb[row * N + col] =
+  // bf16(new stream value) and ssq_out[row * (N/128) + col/128] = the sum of the
+  // squares of its 128-column slice.  EPI_QKV / EPI_SWIGLU multiply every
+  // accumulator of row r by 1 / sqrt(sum_k ssq_in[r * ssq_parts + k] / norm_d + eps),
+  // i.e. they project bf16(x) and apply the norm afterwards: (x / rms) W = (x W) / rms.
+  void* xb = nullptr;
+  float* ssq_out = nullptr;
+  const float* ssq_in = nullptr;
+  int ssq_parts = 0, norm_d = 0;
+  float eps = 0.f;
   int64_t row_mul = 1, row_add = 0;   // EPI_RESID writes stream row (row*row_mul + row_add)
   // EPI_QKV: columns [0, hq*hd) are queries, then hkv*hd keys, then hkv*hd values.
   void* q = nullptr;              // act [M][hq*hd]
@@ -118,6 +128,19 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s);
 int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int* status,
                     cudaStream_t s);
 void attn_mma_prefill(const AttnParams& a, const int32_t* items, int n_items, cudaStream_t s);
+
+// ---- operator evaluation sequence (api.cu), shared by st_op_eval and st_op_eval_noalloc ----
+struct EvalBufs {
+  float *x, *tmp, *ssq;
+  void *xn, *q, *kp, *vp, *o, *h;
+  int32_t *pos, *tup, *len, *nk;
+};
+// Lays the buffers for `rows` prompt rows of `tuples` tuples out from `base`
+// (nullptr: layout only); returns the bytes needed.
+size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t tuples, char* base, EvalBufs* w);
+// One batch of nc tuples through every layer and the label head.
+int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_t* tuple_ids,
+               int nc, const EvalBufs& w, float* logits, int32_t* labels, cudaStream_t s);
 
 // ---- retention (retain.cu) ----
 struct RetainParams {
