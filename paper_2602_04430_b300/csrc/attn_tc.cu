@@ -8,11 +8,13 @@
 //               lane, so max / exp2 / sum need no shuffles; P is written as bf16
 //               to shared memory in the MMA's K-major swizzled layout.
 //   O += P V    tcgen05.mma M128 N64 K16 x8, V read MN-major straight from its
-//               [key][dim] tile; the per-tile partial lands in TMEM (two
-//               64-column buffers) and is folded into the thread's registers with
-//               the online-softmax rescale.
-//   loads       one thread issues TMA for 128-key K and V tiles (three stages);
-//               the MMA thread TMA-loads each next item's Q (3-D box).
+//               [key][dim] tile, accumulated in TMEM (one 64-column O buffer
+//               per item, two in flight); a row's running max moves only when
+//               a tile maximum exceeds it by more than 8 (P <= 256), and then
+//               the row of O is rescaled in place (tcgen05.ld / st) before the
+//               next P.V; O is read out once, at the end of the item.
+//   loads       one thread issues TMA for each item's Q (3-D box, two buffers)
+//               and its 128-key K and V tiles (three stages).
 //   E4M3 KV     raw code tiles land in two raw stages; two warps widen them
 //               exactly to f16 into the swizzled K/V stage; Q and the prompt's
 //               K/V arrive in f16, both products run as f16 MMAs, the K block
@@ -33,7 +35,7 @@ constexpr int HD = 64;
 constexpr int TK = 128;          // keys per tile
 constexpr int ROWS = 128;        // query rows per work item
 constexpr int NKV = 3;           // K/V stages
-// warps 0-3 softmax, 4 K/V loads, 5 MMA issue + Q loads, (E4M3 KV) 6-7 widen codes to bf16
+// warps 0-3 softmax, 4 Q and K/V loads, 5 MMA issue, (E4M3 KV) 6-7 widen codes to f16
 constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
 constexpr int OFF_Q = 0;                           // 2 x 16 KB
 constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // NKV x 16 KB
@@ -43,10 +45,10 @@ constexpr int OFF_RAW = OFF_P + 2 * ROWS * TK * 2; // (E4M3) 2 x (K + V codes, 8
 constexpr int RAW_BYTES = 2 * TK * HD;
 constexpr int off_bar(bool fp8) { return OFF_RAW + (fp8 ? 2 * RAW_BYTES : 0); }
 constexpr size_t smem_bytes(bool fp8) { return (size_t)off_bar(fp8) + 256 + 1024; }
-constexpr uint32_t TMEM_COLS = 512;              // S: [0,256), PV: [256,384)
+constexpr uint32_t TMEM_COLS = 512;              // S: [0,256), O: [256,384)
 
 struct Bars {
-  uint64_t kv_full[NKV], kv_empty[NKV], s_full[2], s_free[2], p_full[2], pv_full[2], pv_free[2];
+  uint64_t kv_full[NKV], kv_empty[NKV], s_full[2], s_free[2], p_full[2], pv_done[2], o_free[2];
   uint64_t q_full[2], q_empty[2];
   uint64_t kvc_full[NKV], raw_full[2], raw_empty[2];   // E4M3: widened stages, raw code stages
   uint32_t tmem;
@@ -148,9 +150,9 @@ struct Work {
   }
 };
 
-// Persistent: CTA b processes work items b, b + gridDim.x, ...; the load, MMA
-// (which also loads each next item's Q) and softmax roles each walk the same
-// sequence, connected by mbarrier rings
+// Persistent: CTA b processes work items b, b + gridDim.x, ...; the load (Q per
+// item, K/V per tile), MMA and softmax roles each walk the same sequence,
+// connected by mbarrier rings
 // (Q: 2 buffers, K/V: 3 stages, S and PV accumulators: 2 TMEM buffers each,
 // P: 2 shared-memory tiles), so the next item's loads overlap this item's math.
 template <int MODE, bool FP8>
@@ -183,8 +185,8 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       ptx::mbar_init(&bars->s_full[s], 1);
       ptx::mbar_init(&bars->s_free[s], 128);
       ptx::mbar_init(&bars->p_full[s], 128);
-      ptx::mbar_init(&bars->pv_full[s], 1);
-      ptx::mbar_init(&bars->pv_free[s], 128);
+      ptx::mbar_init(&bars->pv_done[s], 1);
+      ptx::mbar_init(&bars->o_free[s], 128);
       ptx::mbar_init(&bars->q_full[s], 1);
       ptx::mbar_init(&bars->q_empty[s], 129);   // the MMA's commit + 128 softmax threads
     }
@@ -210,12 +212,20 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
         last_kv[s] = -1;
         n_tma[s] = 0;
       }
+      ptx::tma_prefetch_desc(&tmQ);
       bool ok = true;
-      uint32_t c = 0, dc = 0;   // tile counter / E4M3 document-tile counter of this CTA
-      int last_raw[2] = {-1, -1};
-      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+      uint32_t c = 0, dc = 0, qc = 0;   // tile / E4M3 document-tile / item counters of this CTA
+      int last_raw[2] = {-1, -1}, last_q[2] = {-1, -1};
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
         Work<MODE> W;
         W.decode(a, items, w, zb_count);
+        // this item's Q into buffer qc & 1 once the item two back has released it
+        const int qb = qc & 1;
+        if (!ptx::mbar_wait(&bars->q_empty[qb], ((qc >> 1) & 1) ^ 1)) { ok = false; break; }
+        ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
+        ptx::tma_load_3d(smem + OFF_Q + qb * ROWS * 128, &tmQ, &bars->q_full[qb], 0, W.g * W.G,
+                         (int)W.qrow0);
+        last_q[qb] = (int)((qc >> 1) & 1);
         for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
           const int s = c % NKV;
           const uint32_t u = c / NKV;
@@ -254,9 +264,12 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       for (int s = 0; s < NKV; ++s)
         if (last_kv[s] >= 0 && !ptx::mbar_wait(&bars->kv_full[s], (uint32_t)last_kv[s], 100000000LL))
           ok = false;
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < 2; ++s) {
         if (last_raw[s] >= 0 && !ptx::mbar_wait(&bars->raw_full[s], (uint32_t)last_raw[s], 100000000LL))
           ok = false;
+        if (last_q[s] >= 0 && !ptx::mbar_wait(&bars->q_full[s], (uint32_t)last_q[s], 100000000LL))
+          ok = false;
+      }
       if (!ok) atomicExch(status, ST_ETIMEOUT);
     }
   } else if (warp == 5) {
@@ -269,25 +282,11 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       bool ok = true;
       uint32_t c = 0, qc = 0;
       uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};
-      ptx::tma_prefetch_desc(&tmQ);
-      // Q of item qn into buffer qn & 1 once the item two back has released it
-      auto load_q = [&](int wq, uint32_t qn) -> bool {
-        Work<MODE> WQ;
-        WQ.decode(a, items, wq, zb_count);
-        const int qb = qn & 1;
-        if (!ptx::mbar_wait(&bars->q_empty[qb], ((qn >> 1) & 1) ^ 1)) return false;
-        ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
-        ptx::tma_load_3d(smem + OFF_Q + qb * ROWS * 128, &tmQ, &bars->q_full[qb], 0, WQ.g * WQ.G,
-                         (int)WQ.qrow0);
-        return true;
-      };
-      if (blockIdx.x < n_work) ok = load_q(blockIdx.x, 0);
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
         Work<MODE> W;
         W.decode(a, items, w, zb_count);
         const int qb = qc & 1;
         if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
-        if (w + (int)gridDim.x < n_work && !(ok = load_q(w + gridDim.x, qc + 1))) break;
         ptx::tc_fence_after();
         const uint32_t sQ = sQ0 + qb * ROWS * 128;
         const uint32_t base = c;
@@ -317,16 +316,18 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
           const int b = c & 1;
           const uint32_t u = c >> 1;
           if (!ptx::mbar_wait(&bars->p_full[b], u & 1)) { ok = false; break; }
-          if (!ptx::mbar_wait(&bars->pv_free[b], (u & 1) ^ 1)) { ok = false; break; }
+          // the item's first P.V overwrites its O buffer: wait until the item two
+          // back has read it out
+          if (ti == 0 && !ptx::mbar_wait(&bars->o_free[qb], ((qc >> 1) & 1) ^ 1)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint32_t pb = sP0 + b * ROWS * TK * 2;
           const uint32_t vb = sV0 + (c % NKV) * TK * 128;
 #pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk)
-            ptx::mma_f16(tmem + 2 * TK + b * HD,
+            ptx::mma_f16(tmem + 2 * TK + qb * HD,
                          ptx::desc_kmajor_sw128(pb + (kk >> 2) * (ROWS * 128) + (kk & 3) * 32),
-                         desc_mnmajor_sw128(vb + kk * 2048), idPV, kk > 0);
-          ptx::mma_commit(&bars->pv_full[b]);
+                         desc_mnmajor_sw128(vb + kk * 2048), idPV, (ti | kk) > 0);
+          ptx::mma_commit(&bars->pv_done[b]);
           ptx::mma_commit(&bars->kv_empty[c % NKV]);
         }
         if (!ok) break;
@@ -419,27 +420,13 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       if (MODE == 0) row_ok = row_ok && (W.j0 + pos) < W.L;
       ptx::mbar_arrive(&bars->q_empty[qb]);
 
-      float m = -INFINITY, l = 0.f, alpha_prev = 0.f;
-      float o[HD];
-#pragma unroll
-      for (int e = 0; e < HD; ++e) o[e] = 0.f;
+      // O accumulates in TMEM (buffer qb); the running max m only moves when a
+      // row's tile maximum exceeds it by more than 8 (a factor 256 in P), and
+      // then the row's O is rescaled in place before the next P.V is issued.
+      float m = -INFINITY, l = 0.f;
+      const uint32_t o_addr = tmem + lane_base + 2 * TK + qb * HD;
       const int lim = MODE == 0 ? W.j0 + pos : pos;   // causal limit of this row
-      auto fold_pv = [&](uint32_t cj) {
-        const int b = cj & 1;
-        if (!ptx::mbar_wait(&bars->pv_full[b], (cj >> 1) & 1)) { ok = false; return; }
-        ptx::tc_fence_after();
-        uint32_t v0[32], v1[32];
-        ST_TMEM_LD32(tmem + lane_base + 2 * TK + b * HD, v0);
-        ST_TMEM_LD32(tmem + lane_base + 2 * TK + b * HD + 32, v1);
-        ptx::tmem_wait_ld();
-        ptx::tc_fence_before();
-        ptx::mbar_arrive(&bars->pv_free[b]);
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          o[e] = fmaf(o[e], alpha_prev, __uint_as_float(v0[e]));
-          o[32 + e] = fmaf(o[32 + e], alpha_prev, __uint_as_float(v1[e]));
-        }
-      };
+      const uint32_t c0 = c;
       for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
         const int b = c & 1;
         const TileInfo T = W.tile(ti);
@@ -475,15 +462,42 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
             vs[1] = scp[3];
           }
         }
-        float mx4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        float mx8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mx8[k] = -INFINITY;
 #pragma unroll
         for (int k = 0; k < TK; ++k)
-          mx4[k & 3] = fmaxf(mx4[k & 3], __uint_as_float(v[k]) * ks[k >> 6]);
-        const float mx = fmaxf(fmaxf(mx4[0], mx4[1]), fmaxf(mx4[2], mx4[3])) * sl2;
-        const float mn = fmaxf(m, mx);
-        const float base = mn == -INFINITY ? 0.f : mn;
-        const float alpha = ex2(m - base);
-        // probabilities -> bf16 P tile (K-major, 128-byte swizzle)
+          mx8[k & 7] = fmaxf(mx8[k & 7], __uint_as_float(v[k]) * ks[k >> 6]);
+        const float mx = fmaxf(fmaxf(fmaxf(mx8[0], mx8[1]), fmaxf(mx8[2], mx8[3])),
+                               fmaxf(fmaxf(mx8[4], mx8[5]), fmaxf(mx8[6], mx8[7]))) * sl2;
+        const bool need = mx > m + 8.f;
+        if (__any_sync(0xffffffffu, need)) {
+          const float mn = need ? mx : m;
+          const float alpha = need ? ex2(m - mn) : 1.f;
+          if (ti > 0) {
+            // O holds this item's earlier P.V products: scale the row in place
+            if (!ptx::mbar_wait(&bars->pv_done[(c - 1) & 1], ((c - 1) >> 1) & 1)) { ok = false; break; }
+            ptx::tc_fence_after();
+            uint32_t o0[32], o1[32];
+            ST_TMEM_LD32(o_addr, o0);
+            ST_TMEM_LD32(o_addr + 32, o1);
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              o0[e] = __float_as_uint(__uint_as_float(o0[e]) * alpha);
+              o1[e] = __float_as_uint(__uint_as_float(o1[e]) * alpha);
+            }
+            ST_TMEM_ST32(o_addr, o0);
+            ST_TMEM_ST32(o_addr + 32, o1);
+            ptx::tmem_wait_st();
+          }
+          l *= alpha;
+          m = mn;
+        }
+        const float base = m == -INFINITY ? 0.f : m;
+        // the P buffer b was last read by the P.V of tile c - 2
+        if (c >= 2 && !ptx::mbar_wait(&bars->pv_done[b], ((c - 2) >> 1) & 1)) { ok = false; break; }
+        // probabilities -> P tile (K-major, 128-byte swizzle)
         float rs4[4] = {0.f, 0.f, 0.f, 0.f};
         uint8_t* prow = smem + OFF_P + b * (ROWS * TK * 2);
 #pragma unroll
@@ -500,17 +514,22 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
           *reinterpret_cast<uint4*>(prow + (k8 >> 6) * (ROWS * 128) + swz(r, (k8 & 63) >> 3)) =
               make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-        const float rs = (rs4[0] + rs4[1]) + (rs4[2] + rs4[3]);
+        l += (rs4[0] + rs4[1]) + (rs4[2] + rs4[3]);
         fence_proxy_async();
+        ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->p_full[b]);
-        l = l * alpha + rs;
-        if (ti >= 1) fold_pv(c - 1);
-        alpha_prev = alpha;
-        m = mn;
       }
       if (!ok) break;
-      fold_pv(c - 1);
-      if (!ok) break;
+      // the item's last P.V has landed in O: read it out, release the buffer
+      const uint32_t cl = c - 1;
+      if (c == c0 || !ptx::mbar_wait(&bars->pv_done[cl & 1], (cl >> 1) & 1)) { ok = false; break; }
+      ptx::tc_fence_after();
+      uint32_t o0[32], o1[32];
+      ST_TMEM_LD32(o_addr, o0);
+      ST_TMEM_LD32(o_addr + 32, o1);
+      ptx::tmem_wait_ld();
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(&bars->o_free[qb]);
       if (row_ok) {
         const float inv = l > 0.f ? 1.f / l : 0.f;
         int64_t orow;
@@ -518,11 +537,17 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
         else orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
         uint4* dst = reinterpret_cast<uint4*>(og + orow * HD);
 #pragma unroll
-        for (int e = 0; e < HD; e += 8)
-          dst[e / 8] = make_uint4(pack_bf16(o[e] * inv, o[e + 1] * inv),
-                                  pack_bf16(o[e + 2] * inv, o[e + 3] * inv),
-                                  pack_bf16(o[e + 4] * inv, o[e + 5] * inv),
-                                  pack_bf16(o[e + 6] * inv, o[e + 7] * inv));
+        for (int e = 0; e < 32; e += 8) {
+          dst[e / 8] = make_uint4(pack_bf16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
+                                  pack_bf16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
+                                  pack_bf16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
+                                  pack_bf16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
+          dst[4 + e / 8] =
+              make_uint4(pack_bf16(__uint_as_float(o1[e]) * inv, __uint_as_float(o1[e + 1]) * inv),
+                         pack_bf16(__uint_as_float(o1[e + 2]) * inv, __uint_as_float(o1[e + 3]) * inv),
+                         pack_bf16(__uint_as_float(o1[e + 4]) * inv, __uint_as_float(o1[e + 5]) * inv),
+                         pack_bf16(__uint_as_float(o1[e + 6]) * inv, __uint_as_float(o1[e + 7]) * inv));
+        }
       }
     }
     if (!ok) atomicExch(status, ST_ETIMEOUT);
