@@ -177,14 +177,17 @@ def run_reference(args):
     return 0
 
 
-def attention_bytes(cfg, lengths, r, kv_esz):
-    """Algorithmic HBM bytes of the operator's attention over retained KV (all layers):
-    retained K and V once, plus the E4M3 block scales."""
+def attention_bytes(cfg, lengths, r, kv_esz, P):
+    """Compulsory HBM bytes of the operator's attention, all layers: the retained
+    K and V once (plus the E4M3 block scales), and per prompt row its queries,
+    its own keys and values, and its output, 16-bit each."""
     from oracle.operator import n_keep  # host arithmetic only: the retained counts
     n = np.array([n_keep(int(L), r) for L in lengths], dtype=np.float64)
     kv = 2.0 * cfg.layers * cfg.hkv * cfg.hd * kv_esz * n.sum()
     scales = 0.0 if kv_esz == 2 else 2.0 * 4 * cfg.layers * cfg.hkv * np.ceil(n / 64).sum()
-    return kv + scales
+    rows = float(len(lengths)) * P
+    prompt = cfg.layers * rows * 2.0 * cfg.hd * (2 * cfg.hq + 2 * cfg.hkv)
+    return kv + scales + prompt
 
 
 def proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch):
@@ -401,7 +404,8 @@ def main():
         kv_esz = 1 if args.kv_dtype == "e4m3" else 2
         for r in (1.0, 0.5, 0.25, 0.1):
             kv.retain(r, kvd)
-            opr_r = model.operator(synth.make_prompt(32, cfg.vocab, seed=77, label_ids=(1, 0), r=r))
+            pr_r = synth.make_prompt(32, cfg.vocab, seed=77, label_ids=(1, 0), r=r)
+            opr_r = model.operator(pr_r)
             for _ in range(2):
                 opr_r.eval(kv, ids, logits, labels)
             torch.cuda.synchronize()
@@ -418,7 +422,7 @@ def main():
             pr = model.prof_read()
             e_ms = a0.elapsed_time(a1) / reps
             at = pr["attention"]
-            ab = attention_bytes(cfg, table["lengths"], r, kv_esz)
+            ab = attention_bytes(cfg, table["lengths"], r, kv_esz, len(pr_r.prompt))
             gbs = ab / (at["ms"] / reps / 1000.0) / 1e9 if at["ms"] > 0 else 0.0
             gg = pr["gemm"]
             out[str(r)] = {"tuples_per_s": T / (e_ms / 1000.0), "ms": e_ms,

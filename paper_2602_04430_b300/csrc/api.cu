@@ -785,6 +785,7 @@ size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t tuples, char* base, Ev
   b.tup = (int32_t*)take(tuples * 4);
   b.len = (int32_t*)take(tuples * 4);
   b.nk = (int32_t*)take(tuples * 4);
+  b.order = (int32_t*)take(tuples * 4);
   if (w) *w = b;
   return off + 256;
 }
@@ -800,6 +801,10 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
     eval_rowinfo(tuple_ids, nc, P, kv->off, op->desc.r, w.tup, w.len, w.nk, w.pos, s);
+  }
+  if (c.dtype == ST_BF16) {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    eval_order(w.nk, nc, w.order, s);
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
@@ -839,6 +844,7 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_
     a.offp = kv->offp;
     a.tup = w.tup;
     a.nk = w.nk;
+    a.order = c.dtype == ST_BF16 ? w.order : nullptr;
     a.kp = w.kp;
     a.vp = w.vp;
     a.n = nc;

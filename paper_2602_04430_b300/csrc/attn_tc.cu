@@ -2,19 +2,23 @@
 // 128 query rows per CTA: all G query heads of the group share every key/value
 // tile staged in shared memory.
 //
-//   S = Q K^T   tcgen05.mma M128 N128 K16 x4, Q and K K-major (128-byte swizzle),
-//               f32 accumulator in TMEM (two 128-column buffers).
+//   S = Q K^T   tcgen05.mma M128 K16 x4, N = the tile's visible key columns
+//               rounded up to 32; Q and K K-major (128-byte swizzle) in shared
+//               memory, f32 accumulator in TMEM (two 128-column buffers).
 //   softmax     4 warps, one thread per query row: the row is that thread's TMEM
-//               lane, so max / exp2 / sum need no shuffles; P is written as bf16
-//               to shared memory in the MMA's K-major swizzled layout.
-//   O += P V    tcgen05.mma M128 N64 K16 x8, V read MN-major straight from its
-//               [key][dim] tile, accumulated in TMEM (one 64-column O buffer
-//               per item, two in flight); a row's running max moves only when
-//               a tile maximum exceeds it by more than 8 (P <= 256), and then
-//               the row of O is rescaled in place (tcgen05.ld / st) before the
-//               next P.V; O is read out once, at the end of the item.
-//   loads       one thread issues TMA for each item's Q (3-D box, two buffers)
-//               and its 128-key K and V tiles (three stages).
+//               lane, so max / exp2 / sum need no shuffles; P is written back
+//               to TMEM (tcgen05.st) as packed 16-bit pairs.
+//   O += P V    tcgen05.mma M128 N64 K16, A = P read from TMEM, B = V read
+//               MN-major from its [key][dim] shared-memory tile; O accumulates
+//               in TMEM (one 64-column buffer per item, two in flight). A row's
+//               running max moves only when a tile maximum exceeds it by more
+//               than 8 (P <= 256), and then the row of O is rescaled in place
+//               (tcgen05.ld / st) before the next P.V; O is read out once, at
+//               the end of the item.
+//   loads       one thread decodes each work item (into shared memory for the
+//               other roles) and issues TMA for its Q (3-D box, two buffers)
+//               and its K/V tiles (three stages), in 64-row boxes, so that key
+//               rows no query of the item can see are not read.
 //   E4M3 KV     raw code tiles land in two raw stages; two warps widen them
 //               exactly to f16 into the swizzled K/V stage; Q and the prompt's
 //               K/V arrive in f16, both products run as f16 MMAs, the K block
@@ -33,26 +37,32 @@ namespace {
 
 constexpr int HD = 64;
 constexpr int TK = 128;          // keys per tile
+constexpr int BOX = 64;          // key rows per TMA box
 constexpr int ROWS = 128;        // query rows per work item
-constexpr int NKV = 3;           // K/V stages
-// warps 0-3 softmax, 4 Q and K/V loads, 5 MMA issue, (E4M3 KV) 6-7 widen codes to f16
+constexpr int NKV_MAX = 5;       // K/V stages: 5 (bf16 KV), 4 (E4M3 KV, which also holds raw stages)
+constexpr int nkv(bool fp8) { return fp8 ? 4 : 5; }
+// warps 0-3 softmax, 4 item decode + Q and K/V loads, 5 MMA issue,
+// (E4M3 KV) 6-7 widen codes to f16
 constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
 constexpr int OFF_Q = 0;                           // 2 x 16 KB
-constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // NKV x 16 KB
-constexpr int OFF_V = OFF_K + NKV * TK * 128;      // NKV x 16 KB
-constexpr int OFF_P = OFF_V + NKV * TK * 128;      // 2 x 32 KB (two 64-key sub-tiles each)
-constexpr int OFF_RAW = OFF_P + 2 * ROWS * TK * 2; // (E4M3) 2 x (K + V codes, 8 KB each)
-constexpr int RAW_BYTES = 2 * TK * HD;
-constexpr int off_bar(bool fp8) { return OFF_RAW + (fp8 ? 2 * RAW_BYTES : 0); }
-constexpr size_t smem_bytes(bool fp8) { return (size_t)off_bar(fp8) + 256 + 1024; }
-constexpr uint32_t TMEM_COLS = 512;              // S: [0,256), O: [256,384)
+constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // nkv x 16 KB
+constexpr int off_v(bool fp8) { return OFF_K + nkv(fp8) * TK * 128; }      // nkv x 16 KB
+constexpr int off_raw(bool fp8) { return off_v(fp8) + nkv(fp8) * TK * 128; }  // (E4M3) 2 x 16 KB
+constexpr int RAW_BYTES = 2 * TK * HD;             // K + V codes of one tile
+constexpr int off_bar(bool fp8) { return off_raw(fp8) + (fp8 ? 2 * RAW_BYTES : 0); }
+constexpr int off_work(bool fp8) { return off_bar(fp8) + 512; }   // 2 decoded work items
+constexpr size_t smem_bytes(bool fp8) { return (size_t)off_work(fp8) + 256 + 1024; }
+// TMEM columns: S buffers [0, 256), O buffers [256, 384), P buffers [384, 512)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_O = 2 * TK, COL_P = 2 * TK + 2 * HD;
 
 struct Bars {
-  uint64_t kv_full[NKV], kv_empty[NKV], s_full[2], s_free[2], p_full[2], pv_done[2], o_free[2];
+  uint64_t kv_full[NKV_MAX], kv_empty[NKV_MAX], s_full[2], s_free[2], p_full[2], pv_done[2], o_free[2];
   uint64_t q_full[2], q_empty[2];
-  uint64_t kvc_full[NKV], raw_full[2], raw_empty[2];   // E4M3: widened stages, raw code stages
+  uint64_t kvc_full[NKV_MAX], raw_full[2], raw_empty[2];   // E4M3: widened stages, raw code stages
   uint32_t tmem;
 };
+static_assert(sizeof(Bars) <= 512, "barrier block");
 
 __device__ __forceinline__ uint32_t swz(int row, int chunk) {
   return (uint32_t)(row * 128 + ((chunk ^ (row & 7)) << 4));
@@ -60,14 +70,16 @@ __device__ __forceinline__ uint32_t swz(int row, int chunk) {
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-__device__ __forceinline__ void named_sync(int id, int n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
 // 2^x on the special-function unit (flushes subnormal results to zero, which a
 // softmax probability can afford).
 __device__ __forceinline__ float ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float y;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
   return y;
 }
 __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
@@ -92,7 +104,8 @@ __device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t smem_addr) {
 
 struct TileInfo {
   bool prompt;
-  int key0, count;
+  int key0, count;   // first key, keys present in the tile
+  int kc;            // keys visible to at least one query row of the item (>= 1)
 };
 
 // One work item: 128 query rows of one kv head of one tuple.
@@ -101,6 +114,7 @@ struct Work {
   int g, G, rows, row_base, n_tiles, n_doc_tiles;
   int i, n_doc, P;          // eval
   int t, j0, L;             // prefill
+  int lim_max;              // largest causal limit (query position) among the rows
   int64_t doc_row0, prompt_row0, qrow0;
 
   __device__ void decode(const AttnParams& a, const int32_t* items, int w, int zb_count) {
@@ -110,16 +124,18 @@ struct Work {
       const int rest = w / zb_count;
       g = rest % a.hkv;
       i = rest / a.hkv;
+      if (items != nullptr) i = items[i];   // longest tuples first
       P = a.P;
       row_base = zb * ROWS;
       rows = min(ROWS, a.P * G - row_base);
+      lim_max = (row_base + rows - 1) / G;
       const int tt = a.tup[i];
       n_doc = a.nk[i];
       doc_row0 = (int64_t)g * a.Rp_cap + a.offp[tt];
       prompt_row0 = (int64_t)i * a.P;
       qrow0 = (int64_t)i * a.P + row_base / G;
       n_doc_tiles = (n_doc + TK - 1) / TK;
-      n_tiles = n_doc_tiles + (a.P + TK - 1) / TK;
+      n_tiles = n_doc_tiles + (min(a.P, lim_max + 1) + TK - 1) / TK;
     } else {
       const int it = w / a.hkv;
       g = w % a.hkv;
@@ -130,8 +146,8 @@ struct Work {
       rows = ROWS;
       doc_row0 = (int64_t)g * a.R + a.off[t];
       qrow0 = a.off[t] - a.r0 + j0;
-      const int last = min(j0 + ROWS / G, L) - 1;
-      n_doc_tiles = last / TK + 1;
+      lim_max = min(j0 + ROWS / G, L) - 1;
+      n_doc_tiles = lim_max / TK + 1;
       n_tiles = n_doc_tiles;
     }
   }
@@ -146,15 +162,15 @@ struct Work {
       T.key0 = ti * TK;
       T.count = min(TK, (MODE == 1 ? n_doc : L) - T.key0);
     }
+    T.kc = (MODE == 0 || T.prompt) ? min(T.count, lim_max - T.key0 + 1) : T.count;
     return T;
   }
 };
 
-// Persistent: CTA b processes work items b, b + gridDim.x, ...; the load (Q per
-// item, K/V per tile), MMA and softmax roles each walk the same sequence,
-// connected by mbarrier rings
-// (Q: 2 buffers, K/V: 3 stages, S and PV accumulators: 2 TMEM buffers each,
-// P: 2 shared-memory tiles), so the next item's loads overlap this item's math.
+// Persistent: CTA b processes work items b, b + gridDim.x, ...; the load,
+// MMA, softmax (and E4M3 widening) roles each walk the same sequence,
+// connected by mbarrier rings (decoded item + Q: 2 slots, K/V: 3 stages, S, P
+// and O: 2 TMEM buffers each), so the next item's loads overlap this item's math.
 template <int MODE, bool FP8>
 __global__ void __launch_bounds__(nthreads(FP8), 1)
     k_attn_tc(AttnParams a, const int32_t* __restrict__ items, int n_work, int zb_count,
@@ -166,9 +182,11 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   Bars* bars = reinterpret_cast<Bars*>(smem + off_bar(FP8));
+  Work<MODE>* slots = reinterpret_cast<Work<MODE>*>(smem + off_work(FP8));
+  static_assert(sizeof(Work<MODE>) <= 128, "work slot");
   const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
+  constexpr int NKV = nkv(FP8), OFF_V = off_v(FP8), OFF_RAW = off_raw(FP8);
   const uint32_t sK0 = ptx::smem_u32(smem + OFF_K), sV0 = ptx::smem_u32(smem + OFF_V);
-  const uint32_t sP0 = ptx::smem_u32(smem + OFF_P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -188,7 +206,8 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       ptx::mbar_init(&bars->pv_done[s], 1);
       ptx::mbar_init(&bars->o_free[s], 128);
       ptx::mbar_init(&bars->q_full[s], 1);
-      ptx::mbar_init(&bars->q_empty[s], 129);   // the MMA's commit + 128 softmax threads
+      // the MMA's commit once the item's Q is consumed + every other reader of the slot
+      ptx::mbar_init(&bars->q_empty[s], 1 + 128 + (FP8 ? 64 : 0));
     }
     ptx::fence_mbar_init();
   }
@@ -202,8 +221,9 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
   const uint32_t tmem = bars->tmem;
 
   if (warp == 4) {
-    // ------------------------------------------------------------ TMA: K/V tiles
+    // ------------------------------------------------------------ decode + TMA
     if (lane == 0) {
+      ptx::tma_prefetch_desc(&tmQ);
       ptx::tma_prefetch_desc(&tmK);
       ptx::tma_prefetch_desc(&tmV);
       int last_kv[NKV];
@@ -212,16 +232,16 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
         last_kv[s] = -1;
         n_tma[s] = 0;
       }
-      ptx::tma_prefetch_desc(&tmQ);
       bool ok = true;
       uint32_t c = 0, dc = 0, qc = 0;   // tile / E4M3 document-tile / item counters of this CTA
       int last_raw[2] = {-1, -1}, last_q[2] = {-1, -1};
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
-        Work<MODE> W;
-        W.decode(a, items, w, zb_count);
-        // this item's Q into buffer qc & 1 once the item two back has released it
+        // the item into slot qc & 1 once every reader of the item two back is done with it
         const int qb = qc & 1;
         if (!ptx::mbar_wait(&bars->q_empty[qb], ((qc >> 1) & 1) ^ 1)) { ok = false; break; }
+        Work<MODE> W;
+        W.decode(a, items, w, zb_count);
+        slots[qb] = W;
         ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
         ptx::tma_load_3d(smem + OFF_Q + qb * ROWS * 128, &tmQ, &bars->q_full[qb], 0, W.g * W.G,
                          (int)W.qrow0);
@@ -230,31 +250,36 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
           const int s = c % NKV;
           const uint32_t u = c / NKV;
           const TileInfo T = W.tile(ti);
+          const int nbox = (T.kc + BOX - 1) / BOX;
           if (FP8 && !T.prompt) {
             // raw codes into a raw stage; the widening warps fill K/V stage s
             const int rs = dc & 1;
             if (!ptx::mbar_wait(&bars->raw_empty[rs], ((dc >> 1) & 1) ^ 1)) { ok = false; break; }
-            ptx::mbar_arrive_expect_tx(&bars->raw_full[rs], RAW_BYTES);
+            ptx::mbar_arrive_expect_tx(&bars->raw_full[rs], nbox * 2 * BOX * HD);
             uint8_t* dr = smem + OFF_RAW + rs * RAW_BYTES;
-            const int y = (int)(W.doc_row0 + T.key0);
-            ptx::tma_load_2d(dr, &tmK, &bars->raw_full[rs], 0, y);
-            ptx::tma_load_2d(dr + TK * HD, &tmV, &bars->raw_full[rs], 0, y);
+            for (int h = 0; h < nbox; ++h) {
+              const int y = (int)(W.doc_row0 + T.key0 + h * BOX);
+              ptx::tma_load_2d(dr + h * BOX * HD, &tmK, &bars->raw_full[rs], 0, y);
+              ptx::tma_load_2d(dr + TK * HD + h * BOX * HD, &tmV, &bars->raw_full[rs], 0, y);
+            }
             last_raw[rs] = (int)((dc >> 1) & 1);
             ++dc;
             continue;
           }
           if (!ptx::mbar_wait(&bars->kv_empty[s], (u & 1) ^ 1)) { ok = false; break; }
-          ptx::mbar_arrive_expect_tx(&bars->kv_full[s], 2 * TK * 128);
+          ptx::mbar_arrive_expect_tx(&bars->kv_full[s], nbox * 2 * BOX * 128);
           uint8_t* dk = smem + OFF_K + s * TK * 128;
           uint8_t* dv = smem + OFF_V + s * TK * 128;
-          if (T.prompt) {
-            const int y = (int)(W.prompt_row0 + T.key0);
-            ptx::tma_load_2d(dk, &tmKp, &bars->kv_full[s], W.g * HD, y);
-            ptx::tma_load_2d(dv, &tmVp, &bars->kv_full[s], W.g * HD, y);
-          } else {
-            const int y = (int)(W.doc_row0 + T.key0);
-            ptx::tma_load_2d(dk, &tmK, &bars->kv_full[s], 0, y);
-            ptx::tma_load_2d(dv, &tmV, &bars->kv_full[s], 0, y);
+          for (int h = 0; h < nbox; ++h) {
+            if (T.prompt) {
+              const int y = (int)(W.prompt_row0 + T.key0 + h * BOX);
+              ptx::tma_load_2d(dk + h * BOX * 128, &tmKp, &bars->kv_full[s], W.g * HD, y);
+              ptx::tma_load_2d(dv + h * BOX * 128, &tmVp, &bars->kv_full[s], W.g * HD, y);
+            } else {
+              const int y = (int)(W.doc_row0 + T.key0 + h * BOX);
+              ptx::tma_load_2d(dk + h * BOX * 128, &tmK, &bars->kv_full[s], 0, y);
+              ptx::tma_load_2d(dv + h * BOX * 128, &tmV, &bars->kv_full[s], 0, y);
+            }
           }
           last_kv[s] = (int)(n_tma[s] & 1);
           ++n_tma[s];
@@ -274,65 +299,78 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
     }
   } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issue
+    // One stream of tiles over the CTA's items: S of tile c + 1 (which may be
+    // the next item's first) is issued before P.V of tile c, so the softmax
+    // never waits for an S at an item boundary.
     if (lane == 0) {
-      // E4M3 KV runs the products in f16 (codes widen exactly; scales act in f32)
-      constexpr uint32_t idS = FP8 ? ptx::idesc_f16_f32(ROWS, TK) : ptx::idesc_bf16_f32(ROWS, TK);
+      bool ok = true;
+      uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};
+      auto issue_s = [&](const Work<MODE>& W, int ti, uint32_t sQ, uint32_t cc) -> bool {
+        const int s = cc % NKV, b = cc & 1;
+        const TileInfo T = W.tile(ti);
+        const bool widened = FP8 && !T.prompt;
+        // each stage's two "full" barriers complete once per use of their kind
+        uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->kv_full[s];
+        uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
+        const uint32_t par = nuse & 1;
+        ++nuse;
+        if (!ptx::mbar_wait(fb, par)) return false;
+        if (!ptx::mbar_wait(&bars->s_free[b], ((cc >> 1) & 1) ^ 1)) return false;
+        ptx::tc_fence_after();
+        // E4M3 KV runs the products in f16 (codes widen exactly; scales act in f32)
+        const int n = ((T.kc + 31) >> 5) * 32;
+        const uint32_t idS = FP8 ? ptx::idesc_f16_f32(ROWS, n) : ptx::idesc_bf16_f32(ROWS, n);
+        const uint32_t kb = sK0 + s * TK * 128;
+#pragma unroll
+        for (int k = 0; k < HD / 16; ++k)
+          ptx::mma_f16(tmem + b * TK, ptx::desc_kmajor_sw128(sQ + k * 32),
+                       ptx::desc_kmajor_sw128(kb + k * 32), idS, k > 0);
+        ptx::mma_commit(&bars->s_full[b]);
+        return true;
+      };
       constexpr uint32_t idPV =
           (FP8 ? ptx::idesc_f16_f32(ROWS, HD) : ptx::idesc_bf16_f32(ROWS, HD)) | (1u << 16);
-      bool ok = true;
       uint32_t c = 0, qc = 0;
-      uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};
-      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
-        Work<MODE> W;
-        W.decode(a, items, w, zb_count);
+      Work<MODE> W;
+      if (blockIdx.x < n_work) {
+        if (!(ok = ptx::mbar_wait(&bars->q_full[0], 0))) goto mma_done;
+        W = slots[0];
+        if (!(ok = issue_s(W, 0, sQ0, 0))) goto mma_done;
+      }
+      for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++qc) {
         const int qb = qc & 1;
-        if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
-        ptx::tc_fence_after();
-        const uint32_t sQ = sQ0 + qb * ROWS * 128;
-        const uint32_t base = c;
-        auto issue_s = [&](uint32_t cc) -> bool {
-          const int s = cc % NKV, b = cc & 1;
-          const int ti_local = (int)(cc - base);
-          const bool widened = FP8 && !W.tile(ti_local).prompt;
-          // each stage's two "full" barriers complete once per use of their kind
-          uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->kv_full[s];
-          uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
-          const uint32_t par = nuse & 1;
-          ++nuse;
-          if (!ptx::mbar_wait(fb, par)) return false;
-          if (!ptx::mbar_wait(&bars->s_free[b], ((cc >> 1) & 1) ^ 1)) return false;
-          ptx::tc_fence_after();
-          const uint32_t kb = sK0 + s * TK * 128;
-#pragma unroll
-          for (int k = 0; k < HD / 16; ++k)
-            ptx::mma_f16(tmem + b * TK, ptx::desc_kmajor_sw128(sQ + k * 32),
-                         ptx::desc_kmajor_sw128(kb + k * 32), idS, k > 0);
-          ptx::mma_commit(&bars->s_full[b]);
-          return true;
-        };
-        if (!(ok = issue_s(base))) break;
+        const bool has_next = w + (int)gridDim.x < n_work;
+        Work<MODE> Wn;
         for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
-          if (ti + 1 < W.n_tiles && !(ok = issue_s(c + 1))) break;
+          if (ti + 1 < W.n_tiles) {
+            if (!(ok = issue_s(W, ti + 1, sQ0 + qb * ROWS * 128, c + 1))) goto mma_done;
+          } else if (has_next) {
+            // the next item's decoded slot and Q
+            if (!(ok = ptx::mbar_wait(&bars->q_full[qb ^ 1], ((qc + 1) >> 1) & 1))) goto mma_done;
+            Wn = slots[qb ^ 1];
+            if (!(ok = issue_s(Wn, 0, sQ0 + (qb ^ 1) * ROWS * 128, c + 1))) goto mma_done;
+          }
           const int b = c & 1;
-          const uint32_t u = c >> 1;
-          if (!ptx::mbar_wait(&bars->p_full[b], u & 1)) { ok = false; break; }
+          const int ksteps = ((W.tile(ti).kc + 31) >> 5) * 2;
+          if (!(ok = ptx::mbar_wait(&bars->p_full[b], (c >> 1) & 1))) goto mma_done;
           // the item's first P.V overwrites its O buffer: wait until the item two
           // back has read it out
-          if (ti == 0 && !ptx::mbar_wait(&bars->o_free[qb], ((qc >> 1) & 1) ^ 1)) { ok = false; break; }
+          if (ti == 0 && !(ok = ptx::mbar_wait(&bars->o_free[qb], ((qc >> 1) & 1) ^ 1))) goto mma_done;
           ptx::tc_fence_after();
-          const uint32_t pb = sP0 + b * ROWS * TK * 2;
           const uint32_t vb = sV0 + (c % NKV) * TK * 128;
 #pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk)
-            ptx::mma_f16(tmem + 2 * TK + qb * HD,
-                         ptx::desc_kmajor_sw128(pb + (kk >> 2) * (ROWS * 128) + (kk & 3) * 32),
-                         desc_mnmajor_sw128(vb + kk * 2048), idPV, (ti | kk) > 0);
+            if (kk < ksteps)
+              ptx::mma_f16_ta(tmem + COL_O + qb * HD, tmem + COL_P + b * HD + kk * 8,
+                              desc_mnmajor_sw128(vb + kk * 2048), idPV, (ti | kk) > 0);
           ptx::mma_commit(&bars->pv_done[b]);
           ptx::mma_commit(&bars->kv_empty[c % NKV]);
         }
-        if (!ok) break;
+        // Q buffer and slot qb: every S of the item has been issued
         ptx::mma_commit(&bars->q_empty[qb]);
+        W = Wn;
       }
+    mma_done:
       if (!ok) atomicExch(status, ST_ETIMEOUT);
       // every commit of this thread has landed once the last stages are released
       if (ok)
@@ -342,15 +380,17 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
     }
     __syncwarp();
   } else if (FP8 && warp >= 6) {
-    // ------------------------------------------------------------ widen E4M3 -> bf16
+    // ------------------------------------------------------------ widen E4M3 -> f16
     // 64 threads; thread tc widens rows tc and tc + 64 of the K and V code tiles
-    // (value * block scale, rounded to bf16) into the swizzled MMA stage.
+    // into the swizzled MMA stage (the block scales act later, in f32).
     const int tc = threadIdx.x - 192;
     bool ok = true;
-    uint32_t c = 0, dc = 0;
-    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
-      Work<MODE> W;
-      W.decode(a, items, w, zb_count);
+    uint32_t c = 0, dc = 0, qc = 0;
+    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
+      const int qb = qc & 1;
+      if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
+      const Work<MODE> W = slots[qb];
+      ptx::mbar_arrive(&bars->q_empty[qb]);
       for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
         const TileInfo T = W.tile(ti);
         if (T.prompt) continue;
@@ -365,8 +405,8 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
           for (int hrow = 0; hrow < 2; ++hrow) {
             const int row = tc + hrow * 64;
             if (row >= T.count) {
-              // past the tuple's retained slots: exact zeros (their block, and
-              // its scale, may not exist)
+              // past the tuple's retained slots: exact zeros (their codes were
+              // not loaded, and their block scale may not exist)
 #pragma unroll
               for (int ch = 0; ch < 8; ++ch)
                 *reinterpret_cast<uint4*>(dst + swz(row, ch)) = make_uint4(0, 0, 0, 0);
@@ -407,43 +447,82 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
     const float sl2 = a.scale * 1.4426950408889634f;
     const uint32_t lane_base = (uint32_t)((warp * 32) << 16);
     bf16* og = reinterpret_cast<bf16*>(a.o);
-    const bf16* qg = reinterpret_cast<const bf16*>(a.q);
     bool ok = true;
     uint32_t c = 0, qc = 0;
+    // An item's O is read out after the next item's first tile, by when its
+    // last P.V has long completed.
+    struct Pending {
+      bool on, row_ok;
+      int qb;
+      uint32_t cl;    // tile counter of the item's last tile
+      float l;
+      int64_t orow;
+    } pend = {false, false, 0, 0, 0.f, 0};
+    auto read_out = [&]() -> bool {
+      pend.on = false;
+      if (!ptx::mbar_wait(&bars->pv_done[pend.cl & 1], (pend.cl >> 1) & 1)) return false;
+      ptx::tc_fence_after();
+      const uint32_t o_addr = tmem + lane_base + COL_O + pend.qb * HD;
+      uint32_t o0[32], o1[32];
+      ST_TMEM_LD32(o_addr, o0);
+      ST_TMEM_LD32(o_addr + 32, o1);
+      ptx::tmem_wait_ld();
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(&bars->o_free[pend.qb]);
+      if (pend.row_ok) {
+        const float inv = pend.l > 0.f ? 1.f / pend.l : 0.f;
+        uint4* dst = reinterpret_cast<uint4*>(og + pend.orow * HD);
+#pragma unroll
+        for (int e = 0; e < 32; e += 8) {
+          dst[e / 8] = make_uint4(pack_bf16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
+                                  pack_bf16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
+                                  pack_bf16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
+                                  pack_bf16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
+          dst[4 + e / 8] =
+              make_uint4(pack_bf16(__uint_as_float(o1[e]) * inv, __uint_as_float(o1[e + 1]) * inv),
+                         pack_bf16(__uint_as_float(o1[e + 2]) * inv, __uint_as_float(o1[e + 3]) * inv),
+                         pack_bf16(__uint_as_float(o1[e + 4]) * inv, __uint_as_float(o1[e + 5]) * inv),
+                         pack_bf16(__uint_as_float(o1[e + 6]) * inv, __uint_as_float(o1[e + 7]) * inv));
+        }
+      }
+      return true;
+    };
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
-      Work<MODE> W;
-      W.decode(a, items, w, zb_count);
       const int qb = qc & 1;
+      if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
+      const Work<MODE> W = slots[qb];
+      ptx::mbar_arrive(&bars->q_empty[qb]);
       const int rr = W.row_base + r;
       const int pos = rr / W.G, hh = rr % W.G;
       bool row_ok = r < W.rows;
       if (MODE == 0) row_ok = row_ok && (W.j0 + pos) < W.L;
-      ptx::mbar_arrive(&bars->q_empty[qb]);
 
       // O accumulates in TMEM (buffer qb); the running max m only moves when a
       // row's tile maximum exceeds it by more than 8 (a factor 256 in P), and
       // then the row's O is rescaled in place before the next P.V is issued.
       float m = -INFINITY, l = 0.f;
-      const uint32_t o_addr = tmem + lane_base + 2 * TK + qb * HD;
+      const uint32_t o_addr = tmem + lane_base + COL_O + qb * HD;
       const int lim = MODE == 0 ? W.j0 + pos : pos;   // causal limit of this row
-      const uint32_t c0 = c;
       for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
         const int b = c & 1;
         const TileInfo T = W.tile(ti);
+        const int nch = (T.kc + 31) >> 5;           // 32-key chunks any row can see
         const bool causal = (MODE == 0) || T.prompt;
         if (!ptx::mbar_wait(&bars->s_full[b], (c >> 1) & 1)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t sb = tmem + lane_base + b * TK;
-        // the whole S row into registers with one wait, then release the TMEM buffer
+        // the row's visible chunks of S into registers with one wait, then
+        // release the TMEM buffer
         uint32_t v[TK];
         ST_TMEM_LD32(sb, v);
-        ST_TMEM_LD32(sb + 32, (v + 32));
-        ST_TMEM_LD32(sb + 64, (v + 64));
-        ST_TMEM_LD32(sb + 96, (v + 96));
+        if (nch > 1) ST_TMEM_LD32(sb + 32, (v + 32));
+        if (nch > 2) ST_TMEM_LD32(sb + 64, (v + 64));
+        if (nch > 3) ST_TMEM_LD32(sb + 96, (v + 96));
         ptx::tmem_wait_ld();
         ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->s_free[b]);
-        // invisible keys of this row (ragged tail, causal limit) become -inf
+        // invisible keys of this row (ragged tail, causal limit, chunks not
+        // loaded) become -inf
         int nvis = T.count;
         if (causal) nvis = min(nvis, lim - T.key0 + 1);
         if (nvis < TK) {
@@ -462,14 +541,27 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
             vs[1] = scp[3];
           }
         }
-        float mx8[8];
+        float mx;
+        {
+          float m4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) mx8[k] = -INFINITY;
+          for (int ch = 0; ch < 4; ++ch) {
+            if (ch < nch) {
 #pragma unroll
-        for (int k = 0; k < TK; ++k)
-          mx8[k & 7] = fmaxf(mx8[k & 7], __uint_as_float(v[k]) * ks[k >> 6]);
-        const float mx = fmaxf(fmaxf(fmaxf(mx8[0], mx8[1]), fmaxf(mx8[2], mx8[3])),
-                               fmaxf(fmaxf(mx8[4], mx8[5]), fmaxf(mx8[6], mx8[7]))) * sl2;
+              for (int k = 32 * ch; k < 32 * ch + 32; k += 8) {
+                const float sc = ks[ch >> 1];
+                m4[(k >> 3) & 3] = max3(m4[(k >> 3) & 3],
+                                        max3(__uint_as_float(v[k]) * sc, __uint_as_float(v[k + 1]) * sc,
+                                             __uint_as_float(v[k + 2]) * sc),
+                                        max3(__uint_as_float(v[k + 3]) * sc, __uint_as_float(v[k + 4]) * sc,
+                                             max3(__uint_as_float(v[k + 5]) * sc,
+                                                  __uint_as_float(v[k + 6]) * sc,
+                                                  __uint_as_float(v[k + 7]) * sc)));
+              }
+            }
+          }
+          mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3])) * sl2;
+        }
         const bool need = mx > m + 8.f;
         if (__any_sync(0xffffffffu, need)) {
           const float mn = need ? mx : m;
@@ -478,17 +570,15 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
             // O holds this item's earlier P.V products: scale the row in place
             if (!ptx::mbar_wait(&bars->pv_done[(c - 1) & 1], ((c - 1) >> 1) & 1)) { ok = false; break; }
             ptx::tc_fence_after();
-            uint32_t o0[32], o1[32];
-            ST_TMEM_LD32(o_addr, o0);
-            ST_TMEM_LD32(o_addr + 32, o1);
-            ptx::tmem_wait_ld();
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+              uint32_t o0[32];
+              ST_TMEM_LD32(o_addr + 32 * half, o0);
+              ptx::tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              o0[e] = __float_as_uint(__uint_as_float(o0[e]) * alpha);
-              o1[e] = __float_as_uint(__uint_as_float(o1[e]) * alpha);
+              for (int e = 0; e < 32; ++e) o0[e] = __float_as_uint(__uint_as_float(o0[e]) * alpha);
+              ST_TMEM_ST32(o_addr + 32 * half, o0);
             }
-            ST_TMEM_ST32(o_addr, o0);
-            ST_TMEM_ST32(o_addr + 32, o1);
             ptx::tmem_wait_st();
           }
           l *= alpha;
@@ -497,59 +587,42 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
         const float base = m == -INFINITY ? 0.f : m;
         // the P buffer b was last read by the P.V of tile c - 2
         if (c >= 2 && !ptx::mbar_wait(&bars->pv_done[b], ((c - 2) >> 1) & 1)) { ok = false; break; }
-        // probabilities -> P tile (K-major, 128-byte swizzle)
+        ptx::tc_fence_after();
+        // probabilities of the visible chunks, packed in pairs (key 2j low, 2j+1
+        // high), 16 TMEM columns per 32-key chunk
+        const uint32_t pcol = tmem + lane_base + COL_P + b * HD;
         float rs4[4] = {0.f, 0.f, 0.f, 0.f};
-        uint8_t* prow = smem + OFF_P + b * (ROWS * TK * 2);
 #pragma unroll
-        for (int k8 = 0; k8 < TK; k8 += 8) {
-          uint32_t pk[4];
-          const float mul = sl2 * ks[k8 >> 6], vsc = vs[k8 >> 6];
+        for (int ch = 0; ch < 4; ++ch) {
+          if (ch < nch) {
+            const float mul = sl2 * ks[ch >> 1], vsc = vs[ch >> 1];
+            uint32_t pk[16];
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            const float p0 = ex2(fmaf(__uint_as_float(v[k8 + e]), mul, -base));
-            const float p1 = ex2(fmaf(__uint_as_float(v[k8 + e + 1]), mul, -base));
-            rs4[e >> 1] += p0 + p1;
-            pk[e >> 1] = FP8 ? pack_f16(p0 * vsc, p1 * vsc) : pack_bf16(p0, p1);
+            for (int k = 0; k < 32; k += 2) {
+              const float p0 = ex2(fmaf(__uint_as_float(v[32 * ch + k]), mul, -base));
+              const float p1 = ex2(fmaf(__uint_as_float(v[32 * ch + k + 1]), mul, -base));
+              rs4[(k >> 1) & 3] += p0 + p1;
+              pk[k >> 1] = FP8 ? pack_f16(p0 * vsc, p1 * vsc) : pack_bf16(p0, p1);
+            }
+            ST_TMEM_ST16(pcol + 16 * ch, pk);
           }
-          *reinterpret_cast<uint4*>(prow + (k8 >> 6) * (ROWS * 128) + swz(r, (k8 & 63) >> 3)) =
-              make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
         l += (rs4[0] + rs4[1]) + (rs4[2] + rs4[3]);
-        fence_proxy_async();
+        ptx::tmem_wait_st();
         ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->p_full[b]);
+        if (ti == 0 && pend.on && !(ok = read_out())) break;
       }
       if (!ok) break;
-      // the item's last P.V has landed in O: read it out, release the buffer
-      const uint32_t cl = c - 1;
-      if (c == c0 || !ptx::mbar_wait(&bars->pv_done[cl & 1], (cl >> 1) & 1)) { ok = false; break; }
-      ptx::tc_fence_after();
-      uint32_t o0[32], o1[32];
-      ST_TMEM_LD32(o_addr, o0);
-      ST_TMEM_LD32(o_addr + 32, o1);
-      ptx::tmem_wait_ld();
-      ptx::tc_fence_before();
-      ptx::mbar_arrive(&bars->o_free[qb]);
-      if (row_ok) {
-        const float inv = l > 0.f ? 1.f / l : 0.f;
-        int64_t orow;
-        if (MODE == 1) orow = ((int64_t)W.i * a.P + pos) * a.hq + (int64_t)W.g * W.G + hh;
-        else orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
-        uint4* dst = reinterpret_cast<uint4*>(og + orow * HD);
-#pragma unroll
-        for (int e = 0; e < 32; e += 8) {
-          dst[e / 8] = make_uint4(pack_bf16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
-                                  pack_bf16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
-                                  pack_bf16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
-                                  pack_bf16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
-          dst[4 + e / 8] =
-              make_uint4(pack_bf16(__uint_as_float(o1[e]) * inv, __uint_as_float(o1[e + 1]) * inv),
-                         pack_bf16(__uint_as_float(o1[e + 2]) * inv, __uint_as_float(o1[e + 3]) * inv),
-                         pack_bf16(__uint_as_float(o1[e + 4]) * inv, __uint_as_float(o1[e + 5]) * inv),
-                         pack_bf16(__uint_as_float(o1[e + 6]) * inv, __uint_as_float(o1[e + 7]) * inv));
-        }
-      }
+      pend.on = true;
+      pend.row_ok = row_ok;
+      pend.qb = qb;
+      pend.cl = c - 1;
+      pend.l = l;
+      if (MODE == 1) pend.orow = ((int64_t)W.i * a.P + pos) * a.hq + (int64_t)W.g * W.G + hh;
+      else pend.orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
     }
+    if (ok && pend.on) ok = read_out();
     if (!ok) atomicExch(status, ST_ETIMEOUT);
   }
   ptx::tc_fence_before();
@@ -559,6 +632,7 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
     ptx::tmem_dealloc(tmem, TMEM_COLS);
   }
 }
+
 
 bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_outer,
            CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
@@ -662,21 +736,21 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   const uint64_t prow = (uint64_t)a.n * a.P;
   const CUtensorMapDataType qt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   bool ok = map_q(&mq, a.q, a.hq, prow, G, qt) &&
-            map2d(&mkp, a.kp, (uint64_t)a.hkv * HD, prow, TK, qt) &&
-            map2d(&mvp, a.vp, (uint64_t)a.hkv * HD, prow, TK, qt);
-  if (fp8) ok = ok && map2d_u8(&mk, a.Kr, planes, TK) && map2d_u8(&mv, a.Vr, planes, TK);
-  else ok = ok && map2d(&mk, a.Kr, HD, planes, TK) && map2d(&mv, a.Vr, HD, planes, TK);
+            map2d(&mkp, a.kp, (uint64_t)a.hkv * HD, prow, BOX, qt) &&
+            map2d(&mvp, a.vp, (uint64_t)a.hkv * HD, prow, BOX, qt);
+  if (fp8) ok = ok && map2d_u8(&mk, a.Kr, planes, BOX) && map2d_u8(&mv, a.Vr, planes, BOX);
+  else ok = ok && map2d(&mk, a.Kr, HD, planes, BOX) && map2d(&mv, a.Vr, HD, planes, BOX);
   if (!ok) return ST_ECUDA;
   const int zb = (a.P * G + ROWS - 1) / ROWS;
   const int n_work = a.n * a.hkv * zb;
   const int grid = n_work < sm_count() ? n_work : sm_count();
   if (fp8) {
     set_smem_attr<1, true>();
-    k_attn_tc<1, true><<<grid, nthreads(true), smem_bytes(true), s>>>(a, nullptr, n_work, zb, mq, mk,
+    k_attn_tc<1, true><<<grid, nthreads(true), smem_bytes(true), s>>>(a, a.order, n_work, zb, mq, mk,
                                                                       mv, mkp, mvp, status);
   } else {
     set_smem_attr<1, false>();
-    k_attn_tc<1, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, nullptr, n_work, zb, mq,
+    k_attn_tc<1, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, a.order, n_work, zb, mq,
                                                                          mk, mv, mkp, mvp, status);
   }
   return ST_OK;
@@ -689,8 +763,8 @@ int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int*
   const int G = a.hq / a.hkv;
   CUtensorMap mq, mk, mv;
   const uint64_t planes = (uint64_t)a.hkv * a.R;
-  if (!map_q(&mq, a.q, a.hq, (uint64_t)a.rows, G) || !map2d(&mk, a.K, HD, planes, TK) ||
-      !map2d(&mv, a.V, HD, planes, TK))
+  if (!map_q(&mq, a.q, a.hq, (uint64_t)a.rows, G) || !map2d(&mk, a.K, HD, planes, BOX) ||
+      !map2d(&mv, a.V, HD, planes, BOX))
     return ST_ECUDA;
   set_smem_attr<0, false>();
   const int n_work = n_items * a.hkv;

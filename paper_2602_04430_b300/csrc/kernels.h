@@ -64,6 +64,7 @@ void build_rowinfo(const int64_t* off, int t0, int t1, int64_t r0, int64_t rows,
                    int32_t* pos, cudaStream_t s);
 void eval_rowinfo(const int32_t* tuple_ids, int n, int P, const int64_t* off, double r,
                   int32_t* tup, int32_t* len, int32_t* nk, int32_t* pos, cudaStream_t s);
+void eval_order(const int32_t* nk, int n, int32_t* order, cudaStream_t s);
 template <typename act_t>
 void qstats(const act_t* q, const int64_t* off, int t0, int t1, int64_t r0, int hq, int hkv,
             int hd, float* mu, float* s2, cudaStream_t s);
@@ -115,6 +116,7 @@ struct AttnParams {
   const int64_t* offp = nullptr;
   const int32_t* tup = nullptr;   // [n] tuple of each evaluated item
   const int32_t* nk = nullptr;    // [n] retained slots read per item
+  const int32_t* order = nullptr; // [n] item positions, longest first (nullptr: as given)
   const void* kp = nullptr;       // prompt keys kp[(i*P + p)*hkv*hd + g*hd + c]
   const void* vp = nullptr;
   int n = 0, P = 0;
@@ -133,7 +135,7 @@ void attn_mma_prefill(const AttnParams& a, const int32_t* items, int n_items, cu
 struct EvalBufs {
   float *x, *tmp, *ssq;
   void *xn, *q, *kp, *vp, *o, *h;
-  int32_t *pos, *tup, *len, *nk;
+  int32_t *pos, *tup, *len, *nk, *order;
 };
 // Lays the buffers for `rows` prompt rows of `tuples` tuples out from `base`
 // (nullptr: layout only); returns the bytes needed.

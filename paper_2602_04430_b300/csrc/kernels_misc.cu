@@ -75,6 +75,50 @@ void eval_rowinfo(const int32_t* tuple_ids, int n, int P, const int64_t* off, do
                                                                  nk, pos);
 }
 
+// Positions of the n evaluated items ordered by retained length, longest
+// first (a counting sort on the 128-key tile count, capped at 1023), so that a
+// persistent attention grid walking them in turn ends with its shortest items.
+// One block of 1024 threads; the order within a bucket is arbitrary.
+__global__ void __launch_bounds__(1024) k_eval_order(const int32_t* __restrict__ nk, int n,
+                                                     int32_t* order) {
+  __shared__ int cnt[1024];
+  __shared__ int wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  cnt[tid] = 0;
+  __syncthreads();
+  auto bucket = [&](int i) { return 1023 - min((nk[i] + 127) / 128, 1023); };
+  for (int i = tid; i < n; i += 1024) atomicAdd(&cnt[bucket(i)], 1);
+  __syncthreads();
+  // exclusive prefix sum over the buckets
+  const int x = cnt[tid];
+  int inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int ws = wsum[lane], wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    wsum[lane] = wi - ws;
+  }
+  __syncthreads();
+  cnt[tid] = wsum[wid] + inc - x;
+  __syncthreads();
+  for (int i = tid; i < n; i += 1024) order[atomicAdd(&cnt[bucket(i)], 1)] = i;
+}
+
+void eval_order(const int32_t* nk, int n, int32_t* order, cudaStream_t s) {
+  if (n <= 0) return;
+  k_eval_order<<<1, 1024, 0, s>>>(nk, n, order);
+}
+
 // Retained counts and padded (64-slot) offsets of every tuple, one block.
 __global__ void k_nkeep_offp(const int64_t* __restrict__ off, int T, double r, int32_t* nkeep,
                              int64_t* offp) {
