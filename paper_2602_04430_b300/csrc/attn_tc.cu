@@ -39,8 +39,14 @@ constexpr int HD = 64;
 constexpr int TK = 128;          // keys per tile
 constexpr int BOX = 64;          // key rows per TMA box
 constexpr int ROWS = 128;        // query rows per work item
-constexpr int NKV_MAX = 5;       // K/V stages: 5 (bf16 KV), 4 (E4M3 KV, which also holds raw stages)
-constexpr int nkv(bool fp8) { return fp8 ? 4 : 5; }
+// BF16 KV: two CTAs per SM (each with one S, P and O buffer in 256 TMEM
+// columns and two K/V stages), so every SM sub-partition runs two independent
+// softmax warps. E4M3 KV: one CTA per SM with double buffers and 4 stages
+// (its raw code stages leave no room for a second CTA).
+constexpr int ctas_per_sm(bool fp8) { return fp8 ? 1 : 2; }
+constexpr int nbuf(bool fp8) { return fp8 ? 2 : 1; }     // S, P and O buffers
+constexpr int NKV_MAX = 4;
+constexpr int nkv(bool fp8) { return fp8 ? 4 : 2; }
 // warps 0-3 softmax, 4 item decode + Q and K/V loads, 5 MMA issue,
 // (E4M3 KV) 6-7 widen codes to f16
 constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
@@ -52,9 +58,10 @@ constexpr int RAW_BYTES = 2 * TK * HD;             // K + V codes of one tile
 constexpr int off_bar(bool fp8) { return off_raw(fp8) + (fp8 ? 2 * RAW_BYTES : 0); }
 constexpr int off_work(bool fp8) { return off_bar(fp8) + 512; }   // 2 decoded work items
 constexpr size_t smem_bytes(bool fp8) { return (size_t)off_work(fp8) + 256 + 1024; }
-// TMEM columns: S buffers [0, 256), O buffers [256, 384), P buffers [384, 512)
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t COL_O = 2 * TK, COL_P = 2 * TK + 2 * HD;
+// TMEM columns: S buffers [0, 128 nb), O buffers [128 nb, 192 nb), P buffers [192 nb, 256 nb)
+constexpr uint32_t tmem_cols(bool fp8) { return 256 * nbuf(fp8); }
+constexpr uint32_t col_o(bool fp8) { return TK * nbuf(fp8); }
+constexpr uint32_t col_p(bool fp8) { return (TK + HD) * nbuf(fp8); }
 
 struct Bars {
   uint64_t kv_full[NKV_MAX], kv_empty[NKV_MAX], s_full[2], s_free[2], p_full[2], pv_done[2], o_free[2];
@@ -81,6 +88,38 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
   float y;
   asm("max.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
   return y;
+}
+// Two float32 lanes in one 64-bit register (lane 0 low): Blackwell's packed
+// FP32 pipe runs fma / add / mul on both with one instruction.
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+  return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2lo(uint64_t x) { return __uint_as_float((uint32_t)x); }
+__device__ __forceinline__ float f2hi(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Maximum of the 32 scores of one chunk, as a tree of 3-input maxima.
+__device__ __forceinline__ float chunk_max(const uint32_t* v) {
+  float t[11];
+#pragma unroll
+  for (int i = 0; i < 10; ++i)
+    t[i] = max3(__uint_as_float(v[3 * i]), __uint_as_float(v[3 * i + 1]), __uint_as_float(v[3 * i + 2]));
+  t[10] = fmaxf(__uint_as_float(v[30]), __uint_as_float(v[31]));
+  const float u0 = max3(t[0], t[1], t[2]), u1 = max3(t[3], t[4], t[5]), u2 = max3(t[6], t[7], t[8]);
+  return max3(max3(u0, u1, u2), t[9], t[10]);
 }
 __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
   __half2 v = __floats2half2_rn(lo, hi);
@@ -172,7 +211,7 @@ struct Work {
 // connected by mbarrier rings (decoded item + Q: 2 slots, K/V: 3 stages, S, P
 // and O: 2 TMEM buffers each), so the next item's loads overlap this item's math.
 template <int MODE, bool FP8>
-__global__ void __launch_bounds__(nthreads(FP8), 1)
+__global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
     k_attn_tc(AttnParams a, const int32_t* __restrict__ items, int n_work, int zb_count,
               const __grid_constant__ CUtensorMap tmQ,
               const __grid_constant__ CUtensorMap tmK, const __grid_constant__ CUtensorMap tmV,
@@ -185,7 +224,8 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
   Work<MODE>* slots = reinterpret_cast<Work<MODE>*>(smem + off_work(FP8));
   static_assert(sizeof(Work<MODE>) <= 128, "work slot");
   const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
-  constexpr int NKV = nkv(FP8), OFF_V = off_v(FP8), OFF_RAW = off_raw(FP8);
+  constexpr int NKV = nkv(FP8), OFF_V = off_v(FP8), OFF_RAW = off_raw(FP8), NB = nbuf(FP8);
+  constexpr uint32_t TMEM_COLS = tmem_cols(FP8), COL_O = col_o(FP8), COL_P = col_p(FP8);
   const uint32_t sK0 = ptx::smem_u32(smem + OFF_K), sV0 = ptx::smem_u32(smem + OFF_V);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -306,7 +346,7 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       bool ok = true;
       uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};
       auto issue_s = [&](const Work<MODE>& W, int ti, uint32_t sQ, uint32_t cc) -> bool {
-        const int s = cc % NKV, b = cc & 1;
+        const int s = cc % NKV, b = cc % NB;
         const TileInfo T = W.tile(ti);
         const bool widened = FP8 && !T.prompt;
         // each stage's two "full" barriers complete once per use of their kind
@@ -315,7 +355,7 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
         const uint32_t par = nuse & 1;
         ++nuse;
         if (!ptx::mbar_wait(fb, par)) return false;
-        if (!ptx::mbar_wait(&bars->s_free[b], ((cc >> 1) & 1) ^ 1)) return false;
+        if (!ptx::mbar_wait(&bars->s_free[b], ((cc / NB) & 1) ^ 1)) return false;
         ptx::tc_fence_after();
         // E4M3 KV runs the products in f16 (codes widen exactly; scales act in f32)
         const int n = ((T.kc + 31) >> 5) * 32;
@@ -331,44 +371,42 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       constexpr uint32_t idPV =
           (FP8 ? ptx::idesc_f16_f32(ROWS, HD) : ptx::idesc_bf16_f32(ROWS, HD)) | (1u << 16);
       uint32_t c = 0, qc = 0;
-      Work<MODE> W;
+      // decoded items are read in place: a slot is rewritten only after this
+      // thread's commit at the end of its item
       if (blockIdx.x < n_work) {
         if (!(ok = ptx::mbar_wait(&bars->q_full[0], 0))) goto mma_done;
-        W = slots[0];
-        if (!(ok = issue_s(W, 0, sQ0, 0))) goto mma_done;
+        if (!(ok = issue_s(slots[0], 0, sQ0, 0))) goto mma_done;
       }
       for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++qc) {
         const int qb = qc & 1;
         const bool has_next = w + (int)gridDim.x < n_work;
-        Work<MODE> Wn;
+        const Work<MODE>& W = slots[qb];
         for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
           if (ti + 1 < W.n_tiles) {
             if (!(ok = issue_s(W, ti + 1, sQ0 + qb * ROWS * 128, c + 1))) goto mma_done;
           } else if (has_next) {
             // the next item's decoded slot and Q
             if (!(ok = ptx::mbar_wait(&bars->q_full[qb ^ 1], ((qc + 1) >> 1) & 1))) goto mma_done;
-            Wn = slots[qb ^ 1];
-            if (!(ok = issue_s(Wn, 0, sQ0 + (qb ^ 1) * ROWS * 128, c + 1))) goto mma_done;
+            if (!(ok = issue_s(slots[qb ^ 1], 0, sQ0 + (qb ^ 1) * ROWS * 128, c + 1))) goto mma_done;
           }
-          const int b = c & 1;
+          const int b = c % NB, ob = qc % NB;
           const int ksteps = ((W.tile(ti).kc + 31) >> 5) * 2;
-          if (!(ok = ptx::mbar_wait(&bars->p_full[b], (c >> 1) & 1))) goto mma_done;
-          // the item's first P.V overwrites its O buffer: wait until the item two
+          if (!(ok = ptx::mbar_wait(&bars->p_full[b], (c / NB) & 1))) goto mma_done;
+          // the item's first P.V overwrites its O buffer: wait until the item NB
           // back has read it out
-          if (ti == 0 && !(ok = ptx::mbar_wait(&bars->o_free[qb], ((qc >> 1) & 1) ^ 1))) goto mma_done;
+          if (ti == 0 && !(ok = ptx::mbar_wait(&bars->o_free[ob], ((qc / NB) & 1) ^ 1))) goto mma_done;
           ptx::tc_fence_after();
           const uint32_t vb = sV0 + (c % NKV) * TK * 128;
 #pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk)
             if (kk < ksteps)
-              ptx::mma_f16_ta(tmem + COL_O + qb * HD, tmem + COL_P + b * HD + kk * 8,
+              ptx::mma_f16_ta(tmem + COL_O + ob * HD, tmem + COL_P + b * HD + kk * 8,
                               desc_mnmajor_sw128(vb + kk * 2048), idPV, (ti | kk) > 0);
           ptx::mma_commit(&bars->pv_done[b]);
           ptx::mma_commit(&bars->kv_empty[c % NKV]);
         }
         // Q buffer and slot qb: every S of the item has been issued
         ptx::mma_commit(&bars->q_empty[qb]);
-        W = Wn;
       }
     mma_done:
       if (!ok) atomicExch(status, ST_ETIMEOUT);
@@ -449,29 +487,23 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
     bf16* og = reinterpret_cast<bf16*>(a.o);
     bool ok = true;
     uint32_t c = 0, qc = 0;
-    // An item's O is read out after the next item's first tile, by when its
-    // last P.V has long completed.
-    struct Pending {
-      bool on, row_ok;
-      int qb;
-      uint32_t cl;    // tile counter of the item's last tile
-      float l;
-      int64_t orow;
-    } pend = {false, false, 0, 0, 0.f, 0};
-    auto read_out = [&]() -> bool {
-      pend.on = false;
-      if (!ptx::mbar_wait(&bars->pv_done[pend.cl & 1], (pend.cl >> 1) & 1)) return false;
+    // With two O buffers an item's O is read out after the next item's first
+    // tile, by when its last P.V has long completed; with one, at its end.
+    // O buffer ob of the item whose last tile was cl: wait for its last P.V,
+    // release the buffer, write the row normalised by l (orow < 0: no row)
+    auto read_out = [&](int ob, uint32_t cl, float l, int64_t orow) -> bool {
+      if (!ptx::mbar_wait(&bars->pv_done[cl % NB], (cl / NB) & 1)) return false;
       ptx::tc_fence_after();
-      const uint32_t o_addr = tmem + lane_base + COL_O + pend.qb * HD;
+      const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD;
       uint32_t o0[32], o1[32];
       ST_TMEM_LD32(o_addr, o0);
       ST_TMEM_LD32(o_addr + 32, o1);
       ptx::tmem_wait_ld();
       ptx::tc_fence_before();
-      ptx::mbar_arrive(&bars->o_free[pend.qb]);
-      if (pend.row_ok) {
-        const float inv = pend.l > 0.f ? 1.f / pend.l : 0.f;
-        uint4* dst = reinterpret_cast<uint4*>(og + pend.orow * HD);
+      ptx::mbar_arrive(&bars->o_free[ob]);
+      if (orow >= 0) {
+        const float inv = l > 0.f ? 1.f / l : 0.f;
+        uint4* dst = reinterpret_cast<uint4*>(og + orow * HD);
 #pragma unroll
         for (int e = 0; e < 32; e += 8) {
           dst[e / 8] = make_uint4(pack_bf16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
@@ -487,28 +519,31 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
       }
       return true;
     };
+    bool pend_on = false;           // (two O buffers) the item read out after the next one's first tile
+    int pend_ob = 0;
+    uint32_t pend_cl = 0;
+    float pend_l = 0.f;
+    int64_t pend_orow = -1;
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
       const int qb = qc & 1;
       if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
-      const Work<MODE> W = slots[qb];
-      ptx::mbar_arrive(&bars->q_empty[qb]);
-      const int rr = W.row_base + r;
-      const int pos = rr / W.G, hh = rr % W.G;
-      bool row_ok = r < W.rows;
-      if (MODE == 0) row_ok = row_ok && (W.j0 + pos) < W.L;
+      // read in place; the slot is released at the item's end
+      const Work<MODE>& W = slots[qb];
+      const int pos = (W.row_base + r) / W.G;
 
       // O accumulates in TMEM (buffer qb); the running max m only moves when a
       // row's tile maximum exceeds it by more than 8 (a factor 256 in P), and
       // then the row's O is rescaled in place before the next P.V is issued.
       float m = -INFINITY, l = 0.f;
-      const uint32_t o_addr = tmem + lane_base + COL_O + qb * HD;
+      const int ob = qc % NB;
+      const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD;
       const int lim = MODE == 0 ? W.j0 + pos : pos;   // causal limit of this row
       for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
-        const int b = c & 1;
+        const int b = c % NB;
         const TileInfo T = W.tile(ti);
         const int nch = (T.kc + 31) >> 5;           // 32-key chunks any row can see
         const bool causal = (MODE == 0) || T.prompt;
-        if (!ptx::mbar_wait(&bars->s_full[b], (c >> 1) & 1)) { ok = false; break; }
+        if (!ptx::mbar_wait(&bars->s_full[b], (c / NB) & 1)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t sb = tmem + lane_base + b * TK;
         // the row's visible chunks of S into registers with one wait, then
@@ -521,14 +556,18 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
         ptx::tmem_wait_ld();
         ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->s_free[b]);
-        // invisible keys of this row (ragged tail, causal limit, chunks not
-        // loaded) become -inf
+        // invisible keys of this row (ragged tail, causal limit) in the loaded
+        // chunks become -inf
         int nvis = T.count;
         if (causal) nvis = min(nvis, lim - T.key0 + 1);
-        if (nvis < TK) {
 #pragma unroll
-          for (int k = 0; k < TK; ++k)
-            if (k >= nvis) v[k] = 0xFF800000u;
+        for (int ch = 0; ch < 4; ++ch) {
+          const int lo = nvis - 32 * ch;    // visible keys of this chunk
+          if (ch < nch && lo < 32) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j >= lo) v[32 * ch + j] = 0xFF800000u;
+          }
         }
         // E4M3 document tiles: one K and one V scale per 64-slot half of the tile
         float ks[2] = {1.f, 1.f}, vs[2] = {1.f, 1.f};
@@ -541,43 +580,33 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
             vs[1] = scp[3];
           }
         }
-        float mx;
-        {
-          float m4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        // row maximum of the scaled scores (a positive scale commutes with the max)
+        float cm[4];
 #pragma unroll
-          for (int ch = 0; ch < 4; ++ch) {
-            if (ch < nch) {
-#pragma unroll
-              for (int k = 32 * ch; k < 32 * ch + 32; k += 8) {
-                const float sc = ks[ch >> 1];
-                m4[(k >> 3) & 3] = max3(m4[(k >> 3) & 3],
-                                        max3(__uint_as_float(v[k]) * sc, __uint_as_float(v[k + 1]) * sc,
-                                             __uint_as_float(v[k + 2]) * sc),
-                                        max3(__uint_as_float(v[k + 3]) * sc, __uint_as_float(v[k + 4]) * sc,
-                                             max3(__uint_as_float(v[k + 5]) * sc,
-                                                  __uint_as_float(v[k + 6]) * sc,
-                                                  __uint_as_float(v[k + 7]) * sc)));
-              }
-            }
-          }
-          mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3])) * sl2;
-        }
+        for (int ch = 0; ch < 4; ++ch)
+          cm[ch] = ch < nch ? chunk_max(v + 32 * ch) * ks[ch >> 1] : -INFINITY;
+        const float mx = max3(cm[0], cm[1], fmaxf(cm[2], cm[3])) * sl2;
         const bool need = mx > m + 8.f;
         if (__any_sync(0xffffffffu, need)) {
           const float mn = need ? mx : m;
           const float alpha = need ? ex2(m - mn) : 1.f;
           if (ti > 0) {
             // O holds this item's earlier P.V products: scale the row in place
-            if (!ptx::mbar_wait(&bars->pv_done[(c - 1) & 1], ((c - 1) >> 1) & 1)) { ok = false; break; }
+            if (!ptx::mbar_wait(&bars->pv_done[(c - 1) % NB], ((c - 1) / NB) & 1)) { ok = false; break; }
             ptx::tc_fence_after();
+            const uint64_t a2 = f2pack(alpha, alpha);
 #pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
-              uint32_t o0[32];
-              ST_TMEM_LD32(o_addr + 32 * half, o0);
+            for (int part = 0; part < 4; ++part) {
+              uint32_t o0[16];
+              ST_TMEM_LD16(o_addr + 16 * part, o0);
               ptx::tmem_wait_ld();
 #pragma unroll
-              for (int e = 0; e < 32; ++e) o0[e] = __float_as_uint(__uint_as_float(o0[e]) * alpha);
-              ST_TMEM_ST32(o_addr + 32 * half, o0);
+              for (int e = 0; e < 16; e += 2) {
+                const uint64_t x = mul2((uint64_t)o0[e] | ((uint64_t)o0[e + 1] << 32), a2);
+                o0[e] = (uint32_t)x;
+                o0[e + 1] = (uint32_t)(x >> 32);
+              }
+              ST_TMEM_ST16(o_addr + 16 * part, o0);
             }
             ptx::tmem_wait_st();
           }
@@ -585,44 +614,73 @@ __global__ void __launch_bounds__(nthreads(FP8), 1)
           m = mn;
         }
         const float base = m == -INFINITY ? 0.f : m;
-        // the P buffer b was last read by the P.V of tile c - 2
-        if (c >= 2 && !ptx::mbar_wait(&bars->pv_done[b], ((c - 2) >> 1) & 1)) { ok = false; break; }
+        // the P buffer b was last read by the P.V of tile c - NB
+        if (c >= (uint32_t)NB && !ptx::mbar_wait(&bars->pv_done[b], ((c - NB) / NB) & 1)) { ok = false; break; }
         ptx::tc_fence_after();
         // probabilities of the visible chunks, packed in pairs (key 2j low, 2j+1
         // high), 16 TMEM columns per 32-key chunk
         const uint32_t pcol = tmem + lane_base + COL_P + b * HD;
-        float rs4[4] = {0.f, 0.f, 0.f, 0.f};
+        // p = 2^(s * mul - base), two keys per packed FP32 operation
+        const uint64_t nb2 = f2pack(-base, -base);
+        uint64_t rs2[2] = {0, 0};           // packed partial row sums (+0.0f lanes)
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
           if (ch < nch) {
-            const float mul = sl2 * ks[ch >> 1], vsc = vs[ch >> 1];
-            uint32_t pk[16];
+            const float mul = sl2 * ks[ch >> 1];
+            const uint64_t m2 = f2pack(mul, mul), vs2 = f2pack(vs[ch >> 1], vs[ch >> 1]);
 #pragma unroll
-            for (int k = 0; k < 32; k += 2) {
-              const float p0 = ex2(fmaf(__uint_as_float(v[32 * ch + k]), mul, -base));
-              const float p1 = ex2(fmaf(__uint_as_float(v[32 * ch + k + 1]), mul, -base));
-              rs4[(k >> 1) & 3] += p0 + p1;
-              pk[k >> 1] = FP8 ? pack_f16(p0 * vsc, p1 * vsc) : pack_bf16(p0, p1);
+            for (int h = 0; h < 2; ++h) {
+              uint32_t pk[8];
+#pragma unroll
+              for (int k = 0; k < 16; k += 2) {
+                const int kk = 32 * ch + 16 * h + k;
+                const uint64_t y = fma2((uint64_t)v[kk] | ((uint64_t)v[kk + 1] << 32), m2, nb2);
+                const uint64_t p = f2pack(ex2(f2lo(y)), ex2(f2hi(y)));
+                rs2[(k >> 1) & 1] = add2(rs2[(k >> 1) & 1], p);
+                if (FP8) {
+                  const uint64_t q = mul2(p, vs2);
+                  pk[k >> 1] = pack_f16(f2lo(q), f2hi(q));
+                } else {
+                  pk[k >> 1] = pack_bf16(f2lo(p), f2hi(p));
+                }
+              }
+              ST_TMEM_ST8(pcol + 16 * ch + 8 * h, pk);
             }
-            ST_TMEM_ST16(pcol + 16 * ch, pk);
           }
         }
-        l += (rs4[0] + rs4[1]) + (rs4[2] + rs4[3]);
+        {
+          const uint64_t t = add2(rs2[0], rs2[1]);
+          l += f2lo(t) + f2hi(t);
+        }
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->p_full[b]);
-        if (ti == 0 && pend.on && !(ok = read_out())) break;
+        if (NB == 2 && ti == 0 && pend_on && !(ok = read_out(pend_ob, pend_cl, pend_l, pend_orow))) break;
       }
       if (!ok) break;
-      pend.on = true;
-      pend.row_ok = row_ok;
-      pend.qb = qb;
-      pend.cl = c - 1;
-      pend.l = l;
-      if (MODE == 1) pend.orow = ((int64_t)W.i * a.P + pos) * a.hq + (int64_t)W.g * W.G + hh;
-      else pend.orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
+      // the output row of this thread (-1: past the item's rows)
+      int64_t orow = -1;
+      {
+        const int rr = W.row_base + r, hh = rr % W.G;
+        const bool row_ok = r < W.rows && (MODE == 1 || (W.j0 + pos) < W.L);
+        if (row_ok) {
+          if (MODE == 1) orow = ((int64_t)W.i * a.P + pos) * a.hq + (int64_t)W.g * W.G + hh;
+          else orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
+        }
+      }
+      ptx::mbar_arrive(&bars->q_empty[qb]);
+      if (NB == 1) {
+        // a single O buffer is read out at once
+        if (!(ok = read_out(ob, c - 1, l, orow))) break;
+      } else {
+        pend_on = true;
+        pend_ob = ob;
+        pend_cl = c - 1;
+        pend_l = l;
+        pend_orow = orow;
+      }
     }
-    if (ok && pend.on) ok = read_out();
+    if (ok && pend_on) ok = read_out(pend_ob, pend_cl, pend_l, pend_orow);
     if (!ok) atomicExch(status, ST_ETIMEOUT);
   }
   ptx::tc_fence_before();
@@ -743,7 +801,8 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   if (!ok) return ST_ECUDA;
   const int zb = (a.P * G + ROWS - 1) / ROWS;
   const int n_work = a.n * a.hkv * zb;
-  const int grid = n_work < sm_count() ? n_work : sm_count();
+  const int slots = sm_count() * ctas_per_sm(fp8);
+  const int grid = n_work < slots ? n_work : slots;
   if (fp8) {
     set_smem_attr<1, true>();
     k_attn_tc<1, true><<<grid, nthreads(true), smem_bytes(true), s>>>(a, a.order, n_work, zb, mq, mk,
@@ -768,7 +827,8 @@ int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int*
     return ST_ECUDA;
   set_smem_attr<0, false>();
   const int n_work = n_items * a.hkv;
-  const int grid = n_work < sm_count() ? n_work : sm_count();
+  const int slots = sm_count() * ctas_per_sm(false);
+  const int grid = n_work < slots ? n_work : slots;
   k_attn_tc<0, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, items, n_work, 1, mq, mk,
                                                                        mv, mk, mv, status);
   return ST_OK;
