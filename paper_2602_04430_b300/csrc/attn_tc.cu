@@ -64,7 +64,9 @@ constexpr uint32_t col_o(bool fp8) { return TK * nbuf(fp8); }
 constexpr uint32_t col_p(bool fp8) { return (TK + HD) * nbuf(fp8); }
 
 struct Bars {
-  uint64_t kv_full[NKV_MAX], kv_empty[NKV_MAX], s_full[2], s_free[2], p_full[2], pv_done[2], o_free[2];
+  // K and V halves of a stage fill and free separately: K after the tile's
+  // S = Q K^T, V after its P.V
+  uint64_t k_full[NKV_MAX], v_full[NKV_MAX], k_empty[NKV_MAX], v_empty[NKV_MAX], s_full[2], s_free[2], p_full[2], pv_done[2], o_free[2];
   uint64_t q_full[2], q_empty[2];
   uint64_t kvc_full[NKV_MAX], raw_full[2], raw_empty[2];   // E4M3: widened stages, raw code stages
   uint32_t tmem;
@@ -231,8 +233,10 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NKV; ++s) {
-      ptx::mbar_init(&bars->kv_full[s], 1);
-      ptx::mbar_init(&bars->kv_empty[s], 1);
+      ptx::mbar_init(&bars->k_full[s], 1);
+      ptx::mbar_init(&bars->v_full[s], 1);
+      ptx::mbar_init(&bars->k_empty[s], 1);
+      ptx::mbar_init(&bars->v_empty[s], 1);
       ptx::mbar_init(&bars->kvc_full[s], 64);
     }
     for (int s = 0; s < 2; ++s) {
@@ -267,11 +271,40 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
       ptx::tma_prefetch_desc(&tmK);
       ptx::tma_prefetch_desc(&tmV);
       int last_kv[NKV];
-      uint32_t n_tma[NKV];      // TMA fills of each stage (its kv_full completions)
+      uint32_t n_tma[NKV];      // TMA fills of each stage (its k_full / v_full completions)
       for (int s = 0; s < NKV; ++s) {
         last_kv[s] = -1;
         n_tma[s] = 0;
       }
+      // L2 prefetch cursor: walks the same (item, tile) sequence PF tiles ahead
+      // of the loads, so that a stage's TMA load, issued once the stage is
+      // free, finds its rows in L2
+      constexpr int PF = 4;
+      Work<MODE> PW;
+      int pw = blockIdx.x, pti = 0;
+      if (pw < n_work) PW.decode(a, items, pw, zb_count);
+      auto prefetch_next = [&]() {
+        if (pw >= n_work) return;
+        const TileInfo T = PW.tile(pti);
+        const int nbox = (T.kc + BOX - 1) / BOX;
+        for (int h = 0; h < nbox; ++h) {
+          if (T.prompt) {
+            const int y = (int)(PW.prompt_row0 + T.key0 + h * BOX);
+            ptx::tma_prefetch_l2_2d(&tmKp, PW.g * HD, y);
+            ptx::tma_prefetch_l2_2d(&tmVp, PW.g * HD, y);
+          } else {
+            const int y = (int)(PW.doc_row0 + T.key0 + h * BOX);
+            ptx::tma_prefetch_l2_2d(&tmK, 0, y);
+            ptx::tma_prefetch_l2_2d(&tmV, 0, y);
+          }
+        }
+        if (++pti == PW.n_tiles) {
+          pti = 0;
+          pw += gridDim.x;
+          if (pw < n_work) PW.decode(a, items, pw, zb_count);
+        }
+      };
+      for (int i = 0; i < PF; ++i) prefetch_next();
       bool ok = true;
       uint32_t c = 0, dc = 0, qc = 0;   // tile / E4M3 document-tile / item counters of this CTA
       int last_raw[2] = {-1, -1}, last_q[2] = {-1, -1};
@@ -291,6 +324,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
           const uint32_t u = c / NKV;
           const TileInfo T = W.tile(ti);
           const int nbox = (T.kc + BOX - 1) / BOX;
+          prefetch_next();
           if (FP8 && !T.prompt) {
             // raw codes into a raw stage; the widening warps fill K/V stage s
             const int rs = dc & 1;
@@ -306,28 +340,28 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
             ++dc;
             continue;
           }
-          if (!ptx::mbar_wait(&bars->kv_empty[s], (u & 1) ^ 1)) { ok = false; break; }
-          ptx::mbar_arrive_expect_tx(&bars->kv_full[s], nbox * 2 * BOX * 128);
           uint8_t* dk = smem + OFF_K + s * TK * 128;
           uint8_t* dv = smem + OFF_V + s * TK * 128;
-          for (int h = 0; h < nbox; ++h) {
-            if (T.prompt) {
-              const int y = (int)(W.prompt_row0 + T.key0 + h * BOX);
-              ptx::tma_load_2d(dk + h * BOX * 128, &tmKp, &bars->kv_full[s], W.g * HD, y);
-              ptx::tma_load_2d(dv + h * BOX * 128, &tmVp, &bars->kv_full[s], W.g * HD, y);
-            } else {
-              const int y = (int)(W.doc_row0 + T.key0 + h * BOX);
-              ptx::tma_load_2d(dk + h * BOX * 128, &tmK, &bars->kv_full[s], 0, y);
-              ptx::tma_load_2d(dv + h * BOX * 128, &tmV, &bars->kv_full[s], 0, y);
-            }
-          }
+          const int64_t y0 = (T.prompt ? W.prompt_row0 : W.doc_row0) + T.key0;
+          const int x0 = T.prompt ? W.g * HD : 0;
+          const CUtensorMap* mk = T.prompt ? &tmKp : &tmK;
+          const CUtensorMap* mv = T.prompt ? &tmVp : &tmV;
+          if (!ptx::mbar_wait(&bars->k_empty[s], (u & 1) ^ 1)) { ok = false; break; }
+          ptx::mbar_arrive_expect_tx(&bars->k_full[s], nbox * BOX * 128);
+          for (int h = 0; h < nbox; ++h)
+            ptx::tma_load_2d(dk + h * BOX * 128, mk, &bars->k_full[s], x0, (int)(y0 + h * BOX));
+          if (!ptx::mbar_wait(&bars->v_empty[s], (u & 1) ^ 1)) { ok = false; break; }
+          ptx::mbar_arrive_expect_tx(&bars->v_full[s], nbox * BOX * 128);
+          for (int h = 0; h < nbox; ++h)
+            ptx::tma_load_2d(dv + h * BOX * 128, mv, &bars->v_full[s], x0, (int)(y0 + h * BOX));
           last_kv[s] = (int)(n_tma[s] & 1);
           ++n_tma[s];
         }
       }
       // let every load this CTA issued land before it can exit
       for (int s = 0; s < NKV; ++s)
-        if (last_kv[s] >= 0 && !ptx::mbar_wait(&bars->kv_full[s], (uint32_t)last_kv[s], 100000000LL))
+        if (last_kv[s] >= 0 && (!ptx::mbar_wait(&bars->k_full[s], (uint32_t)last_kv[s], 100000000LL) ||
+                                !ptx::mbar_wait(&bars->v_full[s], (uint32_t)last_kv[s], 100000000LL)))
           ok = false;
       for (int s = 0; s < 2; ++s) {
         if (last_raw[s] >= 0 && !ptx::mbar_wait(&bars->raw_full[s], (uint32_t)last_raw[s], 100000000LL))
@@ -350,7 +384,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
         const TileInfo T = W.tile(ti);
         const bool widened = FP8 && !T.prompt;
         // each stage's two "full" barriers complete once per use of their kind
-        uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->kv_full[s];
+        uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->k_full[s];
         uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
         const uint32_t par = nuse & 1;
         ++nuse;
@@ -366,6 +400,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
           ptx::mma_f16(tmem + b * TK, ptx::desc_kmajor_sw128(sQ + k * 32),
                        ptx::desc_kmajor_sw128(kb + k * 32), idS, k > 0);
         ptx::mma_commit(&bars->s_full[b]);
+        ptx::mma_commit(&bars->k_empty[s]);
         return true;
       };
       constexpr uint32_t idPV =
@@ -389,8 +424,11 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
             if (!(ok = ptx::mbar_wait(&bars->q_full[qb ^ 1], ((qc + 1) >> 1) & 1))) goto mma_done;
             if (!(ok = issue_s(slots[qb ^ 1], 0, sQ0 + (qb ^ 1) * ROWS * 128, c + 1))) goto mma_done;
           }
-          const int b = c % NB, ob = qc % NB;
-          const int ksteps = ((W.tile(ti).kc + 31) >> 5) * 2;
+          const int b = c % NB, ob = qc % NB, s = c % NKV;
+          const TileInfo T = W.tile(ti);
+          const int ksteps = ((T.kc + 31) >> 5) * 2;
+          // TMA-filled V of this tile (the stage's latest TMA fill)
+          if ((!FP8 || T.prompt) && !(ok = ptx::mbar_wait(&bars->v_full[s], (n_tma[s] - 1) & 1))) goto mma_done;
           if (!(ok = ptx::mbar_wait(&bars->p_full[b], (c / NB) & 1))) goto mma_done;
           // the item's first P.V overwrites its O buffer: wait until the item NB
           // back has read it out
@@ -403,7 +441,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
               ptx::mma_f16_ta(tmem + COL_O + ob * HD, tmem + COL_P + b * HD + kk * 8,
                               desc_mnmajor_sw128(vb + kk * 2048), idPV, (ti | kk) > 0);
           ptx::mma_commit(&bars->pv_done[b]);
-          ptx::mma_commit(&bars->kv_empty[c % NKV]);
+          ptx::mma_commit(&bars->v_empty[s]);
         }
         // Q buffer and slot qb: every S of the item has been issued
         ptx::mma_commit(&bars->q_empty[qb]);
@@ -413,7 +451,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
       // every commit of this thread has landed once the last stages are released
       if (ok)
         for (uint32_t cc = c >= NKV ? c - NKV : 0; cc < c; ++cc)
-          if (!ptx::mbar_wait(&bars->kv_empty[cc % NKV], (cc / NKV) & 1, 100000000LL))
+          if (!ptx::mbar_wait(&bars->v_empty[cc % NKV], (cc / NKV) & 1, 100000000LL))
             atomicExch(status, ST_ETIMEOUT);
     }
     __syncwarp();
@@ -434,7 +472,8 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
         if (T.prompt) continue;
         const int s = c % NKV, rs = dc & 1;
         if (!ptx::mbar_wait(&bars->raw_full[rs], (dc >> 1) & 1)) { ok = false; break; }
-        if (!ptx::mbar_wait(&bars->kv_empty[s], ((c / NKV) & 1) ^ 1)) { ok = false; break; }
+        if (!ptx::mbar_wait(&bars->k_empty[s], ((c / NKV) & 1) ^ 1) ||
+            !ptx::mbar_wait(&bars->v_empty[s], ((c / NKV) & 1) ^ 1)) { ok = false; break; }
         const uint8_t* raw = smem + OFF_RAW + rs * RAW_BYTES;
 #pragma unroll
         for (int kv = 0; kv < 2; ++kv) {
