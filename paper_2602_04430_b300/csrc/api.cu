@@ -320,6 +320,18 @@ extern "C" int st_create(const st_model_cfg* cfg, const void* const* weights, vo
     return cleanup_fail(rc);
   }
   copy(ctx->rope, tab.data(), tab.size() * sizeof(float2));
+  // the same table position-fastest ([hd/2][max_pos]): the tcgen05 GEMM's
+  // epilogue reads one frequency for 32 consecutive rows in one coalesced load
+  {
+    std::vector<float2> tt(tab.size());
+    for (int p = 0; p < c.max_pos; ++p)
+      for (int i = 0; i < half; ++i) tt[(size_t)i * c.max_pos + p] = tab[(size_t)p * half + i];
+    if ((rc = dev_alloc(ctx, (void**)&ctx->rope_t, tt.size() * sizeof(float2)))) {
+      g_err = ctx->err;
+      return cleanup_fail(rc);
+    }
+    copy(ctx->rope_t, tt.data(), tt.size() * sizeof(float2));
+  }
   if ((rc = dev_alloc(ctx, (void**)&ctx->dstatus, sizeof(int32_t)))) {
     g_err = ctx->err;
     return cleanup_fail(rc);
@@ -346,6 +358,7 @@ extern "C" void st_destroy(st_ctx* ctx) {
     cudaFree(L.wd);
   }
   cudaFree(ctx->rope);
+  cudaFree(ctx->rope_t);
   cudaFree(ctx->dstatus);
   cudaFree(ctx->ws_build.p);
   cudaFree(ctx->ws_eval.p);
@@ -517,6 +530,8 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
       ep.kv_sr = c.hd;
       ep.pos = w.pos;
       ep.rope = ctx->rope;
+      ep.rope_t = ctx->rope_t;
+      ep.rope_np = c.max_pos;
       ep.hq = c.hq;
       ep.hkv = c.hkv;
       ep.hd = c.hd;
@@ -824,6 +839,8 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_
     ep.kv_sr = kd;
     ep.pos = w.pos;
     ep.rope = ctx->rope;
+    ep.rope_t = ctx->rope_t;
+    ep.rope_np = c.max_pos;
     ep.hq = c.hq;
     ep.hkv = c.hkv;
     ep.hd = c.hd;

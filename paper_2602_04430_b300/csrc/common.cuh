@@ -107,6 +107,7 @@ struct st_ctx {
   void* w_lm = nullptr;
   std::vector<st::LayerW> layers;
   float2* rope = nullptr;         // [max_pos][hd/2] (cos, sin)
+  float2* rope_t = nullptr;       // the same, [hd/2][max_pos]
   // workspaces
   st::DevBuf ws_build, ws_eval;
   int64_t build_rows_cap = 0, eval_rows_cap = 0;

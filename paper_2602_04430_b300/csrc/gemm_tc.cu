@@ -11,8 +11,10 @@
 //               on one lane, the tcgen05.mma issuer (M=128, N=256, K=16 steps).
 //   warps 2-9   epilogue: tcgen05.ld of the accumulator rows (warp w reads TMEM
 //               lanes 32*(w%4) .., warps w and w+4 split the tile's columns),
-//               fused epilogue (RoPE + Q/K/V scatter, residual add, SwiGLU)
-//               straight from registers to global memory.
+//               fused epilogue (RoPE + Q/K/V scatter, residual add, SwiGLU).
+//               A thread holds one row; each warp turns its 32 rows around in
+//               a 4 KB shared-memory buffer so that global loads and stores
+//               move whole 128-byte row segments (coalesced).
 // The two accumulators let the epilogue of tile i overlap the main loop of
 // tile i+1.  Every mbarrier wait is bounded; a timeout sets the status word.
 #include <cudaTypedefs.h>
@@ -27,17 +29,104 @@ constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NUM_THREADS = 320;   // producer, MMA, 8 epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int STG_BYTES = 4096;     // per epilogue warp: 32 rows x 128 B
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 8 * STG_BYTES + 1024 + 256;
 
 struct Bars {
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   uint32_t tmem_base;
 };
 
-// Columns [half * BN/2, (half + 1) * BN/2) of the tile for one accumulator row
+// Staging layouts (16-byte chunk j of row r), conflict-free for both the
+// row-per-thread side and the row-segment-per-8-threads side.
+__device__ __forceinline__ uint32_t sw128(int r, int j) {
+  return (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4));
+}
+__device__ __forceinline__ uint32_t sw64(int r, int j) {
+  return (uint32_t)(r * 64 + ((j ^ ((r >> 1) & 3)) << 4));
+}
+// 32 rows x 128 B (or 64 B) from the staging buffer to dst + r * stride; rows
+// r >= nrows are past the matrix and skipped.
+__device__ __forceinline__ void copy_out128(const uint8_t* st, char* dst, int64_t stride, int nrows,
+                                            int lane) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = (lane >> 3) + 4 * i, j = lane & 7;
+    if (r < nrows)
+      *reinterpret_cast<uint4*>(dst + r * stride + j * 16) = *reinterpret_cast<const uint4*>(st + sw128(r, j));
+  }
+}
+__device__ __forceinline__ void copy_out64(const uint8_t* st, char* dst, int64_t stride, int nrows,
+                                           int lane) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = (lane >> 2) + 8 * i, j = lane & 3;
+    if (r < nrows)
+      *reinterpret_cast<uint4*>(dst + r * stride + j * 16) = *reinterpret_cast<const uint4*>(st + sw64(r, j));
+  }
+}
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if (F16) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// One head (64 columns) of the QKV projection for the warp's 32 rows: RoPE on
+// Q and K columns, then the 16-bit head row to Q or to the K / V cache planes.
+template <bool F16>
+__device__ __forceinline__ void epi_qkv_head(const EpiParams& ep, uint8_t* st, float (&v)[64], int row,
+                                             int row0, int nrows, int col0, int lane, int M) {
+  const int qcols = ep.hq * 64, kcols = ep.hkv * 64;
+  if (col0 < qcols + kcols) {
+    const int pos = row < M ? ep.pos[row] : 0;
+    const float2* tab = ep.rope_t + pos;
+    // eight frequencies per group: bounds the table loads in flight (registers)
+#pragma unroll
+    for (int i0 = 0; i0 < 32; i0 += 8) {
+      float2 cs[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) cs[i] = tab[(int64_t)(i0 + i) * ep.rope_np];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float a = v[i0 + i], b = v[i0 + i + 32];
+        v[i0 + i] = a * cs[i].x - b * cs[i].y;
+        v[i0 + i + 32] = b * cs[i].x + a * cs[i].y;
+      }
+      asm volatile("" ::: "memory");
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    *reinterpret_cast<uint4*>(st + sw128(lane, j)) =
+        make_uint4(pack2<F16>(v[8 * j], v[8 * j + 1]), pack2<F16>(v[8 * j + 2], v[8 * j + 3]),
+                   pack2<F16>(v[8 * j + 4], v[8 * j + 5]), pack2<F16>(v[8 * j + 6], v[8 * j + 7]));
+  __syncwarp();
+  char* dst;
+  int64_t stride;
+  if (col0 < qcols) {
+    dst = reinterpret_cast<char*>(ep.q) + ((int64_t)row0 * qcols + col0) * 2;
+    stride = (int64_t)qcols * 2;
+  } else {
+    const bool isk = col0 < qcols + kcols;
+    const int head = (col0 - qcols - (isk ? 0 : kcols)) / 64;
+    dst = reinterpret_cast<char*>(isk ? ep.kbase : ep.vbase) +
+          ((int64_t)head * ep.kv_sg + (int64_t)row0 * ep.kv_sr) * 2;
+    stride = ep.kv_sr * 2;
+  }
+  copy_out128(st, dst, stride, nrows, lane);
+  __syncwarp();
+}
+
+// Columns [half * BN/2, (half + 1) * BN/2) of the tile for the warp's 32 rows
 // (SwiGLU: gate columns [half*64, half*64 + 64) with their up columns).
-__device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int n0,
-                                              uint32_t taddr, int M, int half) {
+__device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, int row0, int n0,
+                                              uint32_t taddr, int M, int half, int lane) {
+  const int row = row0 + lane;
+  const int nrows = M - row0 < 32 ? M - row0 : 32;
   const float inv = row < M ? row_inv_rms(ep, row) : 1.f;
   if (ep.mode == EPI_SWIGLU) {
     // columns [0,128) are gate, [128,256) the matching up projections
@@ -47,18 +136,83 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int 
       ST_TMEM_LD32(taddr + j, g);
       ST_TMEM_LD32(taddr + BN / 2 + j, u);
       ptx::tmem_wait_ld();
-      if (row < M) {
-        float gf[32], uf[32];
+      float hv[32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          gf[e] = __uint_as_float(g[e]) * inv;
-          uf[e] = __uint_as_float(u[e]) * inv;
-        }
-        epilogue_swiglu<bf16, 32>(ep, row, n0 / 2 + j, gf, uf);
+      for (int e = 0; e < 32; ++e) hv[e] = silu_f(__uint_as_float(g[e]) * inv) * (__uint_as_float(u[e]) * inv);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(st + sw64(lane, q)) =
+            make_uint4(pack2<false>(hv[8 * q], hv[8 * q + 1]), pack2<false>(hv[8 * q + 2], hv[8 * q + 3]),
+                       pack2<false>(hv[8 * q + 4], hv[8 * q + 5]), pack2<false>(hv[8 * q + 6], hv[8 * q + 7]));
+      __syncwarp();
+      copy_out64(st, reinterpret_cast<char*>(ep.h) + ((int64_t)row0 * ep.ld + n0 / 2 + j) * 2,
+                 ep.ld * 2, nrows, lane);
+      __syncwarp();
+    }
+  } else if (ep.mode == EPI_QKV) {
+#pragma unroll 1
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 64) {
+      uint32_t r[64];
+      uint32_t* r2 = r + 32;
+      ST_TMEM_LD32(taddr + c, r);
+      ST_TMEM_LD32(taddr + c + 32, r2);
+      ptx::tmem_wait_ld();
+      float v[64];
+#pragma unroll
+      for (int e = 0; e < 64; ++e) v[e] = __uint_as_float(r[e]) * inv;
+      if (ep.qkv_f16) epi_qkv_head<true>(ep, st, v, row, row0, nrows, n0 + c, lane, M);
+      else epi_qkv_head<false>(ep, st, v, row, row0, nrows, n0 + c, lane, M);
+    }
+  } else if (ep.mode == EPI_RESID) {
+    // x[row*row_mul + row_add] += acc, 32 columns at a time through the
+    // staging buffer (coalesced float32 read-modify-write); xb = bf16(x)
+    const int64_t xs = (int64_t)ep.row_mul * ep.ld * 4;   // byte stride of the warp's x rows
+    char* xrow0 = reinterpret_cast<char*>(ep.x) + ((int64_t)row0 * ep.row_mul + ep.row_add) * ep.ld * 4;
+    float ss = 0.f;
+#pragma unroll 1
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+      uint32_t r[32];
+      ST_TMEM_LD32(taddr + c, r);
+      char* xc = xrow0 + (int64_t)(n0 + c) * 4;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int rr = (lane >> 3) + 4 * i, j = lane & 7;
+        if (rr < nrows)
+          *reinterpret_cast<uint4*>(st + sw128(rr, j)) = *reinterpret_cast<const uint4*>(xc + rr * xs + j * 16);
+      }
+      ptx::tmem_wait_ld();
+      __syncwarp();
+      float nv[32];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float4 o = *reinterpret_cast<const float4*>(st + sw128(lane, j));
+        o.x += __uint_as_float(r[4 * j]) * inv;
+        o.y += __uint_as_float(r[4 * j + 1]) * inv;
+        o.z += __uint_as_float(r[4 * j + 2]) * inv;
+        o.w += __uint_as_float(r[4 * j + 3]) * inv;
+        nv[4 * j] = o.x; nv[4 * j + 1] = o.y; nv[4 * j + 2] = o.z; nv[4 * j + 3] = o.w;
+        ss += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+        *reinterpret_cast<float4*>(st + sw128(lane, j)) = o;
+      }
+      __syncwarp();
+      copy_out128(st, xc, xs, nrows, lane);
+      __syncwarp();
+      if (ep.xb != nullptr) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(st + sw64(lane, q)) =
+              make_uint4(pack2<false>(nv[8 * q], nv[8 * q + 1]), pack2<false>(nv[8 * q + 2], nv[8 * q + 3]),
+                         pack2<false>(nv[8 * q + 4], nv[8 * q + 5]), pack2<false>(nv[8 * q + 6], nv[8 * q + 7]));
+        __syncwarp();
+        copy_out64(st, reinterpret_cast<char*>(ep.xb) + ((int64_t)row0 * ep.N + n0 + c) * 2,
+                   (int64_t)ep.N * 2, nrows, lane);
+        __syncwarp();
       }
     }
+    if (ep.ssq_out != nullptr && row < M)
+      ep.ssq_out[(int64_t)row * (ep.N / 128) + (n0 + half * (BN / 2)) / 128] = ss;
   } else {
-    float ss = 0.f;
+    // EPI_STORE_F32 (self-test path): straight from the row's registers
 #pragma unroll 1
     for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 64) {
       uint32_t r[64];
@@ -67,14 +221,13 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, int row, int 
       ST_TMEM_LD32(taddr + c + 32, r2);
       ptx::tmem_wait_ld();
       if (row < M) {
-        float v[64];
+        float* o = ep.out + (int64_t)row * ep.ld + n0 + c;
 #pragma unroll
-        for (int e = 0; e < 64; ++e) v[e] = __uint_as_float(r[e]);
-        ss += epilogue_apply<bf16, 64>(ep, row, n0 + c, v, inv);
+        for (int e = 0; e < 64; e += 4)
+          *reinterpret_cast<float4*>(o + e) = make_float4(__uint_as_float(r[e]), __uint_as_float(r[e + 1]),
+                                                          __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
       }
     }
-    if (ep.mode == EPI_RESID && ep.ssq_out != nullptr && row < M)
-      ep.ssq_out[(int64_t)row * (ep.N / 128) + (n0 + half * (BN / 2)) / 128] = ss;
   }
 }
 
@@ -86,7 +239,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  Bars* bars = reinterpret_cast<Bars*>(smem + STAGES * STAGE_BYTES);
+  uint8_t* stg = smem + STAGES * STAGE_BYTES;   // 8 epilogue staging buffers
+  Bars* bars = reinterpret_cast<Bars*>(stg + 8 * STG_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m_blocks = (M + BM - 1) / BM, n_blocks = N / BN;
   const int tiles = m_blocks * n_blocks, nk = K / BK;
@@ -181,9 +335,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       ptx::tc_fence_after();
       const int mb = tile / n_blocks, nb = tile % n_blocks;
-      const int row = mb * BM + quarter * 32 + lane;
+      const int row0 = mb * BM + quarter * 32;
       const uint32_t taddr = tmem + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
-      epilogue_tile(ep, row, nb * BN, taddr, M, half);
+      epilogue_tile(ep, stg + (warp - 2) * STG_BYTES, row0, nb * BN, taddr, M, half, lane);
       ptx::tc_fence_before();
       ptx::mbar_arrive(&bars->tempty[buf]);
     }

@@ -31,6 +31,8 @@ struct EpiParams {
   int64_t kv_sg = 0, kv_sr = 0;
   const int32_t* pos = nullptr;   // [M] RoPE position of each row
   const float2* rope = nullptr;   // [max_pos][hd/2] (cos, sin)
+  const float2* rope_t = nullptr; // the same, [hd/2][rope_np] (tcgen05 GEMM)
+  int rope_np = 0;
   int hq = 0, hkv = 0, hd = 0;
   // EPI_RESID: x[row*ld + col] += acc (float32 residual stream)
   float* x = nullptr;
