@@ -373,84 +373,103 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
     }
   } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issue
-    // One stream of tiles over the CTA's items: S of tile c + 1 (which may be
-    // the next item's first) is issued before P.V of tile c, so the softmax
-    // never waits for an S at an item boundary.
+    // Two cursors walk the CTA's (item, tile) sequence: the S cursor issues
+    // S = Q K^T of tile cs, the P.V cursor issues P.V of tile cp (cp <= cs).
+    // Each step issues whichever is ready, tested without blocking, so that a
+    // late K of the next tile never holds back the P.V of the current one.
     if (lane == 0) {
-      bool ok = true;
-      uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};
-      auto issue_s = [&](const Work<MODE>& W, int ti, uint32_t sQ, uint32_t cc) -> bool {
-        const int s = cc % NKV, b = cc % NB;
-        const TileInfo T = W.tile(ti);
-        const bool widened = FP8 && !T.prompt;
-        // each stage's two "full" barriers complete once per use of their kind
-        uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->k_full[s];
-        uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
-        const uint32_t par = nuse & 1;
-        ++nuse;
-        if (!ptx::mbar_wait(fb, par)) return false;
-        if (!ptx::mbar_wait(&bars->s_free[b], ((cc / NB) & 1) ^ 1)) return false;
-        ptx::tc_fence_after();
-        // E4M3 KV runs the products in f16 (codes widen exactly; scales act in f32)
-        const int n = ((T.kc + 31) >> 5) * 32;
-        const uint32_t idS = FP8 ? ptx::idesc_f16_f32(ROWS, n) : ptx::idesc_bf16_f32(ROWS, n);
-        const uint32_t kb = sK0 + s * TK * 128;
-#pragma unroll
-        for (int k = 0; k < HD / 16; ++k)
-          ptx::mma_f16(tmem + b * TK, ptx::desc_kmajor_sw128(sQ + k * 32),
-                       ptx::desc_kmajor_sw128(kb + k * 32), idS, k > 0);
-        ptx::mma_commit(&bars->s_full[b]);
-        ptx::mma_commit(&bars->k_empty[s]);
-        return true;
-      };
       constexpr uint32_t idPV =
           (FP8 ? ptx::idesc_f16_f32(ROWS, HD) : ptx::idesc_bf16_f32(ROWS, HD)) | (1u << 16);
-      uint32_t c = 0, qc = 0;
-      // decoded items are read in place: a slot is rewritten only after this
-      // thread's commit at the end of its item
-      if (blockIdx.x < n_work) {
-        if (!(ok = ptx::mbar_wait(&bars->q_full[0], 0))) goto mma_done;
-        if (!(ok = issue_s(slots[0], 0, sQ0, 0))) goto mma_done;
-      }
-      for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++qc) {
-        const int qb = qc & 1;
-        const bool has_next = w + (int)gridDim.x < n_work;
-        const Work<MODE>& W = slots[qb];
-        for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
-          if (ti + 1 < W.n_tiles) {
-            if (!(ok = issue_s(W, ti + 1, sQ0 + qb * ROWS * 128, c + 1))) goto mma_done;
-          } else if (has_next) {
-            // the next item's decoded slot and Q
-            if (!(ok = ptx::mbar_wait(&bars->q_full[qb ^ 1], ((qc + 1) >> 1) & 1))) goto mma_done;
-            if (!(ok = issue_s(slots[qb ^ 1], 0, sQ0 + (qb ^ 1) * ROWS * 128, c + 1))) goto mma_done;
-          }
-          const int b = c % NB, ob = qc % NB, s = c % NKV;
-          const TileInfo T = W.tile(ti);
-          const int ksteps = ((T.kc + 31) >> 5) * 2;
-          // TMA-filled V of this tile (the stage's latest TMA fill)
-          if ((!FP8 || T.prompt) && !(ok = ptx::mbar_wait(&bars->v_full[s], (n_tma[s] - 1) & 1))) goto mma_done;
-          if (!(ok = ptx::mbar_wait(&bars->p_full[b], (c / NB) & 1))) goto mma_done;
-          // the item's first P.V overwrites its O buffer: wait until the item NB
-          // back has read it out
-          if (ti == 0 && !(ok = ptx::mbar_wait(&bars->o_free[ob], ((qc / NB) & 1) ^ 1))) goto mma_done;
-          ptx::tc_fence_after();
-          const uint32_t vb = sV0 + (c % NKV) * TK * 128;
+      bool ok = true;
+      uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};   // fills of each stage by kind (parities)
+      uint32_t cs = 0, cp = 0;                     // tiles whose S / P.V has been issued
+      int sw = blockIdx.x, sti = 0;                // S cursor: work item, tile
+      uint32_t sq = 0;                             //   and its item counter
+      bool s_have = false;                         //   its item's slot and Q have landed
+      int pw = blockIdx.x, pti = 0;                // P.V cursor
+      uint32_t pq = 0;
+      long long t_last = clock64();
+      while (pw < n_work) {
+        bool progressed = false;
+        // ---- S of tile cs (the single S buffer: at most one S ahead of the P.V)
+        if (sw < n_work && cs <= cp + (uint32_t)NB) {
+          const int qb = sq & 1;
+          if (!s_have) s_have = ptx::mbar_test(&bars->q_full[qb], (sq >> 1) & 1);
+          if (s_have) {
+            const Work<MODE>& W = slots[qb];
+            const int s = cs % NKV, b = cs % NB;
+            const TileInfo T = W.tile(sti);
+            const bool widened = FP8 && !T.prompt;
+            uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->k_full[s];
+            uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
+            if (ptx::mbar_test(fb, nuse & 1) && ptx::mbar_test(&bars->s_free[b], ((cs / NB) & 1) ^ 1)) {
+              ++nuse;
+              ptx::tc_fence_after();
+              // E4M3 KV runs the products in f16 (codes widen exactly; scales act in f32)
+              const int n = ((T.kc + 31) >> 5) * 32;
+              const uint32_t idS = FP8 ? ptx::idesc_f16_f32(ROWS, n) : ptx::idesc_bf16_f32(ROWS, n);
+              const uint32_t sQ = sQ0 + qb * ROWS * 128, kb = sK0 + s * TK * 128;
 #pragma unroll
-          for (int kk = 0; kk < TK / 16; ++kk)
-            if (kk < ksteps)
-              ptx::mma_f16_ta(tmem + COL_O + ob * HD, tmem + COL_P + b * HD + kk * 8,
-                              desc_mnmajor_sw128(vb + kk * 2048), idPV, (ti | kk) > 0);
-          ptx::mma_commit(&bars->pv_done[b]);
-          ptx::mma_commit(&bars->v_empty[s]);
+              for (int k = 0; k < HD / 16; ++k)
+                ptx::mma_f16(tmem + b * TK, ptx::desc_kmajor_sw128(sQ + k * 32),
+                             ptx::desc_kmajor_sw128(kb + k * 32), idS, k > 0);
+              ptx::mma_commit(&bars->s_full[b]);
+              ptx::mma_commit(&bars->k_empty[s]);
+              ++cs;
+              if (++sti == W.n_tiles) {
+                sti = 0;
+                sw += gridDim.x;
+                ++sq;
+                s_have = false;
+              }
+              progressed = true;
+            }
+          }
         }
-        // Q buffer and slot qb: every S of the item has been issued
-        ptx::mma_commit(&bars->q_empty[qb]);
+        // ---- P.V of tile cp
+        if (cp < cs) {
+          const int qb = pq & 1, ob = pq % NB;
+          const Work<MODE>& W = slots[qb];
+          const int b = cp % NB, s = cp % NKV;
+          const TileInfo T = W.tile(pti);
+          const bool tma_v = !FP8 || T.prompt;
+          // the stage's latest TMA fill is this tile's when the tile is TMA-filled
+          if ((!tma_v || ptx::mbar_test(&bars->v_full[s], (n_tma[s] - 1) & 1)) &&
+              ptx::mbar_test(&bars->p_full[b], (cp / NB) & 1) &&
+              (pti != 0 || ptx::mbar_test(&bars->o_free[ob], ((pq / NB) & 1) ^ 1))) {
+            ptx::tc_fence_after();
+            const int ksteps = ((T.kc + 31) >> 5) * 2;
+            const uint32_t vb = sV0 + s * TK * 128;
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; ++kk)
+              if (kk < ksteps)
+                ptx::mma_f16_ta(tmem + COL_O + ob * HD, tmem + COL_P + b * HD + kk * 8,
+                                desc_mnmajor_sw128(vb + kk * 2048), idPV, (pti | kk) > 0);
+            ptx::mma_commit(&bars->pv_done[b]);
+            ptx::mma_commit(&bars->v_empty[s]);
+            ++cp;
+            if (++pti == W.n_tiles) {
+              // the item's last MMA: its Q buffer and decoded slot (which both
+              // cursors read) may be refilled once it completes
+              ptx::mma_commit(&bars->q_empty[qb]);
+              pti = 0;
+              pw += gridDim.x;
+              ++pq;
+            }
+            progressed = true;
+          }
+        }
+        if (progressed) {
+          t_last = clock64();
+        } else if (clock64() - t_last > 4000000000LL) {
+          ok = false;
+          break;
+        }
       }
-    mma_done:
       if (!ok) atomicExch(status, ST_ETIMEOUT);
       // every commit of this thread has landed once the last stages are released
       if (ok)
-        for (uint32_t cc = c >= NKV ? c - NKV : 0; cc < c; ++cc)
+        for (uint32_t cc = cp >= NKV ? cp - NKV : 0; cc < cp; ++cc)
           if (!ptx::mbar_wait(&bars->v_empty[cc % NKV], (cc / NKV) & 1, 100000000LL))
             atomicExch(status, ST_ETIMEOUT);
     }
