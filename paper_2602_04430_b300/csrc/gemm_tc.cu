@@ -123,12 +123,30 @@ __device__ __forceinline__ void epi_qkv_head(const EpiParams& ep, uint8_t* st, f
 
 // Columns [half * BN/2, (half + 1) * BN/2) of the tile for the warp's 32 rows
 // (SwiGLU: gate columns [half*64, half*64 + 64) with their up columns).
+// Residual epilogue: the warp's x rows of 32 columns at col, as the coalesced
+// 16-byte pieces this lane moves (row (lane >> 3) + 4 i, piece lane & 7).
+__device__ __forceinline__ void resid_load(const EpiParams& ep, uint4 (&pre)[8], int row0, int nrows,
+                                           int col, int lane) {
+  const int64_t xs = (int64_t)ep.row_mul * ep.ld * 4;
+  const char* xc = reinterpret_cast<const char*>(ep.x) +
+                   ((int64_t)row0 * ep.row_mul + ep.row_add) * ep.ld * 4 + (int64_t)col * 4;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int rr = (lane >> 3) + 4 * i, j = lane & 7;
+    if (rr < nrows) pre[i] = *reinterpret_cast<const uint4*>(xc + rr * xs + j * 16);
+  }
+}
+
+// pre: for EPI_RESID, the tile's first x chunk, loaded before the accumulator
+// was ready (resid_load at column n0 + half * BN/2).
+template <int EPI>
 __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, int row0, int n0,
-                                              uint32_t taddr, int M, int half, int lane) {
+                                              uint32_t taddr, int M, int half, int lane,
+                                              uint4 (&pre)[8]) {
   const int row = row0 + lane;
   const int nrows = M - row0 < 32 ? M - row0 : 32;
   const float inv = row < M ? row_inv_rms(ep, row) : 1.f;
-  if (ep.mode == EPI_SWIGLU) {
+  if (EPI == EPI_SWIGLU) {
     // columns [0,128) are gate, [128,256) the matching up projections
 #pragma unroll 1
     for (int j = half * (BN / 4); j < (half + 1) * (BN / 4); j += 32) {
@@ -149,7 +167,7 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
                  ep.ld * 2, nrows, lane);
       __syncwarp();
     }
-  } else if (ep.mode == EPI_QKV) {
+  } else if (EPI == EPI_QKV) {
 #pragma unroll 1
     for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 64) {
       uint32_t r[64];
@@ -163,9 +181,10 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
       if (ep.qkv_f16) epi_qkv_head<true>(ep, st, v, row, row0, nrows, n0 + c, lane, M);
       else epi_qkv_head<false>(ep, st, v, row, row0, nrows, n0 + c, lane, M);
     }
-  } else if (ep.mode == EPI_RESID) {
+  } else if (EPI == EPI_RESID) {
     // x[row*row_mul + row_add] += acc, 32 columns at a time through the
-    // staging buffer (coalesced float32 read-modify-write); xb = bf16(x)
+    // staging buffer (coalesced float32 read-modify-write, the next chunk's x
+    // loads in flight meanwhile); xb = bf16(x)
     const int64_t xs = (int64_t)ep.row_mul * ep.ld * 4;   // byte stride of the warp's x rows
     char* xrow0 = reinterpret_cast<char*>(ep.x) + ((int64_t)row0 * ep.row_mul + ep.row_add) * ep.ld * 4;
     float ss = 0.f;
@@ -177,12 +196,12 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int rr = (lane >> 3) + 4 * i, j = lane & 7;
-        if (rr < nrows)
-          *reinterpret_cast<uint4*>(st + sw128(rr, j)) = *reinterpret_cast<const uint4*>(xc + rr * xs + j * 16);
+        if (rr < nrows) *reinterpret_cast<uint4*>(st + sw128(rr, j)) = pre[i];
       }
+      if (c + 32 < (half + 1) * (BN / 2)) resid_load(ep, pre, row0, nrows, n0 + c + 32, lane);
       ptx::tmem_wait_ld();
       __syncwarp();
-      float nv[32];
+      uint32_t xw[16];   // bf16(x) of the row, packed in pairs
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         float4 o = *reinterpret_cast<const float4*>(st + sw128(lane, j));
@@ -190,7 +209,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
         o.y += __uint_as_float(r[4 * j + 1]) * inv;
         o.z += __uint_as_float(r[4 * j + 2]) * inv;
         o.w += __uint_as_float(r[4 * j + 3]) * inv;
-        nv[4 * j] = o.x; nv[4 * j + 1] = o.y; nv[4 * j + 2] = o.z; nv[4 * j + 3] = o.w;
+        xw[2 * j] = pack2<false>(o.x, o.y);
+        xw[2 * j + 1] = pack2<false>(o.z, o.w);
         ss += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
         *reinterpret_cast<float4*>(st + sw128(lane, j)) = o;
       }
@@ -201,8 +221,7 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           *reinterpret_cast<uint4*>(st + sw64(lane, q)) =
-              make_uint4(pack2<false>(nv[8 * q], nv[8 * q + 1]), pack2<false>(nv[8 * q + 2], nv[8 * q + 3]),
-                         pack2<false>(nv[8 * q + 4], nv[8 * q + 5]), pack2<false>(nv[8 * q + 6], nv[8 * q + 7]));
+              make_uint4(xw[4 * q], xw[4 * q + 1], xw[4 * q + 2], xw[4 * q + 3]);
         __syncwarp();
         copy_out64(st, reinterpret_cast<char*>(ep.xb) + ((int64_t)row0 * ep.N + n0 + c) * 2,
                    (int64_t)ep.N * 2, nrows, lane);
@@ -231,6 +250,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
   }
 }
 
+// One instantiation per epilogue (the launch's EpiParams::mode).
+template <int EPI>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int M, int N, int K, EpiParams ep, int* status) {
@@ -326,9 +347,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int quarter = warp & 3;          // TMEM lanes 32*quarter .. (warp % 4 rule)
     const int half = (warp - 2) >> 2;      // which half of the tile's columns
     int it = 0;
+    uint4 pre[8];
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
       const int buf = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
+      if (EPI == EPI_RESID) {
+        // the residual rows do not depend on the product: fetch the first
+        // chunk while the main loop still runs
+        const int r0 = (tile / n_blocks) * BM + quarter * 32;
+        resid_load(ep, pre, r0, M - r0 < 32 ? M - r0 : 32, (tile % n_blocks) * BN + half * (BN / 2), lane);
+      }
       if (!ptx::mbar_wait(&bars->tfull[buf], use & 1)) {
         atomicExch(status, ST_ETIMEOUT);
         break;
@@ -337,7 +365,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int mb = tile / n_blocks, nb = tile % n_blocks;
       const int row0 = mb * BM + quarter * 32;
       const uint32_t taddr = tmem + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
-      epilogue_tile(ep, stg + (warp - 2) * STG_BYTES, row0, nb * BN, taddr, M, half, lane);
+      epilogue_tile<EPI>(ep, stg + (warp - 2) * STG_BYTES, row0, nb * BN, taddr, M, half, lane, pre);
       ptx::tc_fence_before();
       ptx::mbar_arrive(&bars->tempty[buf]);
     }
@@ -402,12 +430,20 @@ int gemm_tc(const bf16* A, const bf16* W, int M, int N, int K, const EpiParams& 
     return ST_ECUDA;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<EPI_QKV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<EPI_SWIGLU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<EPI_STORE_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     attr = true;
   }
   const int tiles = ((M + BM - 1) / BM) * (N / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  k_gemm_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status);
+  switch (ep.mode) {
+    case EPI_QKV: k_gemm_tc<EPI_QKV><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
+    case EPI_RESID: k_gemm_tc<EPI_RESID><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
+    case EPI_SWIGLU: k_gemm_tc<EPI_SWIGLU><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
+    default: k_gemm_tc<EPI_STORE_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
+  }
   return ST_OK;
 }
 
