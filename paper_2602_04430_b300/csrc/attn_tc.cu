@@ -113,15 +113,17 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
-// Maximum of the 32 scores of one chunk, as a tree of 3-input maxima.
+// Maximum of the 32 scores of one chunk: four chains of 3-input maxima (few
+// live temporaries next to the row's 128 scores).
 __device__ __forceinline__ float chunk_max(const uint32_t* v) {
-  float t[11];
+  float m[4];
 #pragma unroll
-  for (int i = 0; i < 10; ++i)
-    t[i] = max3(__uint_as_float(v[3 * i]), __uint_as_float(v[3 * i + 1]), __uint_as_float(v[3 * i + 2]));
-  t[10] = fmaxf(__uint_as_float(v[30]), __uint_as_float(v[31]));
-  const float u0 = max3(t[0], t[1], t[2]), u1 = max3(t[3], t[4], t[5]), u2 = max3(t[6], t[7], t[8]);
-  return max3(max3(u0, u1, u2), t[9], t[10]);
+  for (int q = 0; q < 4; ++q) m[q] = fmaxf(__uint_as_float(v[8 * q]), __uint_as_float(v[8 * q + 1]));
+#pragma unroll
+  for (int k = 2; k < 8; k += 2)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) m[q] = max3(m[q], __uint_as_float(v[8 * q + k]), __uint_as_float(v[8 * q + k + 1]));
+  return fmaxf(max3(m[0], m[1], m[2]), m[3]);
 }
 __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
   __half2 v = __floats2half2_rn(lo, hi);
@@ -553,26 +555,26 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
       if (!ptx::mbar_wait(&bars->pv_done[cl % NB], (cl / NB) & 1)) return false;
       ptx::tc_fence_after();
       const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD;
-      uint32_t o0[32], o1[32];
-      ST_TMEM_LD32(o_addr, o0);
-      ST_TMEM_LD32(o_addr + 32, o1);
-      ptx::tmem_wait_ld();
-      ptx::tc_fence_before();
-      ptx::mbar_arrive(&bars->o_free[ob]);
-      if (orow >= 0) {
-        const float inv = l > 0.f ? 1.f / l : 0.f;
-        uint4* dst = reinterpret_cast<uint4*>(og + orow * HD);
+      const float inv = l > 0.f ? 1.f / l : 0.f;
+      uint4* dst = reinterpret_cast<uint4*>(og + (orow >= 0 ? orow : 0) * HD);
+      // two 32-column halves (the buffer is released once both are loaded)
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        uint32_t o0[32];
+        ST_TMEM_LD32(o_addr + 32 * h, o0);
+        ptx::tmem_wait_ld();
+        if (h == 1) {
+          ptx::tc_fence_before();
+          ptx::mbar_arrive(&bars->o_free[ob]);
+        }
+        if (orow >= 0) {
 #pragma unroll
-        for (int e = 0; e < 32; e += 8) {
-          dst[e / 8] = make_uint4(pack_bf16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
-                                  pack_bf16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
-                                  pack_bf16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
-                                  pack_bf16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
-          dst[4 + e / 8] =
-              make_uint4(pack_bf16(__uint_as_float(o1[e]) * inv, __uint_as_float(o1[e + 1]) * inv),
-                         pack_bf16(__uint_as_float(o1[e + 2]) * inv, __uint_as_float(o1[e + 3]) * inv),
-                         pack_bf16(__uint_as_float(o1[e + 4]) * inv, __uint_as_float(o1[e + 5]) * inv),
-                         pack_bf16(__uint_as_float(o1[e + 6]) * inv, __uint_as_float(o1[e + 7]) * inv));
+          for (int e = 0; e < 32; e += 8)
+            dst[4 * h + e / 8] =
+                make_uint4(pack_bf16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
+                           pack_bf16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
+                           pack_bf16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
+                           pack_bf16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
         }
       }
       return true;
