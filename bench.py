@@ -31,6 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tuples/s: proxy+FP8 vs plain BF16 at >=99% label agreement; % HBM roofline"
+# DRAM bytes per k_gemm_tc launch on this workload, from the ncu capture of the
+# current kernel (25.2 GB over the four projections of one layer of the
+# 1024-tuple table, 610,382 rows each, scaled to the 652,000 rows of this
+# workload's average launch).  Set to None whenever the kernel changes.
+GEMM_TRAFFIC_PER_LAUNCH = 6.73e9
 
 
 def parse():
@@ -396,7 +401,11 @@ def main():
     roofline = {"kernel": "k_gemm_tc (tcgen05 BF16 projection GEMM)", "bound": "tensor",
                 "achieved": gemm_tf, "peak": tf_peak, "unit": "TFLOP/s",
                 "frac": gemm_tf / tf_peak, "peak_source": f"{peak_src} bf16_tflops_sustained",
-                "traffic": None, "launches": int(g["launches"]),
+                "traffic": GEMM_TRAFFIC_PER_LAUNCH,
+                "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the "
+                                  "four projections of a layer (1024-tuple table), scaled to this "
+                                  "workload's mean rows per launch",
+                "launches": int(g["launches"]),
                 "share_of_step": g["ms"] / ms if ms > 0 else None}
     out = {}
     if not args.no_extra and rank == 0:
