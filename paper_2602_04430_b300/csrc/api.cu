@@ -593,13 +593,16 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
       ed.x = w.x;
       ed.ld = c.d;
       if (fused && l + 1 < c.layers) set_norm_out(ed, w.xn, w.ssq);
+      if (fused && l + 1 == c.layers) ed.ssq_out = w.ssq;   // for the pooled state's 1/rms
       RC(project(ctx, w.h, LW.wd, M, c.d, c.ffn, ed, w.tmp, nullptr, s));
     }
-    // pooled final-normed last-layer document state
-    RC(rmsnorm(ctx, w.x, ch.rows, nullptr, w.inv_rms, s));
+    // pooled final-normed last-layer document state (bf16 path: 1/rms from the
+    // last residual epilogue's partial sums of squares)
+    if (!fused) RC(rmsnorm(ctx, w.x, ch.rows, nullptr, w.inv_rms, s));
     {
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      pool_rows(w.x, w.inv_rms, kv->off, ch.t0, ch.t1, ch.r0, c.d, kv->pooled, s);
+      pool_rows(w.x, fused ? nullptr : w.inv_rms, w.ssq, c.d / 128, c.eps, kv->off, ch.t0, ch.t1,
+                ch.r0, c.d, kv->pooled, s);
     }
     CKLAUNCH();
   }

@@ -74,8 +74,10 @@ template <typename act_t>
 void ea_scores(const act_t* K, const act_t* V, int64_t R, int hkv, int hd, int64_t r0,
                int64_t rows, const int32_t* rowtup, int t0, const float* mu, const float* s2,
                float* scores, cudaStream_t s);
-void pool_rows(const float* x, const float* inv_rms, const int64_t* off, int t0, int t1,
-               int64_t r0, int d, float* pooled, cudaStream_t s);
+// pooled[t] = mean of x[m] / rms(x[m]) over tuple t's rows; 1/rms from inv_rms or,
+// when inv_rms is nullptr, from the partial sums of squares ssq[m][parts]
+void pool_rows(const float* x, const float* inv_rms, const float* ssq, int parts, float eps,
+               const int64_t* off, int t0, int t1, int64_t r0, int d, float* pooled, cudaStream_t s);
 void label_head(const float* x, int n, int P, int d, float eps, const void* w_lm, int dtype,
                 const int32_t* labels, int n_labels, const float* bias, int kind,
                 float theta_pos, float theta_neg, float* logits, int32_t* out_labels,

@@ -264,7 +264,25 @@ __global__ void __launch_bounds__(256) k_qstats(const act_t* __restrict__ q,
   Vec<act_t>::load(base, shift);               // the group's first query vector
 #pragma unroll
   for (int e = 0; e < VN; ++e) a1[e] = a2[e] = 0.f;
-  for (int64_t it = il; it < items; it += lanes) {
+  // four items per thread per step, their loads issued together
+  int64_t it = il;
+  for (; it + 3 * lanes < items; it += 4 * lanes) {
+    float w4[4][VN];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t iu = it + u * lanes, j = iu / G, hh = iu % G;
+      Vec<act_t>::load(base + j * hq * hd + hh * hd, w4[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int e = 0; e < VN; ++e) {
+        const float dv = w4[u][e] - shift[e];
+        a1[e] += dv;
+        a2[e] = fmaf(dv, dv, a2[e]);
+      }
+  }
+  for (; it < items; it += lanes) {
     const int64_t j = it / G, hh = it % G;
     Vec<act_t>::load(base + j * hq * hd + hh * hd, v);
 #pragma unroll
@@ -308,43 +326,54 @@ template void qstats<float>(const float*, const int64_t*, int, int, int64_t, int
 template void qstats<bf16>(const bf16*, const int64_t*, int, int, int64_t, int, int, int, float*,
                            float*, cudaStream_t);
 
-// Thread per (kv head, slot): score = mu.k/sqrt(hd) + sum sigma2 k^2/(2hd) + ln(||v|| + 1e-12).
+// score = mu.k/sqrt(hd) + sum sigma2 k^2/(2hd) + ln(||v|| + 1e-12) per (kv head,
+// slot).  TPR = hd / VN threads share a slot, each reading one 16-byte vector of
+// its K and V rows (a warp reads whole rows), partial sums reduced by shuffles.
 template <typename act_t>
-__global__ void k_scores(const act_t* __restrict__ K, const act_t* __restrict__ V, int64_t R,
-                         int hkv, int hd, int64_t r0, int64_t rows,
-                         const int32_t* __restrict__ rowtup, int t0, const float* __restrict__ mu,
-                         const float* __restrict__ s2, float* __restrict__ scores) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows * hkv) return;
-  int g = (int)(i / rows);
-  int64_t m = i % rows;
-  int lt = rowtup[m] - t0;
-  const act_t* k = K + ((int64_t)g * R + r0 + m) * hd;
-  const act_t* v = V + ((int64_t)g * R + r0 + m) * hd;
-  const float* mup = mu + ((int64_t)lt * hkv + g) * hd;
-  const float* s2p = s2 + ((int64_t)lt * hkv + g) * hd;
-  float d1 = 0.f, d2 = 0.f, vv = 0.f;
+__global__ void __launch_bounds__(256) k_scores(const act_t* __restrict__ K, const act_t* __restrict__ V,
+                                                int64_t R, int hkv, int hd, int64_t r0, int64_t rows,
+                                                const int32_t* __restrict__ rowtup, int t0,
+                                                const float* __restrict__ mu, const float* __restrict__ s2,
+                                                float* __restrict__ scores) {
   constexpr int VN = Vec<act_t>::N;
-  for (int c = 0; c < hd; c += VN) {
+  const int tpr = hd / VN;                      // threads per slot (a power of two <= 32)
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / tpr;
+  const int c = (threadIdx.x % tpr) * VN;
+  const bool live = i < rows * hkv;
+  float d1 = 0.f, d2 = 0.f, vv = 0.f;
+  int g = 0;
+  int64_t m = 0;
+  if (live) {
+    g = (int)(i / rows);
+    m = i % rows;
+    const int lt = rowtup[m] - t0;
     float kk[VN], vx[VN];
-    Vec<act_t>::load(k + c, kk);
-    Vec<act_t>::load(v + c, vx);
+    Vec<act_t>::load(K + ((int64_t)g * R + r0 + m) * hd + c, kk);
+    Vec<act_t>::load(V + ((int64_t)g * R + r0 + m) * hd + c, vx);
+    const float* mup = mu + ((int64_t)lt * hkv + g) * hd + c;
+    const float* s2p = s2 + ((int64_t)lt * hkv + g) * hd + c;
 #pragma unroll
     for (int e = 0; e < VN; ++e) {
-      d1 += mup[c + e] * kk[e];
-      d2 += s2p[c + e] * kk[e] * kk[e];
+      d1 += mup[e] * kk[e];
+      d2 += s2p[e] * kk[e] * kk[e];
       vv += vx[e] * vx[e];
     }
   }
-  scores[(int64_t)g * R + r0 + m] =
-      d1 / sqrtf((float)hd) + d2 / (2.0f * (float)hd) + logf(sqrtf(vv) + 1e-12f);
+  for (int o = tpr / 2; o > 0; o >>= 1) {
+    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    vv += __shfl_xor_sync(0xffffffffu, vv, o);
+  }
+  if (live && c == 0)
+    scores[(int64_t)g * R + r0 + m] =
+        d1 / sqrtf((float)hd) + d2 / (2.0f * (float)hd) + logf(sqrtf(vv) + 1e-12f);
 }
 
 template <typename act_t>
 void ea_scores(const act_t* K, const act_t* V, int64_t R, int hkv, int hd, int64_t r0,
                int64_t rows, const int32_t* rowtup, int t0, const float* mu, const float* s2,
                float* scores, cudaStream_t s) {
-  int64_t n = rows * hkv;
+  const int64_t n = rows * hkv * (hd / Vec<act_t>::N);   // threads
   if (n <= 0) return;
   k_scores<act_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(K, V, R, hkv, hd, r0, rows, rowtup,
                                                               t0, mu, s2, scores);
@@ -357,23 +386,81 @@ template void ea_scores<bf16>(const bf16*, const bf16*, int64_t, int, int, int64
                               cudaStream_t);
 
 // ------------------------------------------------------------------ pooling
-// Block per tuple: pooled[t] = mean over document rows of the final-normed state.
-__global__ void k_pool(const float* __restrict__ x, const float* __restrict__ inv_rms,
-                       const int64_t* __restrict__ off, int t0, int64_t r0, int d,
-                       float* __restrict__ pooled) {
+// Block per tuple: pooled[t] = mean over document rows of the final-normed
+// state x[m] / rms(x[m]).  1/rms comes from inv_rms, or (inv_rms == nullptr)
+// from the residual epilogue's partial sums of squares ssq[m][parts], for 2048
+// rows at a time into shared memory.  A thread owns 4 consecutive columns
+// (16-byte loads) and keeps four rows in flight.
+__global__ void __launch_bounds__(256) k_pool(const float* __restrict__ x, const float* __restrict__ inv_rms,
+                                              const float* __restrict__ ssq, int parts, float eps,
+                                              const int64_t* __restrict__ off, int t0, int64_t r0, int d,
+                                              float* __restrict__ pooled) {
+  constexpr int RB = 2048;
+  __shared__ float inv_s[RB];
   const int t = t0 + blockIdx.x;
   const int64_t a = off[t] - r0, b = off[t + 1] - r0;
-  for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    float acc = 0.f;
-    for (int64_t m = a; m < b; ++m) acc += x[m * d + c] * inv_rms[m];
-    pooled[(int64_t)t * d + c] = acc / (float)(b - a);
+  const int L = (int)(b - a);
+  for (int c0 = 0; c0 < d; c0 += blockDim.x * 4) {
+    const int c = c0 + threadIdx.x * 4;
+    float4 acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int m0 = 0; m0 < L; m0 += RB) {
+      const int nb = min(RB, L - m0);
+      __syncthreads();
+      for (int m = threadIdx.x; m < nb; m += blockDim.x) {
+        const int64_t row = a + m0 + m;
+        float iv;
+        if (inv_rms != nullptr) {
+          iv = inv_rms[row];
+        } else {
+          float sum = 0.f;
+          for (int k = 0; k < parts; ++k) sum += ssq[row * parts + k];
+          iv = 1.0f / sqrtf(sum / (float)d + eps);
+        }
+        inv_s[m] = iv;
+      }
+      __syncthreads();
+      if (c < d) {
+        const float* xr = x + (a + m0) * d + c;
+        int m = 0;
+        for (; m + 3 < nb; m += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 v = *reinterpret_cast<const float4*>(xr + (int64_t)(m + u) * d);
+            const float iv = inv_s[m + u];
+            acc[u].x = fmaf(v.x, iv, acc[u].x);
+            acc[u].y = fmaf(v.y, iv, acc[u].y);
+            acc[u].z = fmaf(v.z, iv, acc[u].z);
+            acc[u].w = fmaf(v.w, iv, acc[u].w);
+          }
+        }
+        for (; m < nb; ++m) {
+          const float4 v = *reinterpret_cast<const float4*>(xr + (int64_t)m * d);
+          const float iv = inv_s[m];
+          acc[0].x = fmaf(v.x, iv, acc[0].x);
+          acc[0].y = fmaf(v.y, iv, acc[0].y);
+          acc[0].z = fmaf(v.z, iv, acc[0].z);
+          acc[0].w = fmaf(v.w, iv, acc[0].w);
+        }
+      }
+    }
+    if (c < d) {
+      const float inv_l = 1.0f / (float)L;
+      float4 o;
+      o.x = ((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x)) * inv_l;
+      o.y = ((acc[0].y + acc[1].y) + (acc[2].y + acc[3].y)) * inv_l;
+      o.z = ((acc[0].z + acc[1].z) + (acc[2].z + acc[3].z)) * inv_l;
+      o.w = ((acc[0].w + acc[1].w) + (acc[2].w + acc[3].w)) * inv_l;
+      *reinterpret_cast<float4*>(pooled + (int64_t)t * d + c) = o;
+    }
   }
 }
 
-void pool_rows(const float* x, const float* inv_rms, const int64_t* off, int t0, int t1,
-               int64_t r0, int d, float* pooled, cudaStream_t s) {
+void pool_rows(const float* x, const float* inv_rms, const float* ssq, int parts, float eps,
+               const int64_t* off, int t0, int t1, int64_t r0, int d, float* pooled, cudaStream_t s) {
   if (t1 <= t0) return;
-  k_pool<<<t1 - t0, 256, 0, s>>>(x, inv_rms, off, t0, r0, d, pooled);
+  k_pool<<<t1 - t0, 256, 0, s>>>(x, inv_rms, ssq, parts, eps, off, t0, r0, d, pooled);
 }
 
 // ------------------------------------------------------------------ label head
