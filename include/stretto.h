@@ -207,6 +207,27 @@ int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
                const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
                int32_t* labels_dev, void* stream);
 
+/* ---- batched evaluation of several operators ----
+ *
+ * Several operators (different prompts, label sets, kinds and retention
+ * ratios r_k <= the retained profile's r), each over its own tuple set, in one
+ * pass: the (operator, tuple) pairs of all operators share every projection
+ * launch and one attention launch per layer; operator k reads the first
+ * n_keep(L, r_k) slots of the shared rank-ordered cache (the retained sets
+ * are nested in r, Sec. 5 "several profiles per item"; batching over items,
+ * Sec. 6).  Results equal n_ops separate st_op_eval calls bit for bit.
+ * ST_MAX_OPERATORS operators at most.
+ * ops[k], tuple_ids_dev[k] (DEVICE int32 [n[k]]), n[k] (host), logits_dev[k]
+ * (DEVICE float32 [n[k]][n_labels of ops[k]]), labels_dev[k] (DEVICE int32
+ * [n[k]]): the arrays of pointers are host arrays of n_ops entries, read
+ * during the call only.
+ * Errors: ST_EINVAL (n_ops outside 1..ST_MAX_OPERATORS, an r above the
+ * retained profile's, a NULL buffer with n[k] > 0). */
+#define ST_MAX_OPERATORS 8
+int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops, const st_operator* const* ops,
+                     const int32_t* const* tuple_ids_dev, const int32_t* n,
+                     float* const* logits_dev, int32_t* const* labels_dev, void* stream);
+
 /* ---- operator evaluation without device allocation ----
  *
  * The paper has no counterpart to this entry; it exists for callers that

@@ -779,7 +779,7 @@ extern "C" void st_op_free(st_operator* op) {
 
 namespace st {
 
-size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t tuples, char* base, EvalBufs* w) {
+size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t pairs, char* base, EvalBufs* w) {
   const st_model_cfg& c = ctx->cfg;
   const size_t e = ctx->esz;
   size_t off = 0;
@@ -789,6 +789,8 @@ size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t tuples, char* base, Ev
     off += bytes;
     return (void*)p;
   };
+  // a pair's 128-row attention blocks: at most ceil(256 G / 128) (P <= 256)
+  const int64_t max_blocks = (256LL * (c.hq / c.hkv) + 127) / 128;
   EvalBufs b;
   b.x = (float*)take(rows * c.d * 4);
   b.xn = take(rows * c.d * e);
@@ -800,33 +802,105 @@ size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t tuples, char* base, Ev
   b.tmp = c.dtype == ST_F32 ? (float*)take(rows * 2 * c.ffn * 4) : nullptr;
   b.ssq = (float*)take(rows * (c.d / 128) * 4);
   b.pos = (int32_t*)take(rows * 4);
-  b.tup = (int32_t*)take(tuples * 4);
-  b.len = (int32_t*)take(tuples * 4);
-  b.nk = (int32_t*)take(tuples * 4);
-  b.order = (int32_t*)take(tuples * 4);
+  b.tok = (int32_t*)take(rows * 4);
+  b.rowpair = (int32_t*)take(rows * 4);
+  b.tup = (int32_t*)take(pairs * 4);
+  b.len = (int32_t*)take(pairs * 4);
+  b.nk = (int32_t*)take(pairs * 4);
+  b.prow = (int32_t*)take(pairs * 4);
+  b.pP = (int32_t*)take(pairs * 4);
+  b.pop = (int32_t*)take(pairs * 4);
+  b.pj = (int32_t*)take(pairs * 4);
+  b.order = (int32_t*)take(pairs * max_blocks * 2 * 4);
   if (w) *w = b;
   return off + 256;
 }
 
-int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_t* tuple_ids,
-               int nc, const EvalBufs& w, float* logits, int32_t* labels, cudaStream_t s) {
+int make_opset(st_ctx* ctx, const st_kv* kv, int n_ops, const st_operator* const* ops,
+               const int32_t* const* tuple_ids, const int32_t* n, float* const* logits,
+               int32_t* const* labels, OpSet* os, int64_t* rows_total, int* pairs_total) {
+  if (!kv || kv->ctx != ctx || n_ops < 1 || n_ops > ST_MAX_OPS || !ops || !tuple_ids || !n ||
+      !logits || !labels || !os)
+    return fail(ctx, ST_EINVAL, "operator evaluation: bad argument (1 to 8 operators)");
+  if (kv->r <= 0.0) return fail(ctx, ST_EINVAL, "operator evaluation: no retained profile (call st_kv_retain)");
   const st_model_cfg& c = ctx->cfg;
-  const int P = op->desc.P;
-  const int M = nc * P;
+  *os = OpSet();
+  os->n_ops = n_ops;
+  int64_t rows = 0;
+  int64_t pairs = 0;
+  for (int k = 0; k < n_ops; ++k) {
+    const st_operator* op = ops[k];
+    if (!op || n[k] < 0) return fail(ctx, ST_EINVAL, "operator evaluation: bad operator or count");
+    if (n[k] > 0 && (!tuple_ids[k] || !logits[k] || !labels[k]))
+      return fail(ctx, ST_EINVAL, "operator evaluation: NULL buffer");
+    if (op->desc.r > kv->r) return fail(ctx, ST_EINVAL, "operator evaluation: operator r exceeds the retained profile's r");
+    if (kv->max_len + op->desc.P > c.max_pos) return fail(ctx, ST_EINVAL, "operator evaluation: document + prompt exceeds max_pos");
+    OpDev& o = os->op[k];
+    o.tuple_ids = tuple_ids[k];
+    o.prompt = op->prompt;
+    o.labels = op->labels;
+    o.bias = op->bias;
+    o.logits = logits[k];
+    o.out_labels = labels[k];
+    o.row0 = rows;
+    o.r = op->desc.r;
+    o.n = n[k];
+    o.P = op->desc.P;
+    o.n_labels = op->desc.n_labels;
+    o.kind = op->desc.kind;
+    o.pair0 = (int)pairs;
+    o.theta_pos = op->desc.theta_pos;
+    o.theta_neg = op->desc.theta_neg;
+    rows += (int64_t)n[k] * op->desc.P;
+    pairs += n[k];
+  }
+  if (pairs > (1LL << 30)) return fail(ctx, ST_EINVAL, "operator evaluation: too many (operator, tuple) pairs");
+  *rows_total = rows;
+  *pairs_total = (int)pairs;
+  return ST_OK;
+}
+
+int64_t opset_rows(const OpSet& os, int p0, int p1) {
+  int64_t r = 0;
+  for (int k = 0; k < os.n_ops; ++k) {
+    const OpDev& o = os.op[k];
+    const int a = std::max(p0, o.pair0), b = std::min(p1, o.pair0 + o.n);
+    if (b > a) r += (int64_t)(b - a) * o.P;
+  }
+  return r;
+}
+
+int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, int64_t row_base,
+               int64_t M, const EvalBufs& w, cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  const int np = p1 - p0;
+  if (np <= 0) return ST_OK;
   const int qd = c.hq * c.hd, kd = c.hkv * c.hd, nqkv = qd + 2 * kd;
   const size_t kr_e = kv->kv_dtype == ST_E4M3 ? 1 : ctx->esz;
   const bool fused = c.dtype == ST_BF16;
+  const int G = c.hq / c.hkv;
+  int n_entries = 0;   // attention work list entries: ceil(P G / 128) per pair
+  for (int k = 0; k < os.n_ops; ++k) {
+    const OpDev& o = os.op[k];
+    const int a = std::max(p0, o.pair0), b = std::min(p1, o.pair0 + o.n);
+    if (b > a) n_entries += (b - a) * ((o.P * G + 127) / 128);
+  }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_rowinfo(tuple_ids, nc, P, kv->off, op->desc.r, w.tup, w.len, w.nk, w.pos, s);
+    eval_pairs(os, p0, np, row_base, kv->off, w.tup, w.len, w.nk, w.prow, w.pP, w.pop, w.pj, s);
+  }
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    eval_rows(os, p0, row_base, M, kv->off, w.pos, w.tok, w.rowpair, s);
   }
   if (c.dtype == ST_BF16) {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_order(w.nk, nc, w.order, s);
+    eval_worklist(w.nk, w.pP, np, G, w.order, s);
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    embed_prompt(op->prompt, P, M, ctx->embed, c.dtype, c.d, w.x, s);
+    if (c.dtype == ST_BF16) embed_rows<bf16>(w.tok, M, (const bf16*)ctx->embed, c.d, w.x, s);
+    else embed_rows<float>(w.tok, M, (const float*)ctx->embed, c.d, w.x, s);
   }
   CKLAUNCH();
   for (int l = 0; l < c.layers; ++l) {
@@ -864,63 +938,131 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_
     a.offp = kv->offp;
     a.tup = w.tup;
     a.nk = w.nk;
-    a.order = c.dtype == ST_BF16 ? w.order : nullptr;
+    a.prow = w.prow;
+    a.pP = w.pP;
+    a.rowpair = w.rowpair;
+    a.work = w.order;
+    a.n_work = n_entries;
+    a.qrows = M;
     a.kp = w.kp;
     a.vp = w.vp;
-    a.n = nc;
-    a.P = P;
+    a.n = np;
     a.kv_dtype = kv->kv_dtype;
     RC(attention(ctx, a, nullptr, 0, s));
-    // In the last layer only each tuple's last prompt row feeds the label head:
-    // the output projection, the FFN and their norms run on those nc rows
-    // (rows i*P + P-1 of the stream), read in place through a row stride.
-    const bool last = (l == c.layers - 1) && P > 1;
-    const int Mr = last ? nc : M;
-    EpiParams eo;
-    eo.mode = EPI_RESID;
-    eo.x = w.x;
-    eo.ld = c.d;
-    if (fused) set_norm_out(eo, w.xn, w.ssq);
-    const void* o_in = w.o;
-    if (last) {
+    if (l + 1 < c.layers) {
+      EpiParams eo;
+      eo.mode = EPI_RESID;
+      eo.x = w.x;
+      eo.ld = c.d;
+      if (fused) set_norm_out(eo, w.xn, w.ssq);
+      RC(project(ctx, w.o, LW.wo, M, c.d, qd, eo, w.tmp, nullptr, s));
+      if (!fused) {
+        Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+        rmsnorm_rows<float>(w.x, M, c.d, c.eps, (float*)w.xn, nullptr, s);
+        CKLAUNCH();
+      }
+      EpiParams eg;
+      eg.mode = EPI_SWIGLU;
+      eg.h = w.h;
+      eg.ld = c.ffn;
+      if (fused) set_norm_in(eg, w.ssq, c);
+      RC(project(ctx, w.xn, LW.wgu, M, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
+      EpiParams ed;
+      ed.mode = EPI_RESID;
+      ed.x = w.x;
+      ed.ld = c.d;
+      if (fused) set_norm_out(ed, w.xn, w.ssq);
+      RC(project(ctx, w.h, LW.wd, M, c.d, c.ffn, ed, w.tmp, nullptr, s));
+      continue;
+    }
+    // Last layer: only each pair's last prompt row feeds the label head, so the
+    // output projection, the FFN and their norms run on those rows only, one
+    // operator segment at a time (its rows are P apart): read in place through
+    // a row stride, residual rows i*P + P-1 of the segment, compact norm / FFN
+    // buffers at the segment's first pair.
+    for (int k = 0; k < os.n_ops; ++k) {
+      const OpDev& od = os.op[k];
+      const int a0 = std::max(p0, od.pair0), b0 = std::min(p1, od.pair0 + od.n);
+      if (b0 <= a0) continue;
+      const int P = od.P, Mr = b0 - a0, ia = a0 - p0;            // pairs, first chunk pair
+      const int64_t ra = od.row0 + (int64_t)(a0 - od.pair0) * P - row_base;   // first row
+      EpiParams eo;
+      eo.mode = EPI_RESID;
+      eo.x = w.x;
+      eo.ld = c.d;
       eo.a_ld = (int64_t)P * qd;
       eo.row_mul = P;
-      eo.row_add = P - 1;
-      o_in = (const char*)w.o + (size_t)(P - 1) * qd * ctx->esz;
-    }
-    RC(project(ctx, o_in, LW.wo, Mr, c.d, qd, eo, w.tmp, nullptr, s));
-    if (!fused) {
-      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      if (last)
-        rmsnorm_rows<float>(w.x + (size_t)(P - 1) * c.d, nc, c.d, c.eps, (float*)w.xn, nullptr, s,
+      eo.row_add = (int)(ra + P - 1);
+      if (fused) set_norm_out(eo, (char*)w.xn + (size_t)ia * c.d * ctx->esz, w.ssq + (size_t)ia * (c.d / 128));
+      const void* o_in = (const char*)w.o + (size_t)(ra + P - 1) * qd * ctx->esz;
+      RC(project(ctx, o_in, LW.wo, Mr, c.d, qd, eo, w.tmp, nullptr, s));
+      void* xn_k = (char*)w.xn + (size_t)ia * c.d * ctx->esz;
+      if (!fused) {
+        Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+        rmsnorm_rows<float>(w.x + (size_t)(ra + P - 1) * c.d, Mr, c.d, c.eps, (float*)xn_k, nullptr, s,
                             (int64_t)P * c.d);
-      else
-        rmsnorm_rows<float>(w.x, M, c.d, c.eps, (float*)w.xn, nullptr, s);
-      CKLAUNCH();
-    }
-    EpiParams eg;
-    eg.mode = EPI_SWIGLU;
-    eg.h = w.h;
-    eg.ld = c.ffn;
-    if (fused) set_norm_in(eg, w.ssq, c);
-    RC(project(ctx, w.xn, LW.wgu, Mr, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
-    EpiParams ed;
-    ed.mode = EPI_RESID;
-    ed.x = w.x;
-    ed.ld = c.d;
-    if (fused && !last) set_norm_out(ed, w.xn, w.ssq);
-    if (last) {
+        CKLAUNCH();
+      }
+      void* h_k = (char*)w.h + (size_t)ia * c.ffn * ctx->esz;
+      EpiParams eg;
+      eg.mode = EPI_SWIGLU;
+      eg.h = h_k;
+      eg.ld = c.ffn;
+      if (fused) set_norm_in(eg, w.ssq + (size_t)ia * (c.d / 128), c);
+      RC(project(ctx, xn_k, LW.wgu, Mr, 2 * c.ffn, c.d, eg, w.tmp, h_k, s));
+      EpiParams ed;
+      ed.mode = EPI_RESID;
+      ed.x = w.x;
+      ed.ld = c.d;
       ed.row_mul = P;
-      ed.row_add = P - 1;
+      ed.row_add = (int)(ra + P - 1);
+      RC(project(ctx, h_k, LW.wd, Mr, c.d, c.ffn, ed, w.tmp, nullptr, s));
     }
-    RC(project(ctx, w.h, LW.wd, Mr, c.d, c.ffn, ed, w.tmp, nullptr, s));
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    label_head(w.x, nc, P, c.d, c.eps, ctx->w_lm, c.dtype, op->labels, op->desc.n_labels, op->bias,
-               op->desc.kind, op->desc.theta_pos, op->desc.theta_neg, logits, labels, s);
+    label_head(w.x, os, np, w.prow, w.pP, w.pop, w.pj, c.d, c.eps, ctx->w_lm, c.dtype, s);
   }
   CKLAUNCH();
+  return ST_OK;
+}
+
+// Chunks the pairs (operator-major) into batches of at most `cap` prompt rows
+// and runs each through eval_chunk.
+int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  int maxP = 1;
+  for (int k = 0; k < os.n_ops; ++k) maxP = std::max(maxP, os.op[k].P);
+  const int64_t cap = std::max<int64_t>(ctx->eval_rows_cap > 0 ? ctx->eval_rows_cap : kDefaultEvalRows, maxP);
+  // chunk boundaries
+  std::vector<int> cuts{0};
+  int64_t acc = 0;
+  for (int k = 0; k < os.n_ops; ++k)
+    for (int j = 0; j < os.op[k].n; ++j) {
+      if (acc + os.op[k].P > cap) {
+        cuts.push_back(os.op[k].pair0 + j);
+        acc = 0;
+      }
+      acc += os.op[k].P;
+    }
+  cuts.push_back(pairs);
+  int64_t max_rows = 0;
+  int max_pairs = 0;
+  for (size_t q = 0; q + 1 < cuts.size(); ++q) {
+    max_rows = std::max(max_rows, opset_rows(os, cuts[q], cuts[q + 1]));
+    max_pairs = std::max(max_pairs, cuts[q + 1] - cuts[q]);
+  }
+  RC(grow(ctx, ctx->ws_eval, eval_bufs(ctx, max_rows, max_pairs, nullptr, nullptr)));
+  EvalBufs w;
+  eval_bufs(ctx, max_rows, max_pairs, (char*)ctx->ws_eval.p, &w);
+  int64_t row_base = 0;
+  for (size_t q = 0; q + 1 < cuts.size(); ++q) {
+    const int64_t M = opset_rows(os, cuts[q], cuts[q + 1]);
+    if (M == 0) continue;
+    RC(eval_chunk(ctx, kv, os, cuts[q], cuts[q + 1], row_base, M, w, s));
+    row_base += M;
+  }
+  (void)c;
   return ST_OK;
 }
 
@@ -932,23 +1074,24 @@ extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
   if (!ctx || !kv || !op || kv->ctx != ctx || n < 0) return fail(ctx, ST_EINVAL, "st_op_eval: bad argument");
   if (n == 0) return ST_OK;
   if (!tuple_ids_dev || !logits_dev || !labels_dev) return fail(ctx, ST_EINVAL, "st_op_eval: NULL buffer");
-  if (kv->r <= 0.0) return fail(ctx, ST_EINVAL, "st_op_eval: no retained profile (call st_kv_retain)");
-  if (op->desc.r > kv->r) return fail(ctx, ST_EINVAL, "st_op_eval: operator r exceeds the retained profile's r");
-  const st_model_cfg& c = ctx->cfg;
-  if (kv->max_len + op->desc.P > c.max_pos) return fail(ctx, ST_EINVAL, "st_op_eval: document + prompt exceeds max_pos");
-  cudaStream_t s = S(stream);
-  const int P = op->desc.P;
-  const int64_t cap = std::max<int64_t>(ctx->eval_rows_cap > 0 ? ctx->eval_rows_cap : kDefaultEvalRows, P);
-  const int per_chunk = (int)std::min<int64_t>(n, cap / P);
-  RC(grow(ctx, ctx->ws_eval, eval_bufs(ctx, (int64_t)per_chunk * P, per_chunk, nullptr, nullptr)));
-  EvalBufs w;
-  eval_bufs(ctx, (int64_t)per_chunk * P, per_chunk, (char*)ctx->ws_eval.p, &w);
-  for (int i0 = 0; i0 < n; i0 += per_chunk) {
-    const int nc = std::min(per_chunk, n - i0);
-    RC(eval_chunk(ctx, kv, op, tuple_ids_dev + i0, nc, w, logits_dev + (size_t)i0 * op->desc.n_labels,
-                  labels_dev + i0, s));
-  }
-  return ST_OK;
+  OpSet os;
+  int64_t rows = 0;
+  int pairs = 0;
+  RC(make_opset(ctx, kv, 1, &op, &tuple_ids_dev, &n, &logits_dev, &labels_dev, &os, &rows, &pairs));
+  return run_opset(ctx, kv, os, pairs, S(stream));
+}
+
+extern "C" int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
+                                const st_operator* const* ops, const int32_t* const* tuple_ids_dev,
+                                const int32_t* n, float* const* logits_dev, int32_t* const* labels_dev,
+                                void* stream) {
+  if (!ctx) return fail(nullptr, ST_EINVAL, "st_op_eval_multi: NULL context");
+  OpSet os;
+  int64_t rows = 0;
+  int pairs = 0;
+  RC(make_opset(ctx, kv, n_ops, ops, tuple_ids_dev, n, logits_dev, labels_dev, &os, &rows, &pairs));
+  if (pairs == 0) return ST_OK;
+  return run_opset(ctx, kv, os, pairs, S(stream));
 }
 
 extern "C" int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,

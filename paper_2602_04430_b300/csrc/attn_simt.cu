@@ -11,7 +11,7 @@ template <typename T, int HD>
 __global__ void __launch_bounds__(256) k_attn_simt(AttnParams a) {
   const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int64_t nrows = a.mode == 0 ? a.rows : (int64_t)a.n * a.P;
+  const int64_t nrows = a.mode == 0 ? a.rows : a.qrows;
   if (wid >= nrows * a.hq) return;
   const int64_t qrow = wid / a.hq;
   const int h = (int)(wid % a.hq);
@@ -31,15 +31,15 @@ __global__ void __launch_bounds__(256) k_attn_simt(AttnParams a) {
     vA = reinterpret_cast<const T*>(a.V) + base;
     nA = a.pos[qrow] + 1;
   } else {
-    const int i = (int)(qrow / a.P), p = (int)(qrow % a.P);
+    const int i = a.rowpair[qrow], p = (int)(qrow - a.prow[i]);
     const int t = a.tup[i];
     const int64_t base = ((int64_t)g * a.Rp_cap + a.offp[t]) * HD;
     kA = reinterpret_cast<const T*>(a.Kr) + base;
     vA = reinterpret_cast<const T*>(a.Vr) + base;
     nA = a.nk[i];
     sB = (int64_t)a.hkv * HD;
-    kB = reinterpret_cast<const T*>(a.kp) + (int64_t)i * a.P * sB + (int64_t)g * HD;
-    vB = reinterpret_cast<const T*>(a.vp) + (int64_t)i * a.P * sB + (int64_t)g * HD;
+    kB = reinterpret_cast<const T*>(a.kp) + (int64_t)a.prow[i] * sB + (int64_t)g * HD;
+    vB = reinterpret_cast<const T*>(a.vp) + (int64_t)a.prow[i] * sB + (int64_t)g * HD;
     nB = p + 1;
   }
   float m = -INFINITY, l = 0.f, acc[HD];
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_attn_simt(AttnParams a) {
 
 template <typename act_t, typename kv_t>
 void attn_simt(const AttnParams& a, cudaStream_t s) {
-  const int64_t nrows = a.mode == 0 ? a.rows : (int64_t)a.n * a.P;
+  const int64_t nrows = a.mode == 0 ? a.rows : a.qrows;
   const int64_t warps = nrows * a.hq;
   if (warps <= 0) return;
   const unsigned grid = (unsigned)((warps + 7) / 8);

@@ -163,22 +163,22 @@ struct Work {
   __device__ void decode(const AttnParams& a, const int32_t* items, int w, int zb_count) {
     G = a.hq / a.hkv;
     if (MODE == 1) {
-      const int zb = w % zb_count;
-      const int rest = w / zb_count;
-      g = rest % a.hkv;
-      i = rest / a.hkv;
-      if (items != nullptr) i = items[i];   // longest tuples first
-      P = a.P;
+      // work list entry (pair, 128-row block), longest documents first; kv head fastest
+      const int e = w / a.hkv;
+      g = w % a.hkv;
+      i = items[2 * e];
+      const int zb = items[2 * e + 1];
+      P = a.pP[i];
       row_base = zb * ROWS;
-      rows = min(ROWS, a.P * G - row_base);
+      rows = min(ROWS, P * G - row_base);
       lim_max = (row_base + rows - 1) / G;
       const int tt = a.tup[i];
       n_doc = a.nk[i];
       doc_row0 = (int64_t)g * a.Rp_cap + a.offp[tt];
-      prompt_row0 = (int64_t)i * a.P;
-      qrow0 = (int64_t)i * a.P + row_base / G;
+      prompt_row0 = a.prow[i];
+      qrow0 = prompt_row0 + row_base / G;
       n_doc_tiles = (n_doc + TK - 1) / TK;
-      n_tiles = n_doc_tiles + (min(a.P, lim_max + 1) + TK - 1) / TK;
+      n_tiles = n_doc_tiles + (min(P, lim_max + 1) + TK - 1) / TK;
     } else {
       const int it = w / a.hkv;
       g = w % a.hkv;
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
         const int rr = W.row_base + r, hh = rr % W.G;
         const bool row_ok = r < W.rows && (MODE == 1 || (W.j0 + pos) < W.L);
         if (row_ok) {
-          if (MODE == 1) orow = ((int64_t)W.i * a.P + pos) * a.hq + (int64_t)W.g * W.G + hh;
+          if (MODE == 1) orow = (W.prompt_row0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
           else orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
         }
       }
@@ -844,14 +844,14 @@ bool attn_tc_supported(int hq, int hkv, int hd) {
 }
 
 int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
-  if (a.n <= 0) return ST_OK;
+  if (a.n_work <= 0) return ST_OK;
   if (!attn_tc_supported(a.hq, a.hkv, a.hd) || (a.kv_dtype != ST_BF16 && a.kv_dtype != ST_E4M3))
     return ST_EUNSUPPORTED;
   const bool fp8 = a.kv_dtype == ST_E4M3;
   const int G = a.hq / a.hkv;
   CUtensorMap mq, mk, mv, mkp, mvp;
   const uint64_t planes = (uint64_t)a.hkv * a.Rp_cap;
-  const uint64_t prow = (uint64_t)a.n * a.P;
+  const uint64_t prow = (uint64_t)a.qrows;
   const CUtensorMapDataType qt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   bool ok = map_q(&mq, a.q, a.hq, prow, G, qt) &&
             map2d(&mkp, a.kp, (uint64_t)a.hkv * HD, prow, BOX, qt) &&
@@ -859,17 +859,17 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   if (fp8) ok = ok && map2d_u8(&mk, a.Kr, planes, BOX) && map2d_u8(&mv, a.Vr, planes, BOX);
   else ok = ok && map2d(&mk, a.Kr, HD, planes, BOX) && map2d(&mv, a.Vr, HD, planes, BOX);
   if (!ok) return ST_ECUDA;
-  const int zb = (a.P * G + ROWS - 1) / ROWS;
-  const int n_work = a.n * a.hkv * zb;
+  const int n_work = a.n_work * a.hkv;
   const int slots = sm_count() * ctas_per_sm(fp8);
   const int grid = n_work < slots ? n_work : slots;
+  const int zb = 1;   // unused in eval (the work list carries the row block)
   if (fp8) {
     set_smem_attr<1, true>();
-    k_attn_tc<1, true><<<grid, nthreads(true), smem_bytes(true), s>>>(a, a.order, n_work, zb, mq, mk,
+    k_attn_tc<1, true><<<grid, nthreads(true), smem_bytes(true), s>>>(a, a.work, n_work, zb, mq, mk,
                                                                       mv, mkp, mvp, status);
   } else {
     set_smem_attr<1, false>();
-    k_attn_tc<1, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, a.order, n_work, zb, mq,
+    k_attn_tc<1, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, a.work, n_work, zb, mq,
                                                                          mk, mv, mkp, mvp, status);
   }
   return ST_OK;

@@ -54,19 +54,46 @@ struct Launch {
   ~Launch();
 };
 
+// ---- batched operator evaluation: the operators of one call as the kernels see
+// them (passed by value in kernel parameters, so a captured graph replays them)
+constexpr int ST_MAX_OPS = 8;
+struct OpDev {
+  const int32_t* tuple_ids = nullptr;   // [n] device: the tuples this operator evaluates
+  const int32_t* prompt = nullptr;      // [P] device
+  const int32_t* labels = nullptr;      // [n_labels] device: label token ids
+  const float* bias = nullptr;          // [n_labels] device (classify)
+  float* logits = nullptr;              // [n][n_labels] device output
+  int32_t* out_labels = nullptr;        // [n] device output
+  int64_t row0 = 0;                     // first prompt row of this operator in the call
+  double r = 1.0;
+  int n = 0, P = 0, n_labels = 0, kind = 0, pair0 = 0;   // pair0: first (operator, tuple) pair
+  float theta_pos = 0.f, theta_neg = 0.f;
+};
+struct OpSet {
+  int n_ops = 0;
+  OpDev op[ST_MAX_OPS];
+};
+
 // ---- misc kernels (kernels_misc.cu) ----
 template <typename act_t>
 void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, float* x, cudaStream_t s);
-void embed_prompt(const int32_t* prompt, int P, int64_t rows, const void* E, int dtype, int d,
-                  float* x, cudaStream_t s);
 template <typename act_t>
 void rmsnorm_rows(const float* x, int64_t rows, int d, float eps, act_t* xn, float* inv_rms,
                   cudaStream_t s, int64_t x_ld = 0);
 void build_rowinfo(const int64_t* off, int t0, int t1, int64_t r0, int64_t rows, int32_t* rowtup,
                    int32_t* pos, cudaStream_t s);
-void eval_rowinfo(const int32_t* tuple_ids, int n, int P, const int64_t* off, double r,
-                  int32_t* tup, int32_t* len, int32_t* nk, int32_t* pos, cudaStream_t s);
-void eval_order(const int32_t* nk, int n, int32_t* order, cudaStream_t s);
+// Plan of pairs [p0, p0 + np) of an operator set whose rows start at row_base:
+// per pair (eval_pairs) its tuple, document length, retained count, prompt row
+// (relative to row_base), prompt length, operator and index within the
+// operator; per row (eval_rows) its RoPE position, prompt token and pair.
+void eval_pairs(const OpSet& os, int p0, int np, int64_t row_base, const int64_t* off, int32_t* tup,
+                int32_t* len, int32_t* nk, int32_t* prow, int32_t* pP, int32_t* pop, int32_t* pj,
+                cudaStream_t s);
+void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const int64_t* off,
+               int32_t* pos, int32_t* tok, int32_t* rowpair, cudaStream_t s);
+// Attention work list: (pair, 128-row block) entries, longest retained
+// documents first; G = query heads per kv head.
+void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int32_t* list, cudaStream_t s);
 template <typename act_t>
 void qstats(const act_t* q, const int64_t* off, int t0, int t1, int64_t r0, int hq, int hkv,
             int hd, float* mu, float* s2, cudaStream_t s);
@@ -78,9 +105,9 @@ void ea_scores(const act_t* K, const act_t* V, int64_t R, int hkv, int hd, int64
 // when inv_rms is nullptr, from the partial sums of squares ssq[m][parts]
 void pool_rows(const float* x, const float* inv_rms, const float* ssq, int parts, float eps,
                const int64_t* off, int t0, int t1, int64_t r0, int d, float* pooled, cudaStream_t s);
-void label_head(const float* x, int n, int P, int d, float eps, const void* w_lm, int dtype,
-                const int32_t* labels, int n_labels, const float* bias, int kind,
-                float theta_pos, float theta_neg, float* logits, int32_t* out_labels,
+// Final RMSNorm of each pair's last prompt row, its operator's label logits and decision.
+void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, const int32_t* pP,
+                const int32_t* pop, const int32_t* pj, int d, float eps, const void* w_lm, int dtype,
                 cudaStream_t s);
 void swiglu_from_f32(const float* t, int64_t rows, int ffn, float* h, cudaStream_t s);
 void nkeep_offp(const int64_t* off, int T, double r, int32_t* nkeep, int64_t* offp,
@@ -120,7 +147,12 @@ struct AttnParams {
   const int64_t* offp = nullptr;
   const int32_t* tup = nullptr;   // [n] tuple of each evaluated item
   const int32_t* nk = nullptr;    // [n] retained slots read per item
-  const int32_t* order = nullptr; // [n] item positions, longest first (nullptr: as given)
+  const int32_t* prow = nullptr;  // [n] first prompt row of each pair
+  const int32_t* pP = nullptr;    // [n] prompt length of each pair
+  const int32_t* rowpair = nullptr; // [qrows] pair of each prompt row (CUDA-core path)
+  const int32_t* work = nullptr;  // tensor-core path: (pair, 128-row block) entries
+  int n_work = 0;                 // entries in work
+  int64_t qrows = 0;              // prompt rows of the call
   const void* kp = nullptr;       // prompt keys kp[(i*P + p)*hkv*hd + g*hd + c]
   const void* vp = nullptr;
   int n = 0, P = 0;
@@ -128,25 +160,33 @@ struct AttnParams {
 };
 template <typename act_t, typename kv_t>
 void attn_simt(const AttnParams& a, cudaStream_t s);
-void attn_mma_eval(const AttnParams& a, cudaStream_t s);
 bool attn_tc_supported(int hq, int hkv, int hd);
 int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s);
 int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int* status,
                     cudaStream_t s);
-void attn_mma_prefill(const AttnParams& a, const int32_t* items, int n_items, cudaStream_t s);
 
 // ---- operator evaluation sequence (api.cu), shared by st_op_eval and st_op_eval_noalloc ----
 struct EvalBufs {
   float *x, *tmp, *ssq;
   void *xn, *q, *kp, *vp, *o, *h;
-  int32_t *pos, *tup, *len, *nk, *order;
+  int32_t *pos, *tok, *rowpair;                       // per prompt row
+  int32_t *tup, *len, *nk, *prow, *pP, *pop, *pj;     // per (operator, tuple) pair
+  int32_t* order;                                     // attention work list
 };
-// Lays the buffers for `rows` prompt rows of `tuples` tuples out from `base`
-// (nullptr: layout only); returns the bytes needed.
-size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t tuples, char* base, EvalBufs* w);
-// One batch of nc tuples through every layer and the label head.
-int eval_chunk(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_t* tuple_ids,
-               int nc, const EvalBufs& w, float* logits, int32_t* labels, cudaStream_t s);
+// Lays the buffers for `rows` prompt rows of `pairs` (operator, tuple) pairs out
+// from `base` (nullptr: layout only); returns the bytes needed.
+size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t pairs, char* base, EvalBufs* w);
+// Validates the operators of one call and lays them out as an OpSet (operator
+// k's pairs follow operator k-1's, its prompt rows likewise).
+int make_opset(st_ctx* ctx, const st_kv* kv, int n_ops, const st_operator* const* ops,
+               const int32_t* const* tuple_ids, const int32_t* n, float* const* logits,
+               int32_t* const* labels, OpSet* os, int64_t* rows_total, int* pairs_total);
+// Pairs [p0, p1) of an operator set (their prompt rows start at row_base, `rows`
+// of them) through every layer and the label head.
+int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, int64_t row_base,
+               int64_t rows, const EvalBufs& w, cudaStream_t s);
+// Prompt rows of pairs [p0, p1) of an operator set.
+int64_t opset_rows(const OpSet& os, int p0, int p1);
 
 // ---- retention (retain.cu) ----
 struct RetainParams {

@@ -51,43 +51,88 @@ void build_rowinfo(const int64_t* off, int t0, int t1, int64_t r0, int64_t rows,
   k_build_rowinfo<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(off, t0, t1, r0, rows, rowtup, pos);
 }
 
-__global__ void k_eval_rowinfo(const int32_t* __restrict__ tuple_ids, int n, int P,
-                               const int64_t* __restrict__ off, double r, int32_t* tup,
-                               int32_t* len, int32_t* nk, int32_t* pos) {
-  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= (int64_t)n * P) return;
-  int i = (int)(m / P), p = (int)(m % P);
-  int t = tuple_ids[i];
-  int L = (int)(off[t + 1] - off[t]);
-  pos[m] = L + p;
-  if (p == 0) {
-    tup[i] = t;
-    len[i] = L;
-    nk[i] = n_keep_dev(L, r);
-  }
+// Operator k of an operator set owning global pair gp (pairs are laid out
+// operator after operator).
+__device__ __forceinline__ int op_of_pair(const OpSet& os, int gp) {
+  int k = 0;
+  while (k + 1 < os.n_ops && gp >= os.op[k + 1].pair0) ++k;
+  return k;
+}
+__device__ __forceinline__ int op_of_row(const OpSet& os, int64_t gr) {
+  int k = 0;
+  while (k + 1 < os.n_ops && gr >= os.op[k + 1].row0) ++k;
+  return k;
 }
 
-void eval_rowinfo(const int32_t* tuple_ids, int n, int P, const int64_t* off, double r,
-                  int32_t* tup, int32_t* len, int32_t* nk, int32_t* pos, cudaStream_t s) {
-  int64_t rows = (int64_t)n * P;
+// Thread per pair of [p0, p0 + np): tuple, length, retained count n_keep(L, r)
+// of its operator, prompt row (relative to row_base), prompt length, operator,
+// index within the operator.
+__global__ void k_eval_pairs(OpSet os, int p0, int np, int64_t row_base,
+                             const int64_t* __restrict__ off, int32_t* tup, int32_t* len,
+                             int32_t* nk, int32_t* prow, int32_t* pP, int32_t* pop, int32_t* pj) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const int gp = p0 + i, k = op_of_pair(os, gp);
+  const OpDev& o = os.op[k];
+  const int j = gp - o.pair0;
+  const int t = o.tuple_ids[j];
+  const int L = (int)(off[t + 1] - off[t]);
+  tup[i] = t;
+  len[i] = L;
+  nk[i] = n_keep_dev(L, o.r);
+  prow[i] = (int32_t)(o.row0 + (int64_t)j * o.P - row_base);
+  pP[i] = o.P;
+  pop[i] = k;
+  pj[i] = j;
+}
+
+// Thread per prompt row of [row_base, row_base + rows): RoPE position L_t + p,
+// the prompt token, and the row's pair (relative to p0).
+__global__ void k_eval_rows(OpSet os, int p0, int64_t row_base, int64_t rows,
+                            const int64_t* __restrict__ off, int32_t* pos, int32_t* tok,
+                            int32_t* rowpair) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= rows) return;
+  const int64_t gr = row_base + m;
+  const int k = op_of_row(os, gr);
+  const OpDev& o = os.op[k];
+  const int j = (int)((gr - o.row0) / o.P), p = (int)((gr - o.row0) % o.P);
+  const int t = o.tuple_ids[j];
+  pos[m] = (int32_t)(off[t + 1] - off[t]) + p;
+  tok[m] = o.prompt[p];
+  rowpair[m] = o.pair0 + j - p0;
+}
+
+void eval_pairs(const OpSet& os, int p0, int np, int64_t row_base, const int64_t* off, int32_t* tup,
+                int32_t* len, int32_t* nk, int32_t* prow, int32_t* pP, int32_t* pop, int32_t* pj,
+                cudaStream_t s) {
+  if (np <= 0) return;
+  k_eval_pairs<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(os, p0, np, row_base, off, tup, len, nk,
+                                                           prow, pP, pop, pj);
+}
+void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const int64_t* off,
+               int32_t* pos, int32_t* tok, int32_t* rowpair, cudaStream_t s) {
   if (rows <= 0) return;
-  k_eval_rowinfo<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(tuple_ids, n, P, off, r, tup, len,
-                                                                 nk, pos);
+  k_eval_rows<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(os, p0, row_base, rows, off, pos, tok,
+                                                             rowpair);
 }
 
-// Positions of the n evaluated items ordered by retained length, longest
-// first (a counting sort on the 128-key tile count, capped at 1023), so that a
-// persistent attention grid walking them in turn ends with its shortest items.
-// One block of 1024 threads; the order within a bucket is arbitrary.
-__global__ void __launch_bounds__(1024) k_eval_order(const int32_t* __restrict__ nk, int n,
-                                                     int32_t* order) {
+// Attention work list: every pair contributes ceil(P G / 128) entries (pair,
+// 128-row block), grouped longest retained document first (a counting sort on
+// the 128-key tile count, capped at 1023), so that a persistent grid walking
+// the list ends with its shortest items.  One block of 1024 threads; the order
+// within a bucket is arbitrary.
+__global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restrict__ nk,
+                                                        const int32_t* __restrict__ pP, int n, int G,
+                                                        int32_t* list) {
   __shared__ int cnt[1024];
   __shared__ int wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   cnt[tid] = 0;
   __syncthreads();
   auto bucket = [&](int i) { return 1023 - min((nk[i] + 127) / 128, 1023); };
-  for (int i = tid; i < n; i += 1024) atomicAdd(&cnt[bucket(i)], 1);
+  auto blocks = [&](int i) { return (pP[i] * G + 127) / 128; };
+  for (int i = tid; i < n; i += 1024) atomicAdd(&cnt[bucket(i)], blocks(i));
   __syncthreads();
   // exclusive prefix sum over the buckets
   const int x = cnt[tid];
@@ -111,12 +156,19 @@ __global__ void __launch_bounds__(1024) k_eval_order(const int32_t* __restrict__
   __syncthreads();
   cnt[tid] = wsum[wid] + inc - x;
   __syncthreads();
-  for (int i = tid; i < n; i += 1024) order[atomicAdd(&cnt[bucket(i)], 1)] = i;
+  for (int i = tid; i < n; i += 1024) {
+    const int nb = blocks(i);
+    const int at = atomicAdd(&cnt[bucket(i)], nb);
+    for (int z = 0; z < nb; ++z) {
+      list[2 * (at + z)] = i;
+      list[2 * (at + z) + 1] = z;
+    }
+  }
 }
 
-void eval_order(const int32_t* nk, int n, int32_t* order, cudaStream_t s) {
-  if (n <= 0) return;
-  k_eval_order<<<1, 1024, 0, s>>>(nk, n, order);
+void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int32_t* list, cudaStream_t s) {
+  if (np <= 0) return;
+  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, np, G, list);
 }
 
 // Retained counts and padded (64-slot) offsets of every tuple, one block.
@@ -157,15 +209,14 @@ void nkeep_offp(const int64_t* off, int T, double r, int32_t* nkeep, int64_t* of
 
 // ------------------------------------------------------------------ embedding
 template <typename act_t>
-__global__ void k_embed(const int32_t* __restrict__ tok, int P, int64_t rows,
+__global__ void k_embed(const int32_t* __restrict__ tok, int64_t rows,
                         const act_t* __restrict__ E, int d, float* __restrict__ x) {
-  // P > 0: row m reads token tok[m % P] (the prompt, same for every tuple)
   const int per = d / 4;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * per) return;
   int64_t m = i / per;
   int c = (int)(i % per) * 4;
-  int t = P > 0 ? tok[m % P] : tok[m];
+  const int t = tok[m];
   const act_t* e = E + (int64_t)t * d + c;
   float4 v = make_float4(to_f(e[0]), to_f(e[1]), to_f(e[2]), to_f(e[3]));
   *reinterpret_cast<float4*>(x + m * d + c) = v;
@@ -175,21 +226,10 @@ template <typename act_t>
 void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, float* x, cudaStream_t s) {
   int64_t n = rows * (d / 4);
   if (n <= 0) return;
-  k_embed<act_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tok, 0, rows, E, d, x);
+  k_embed<act_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tok, rows, E, d, x);
 }
 template void embed_rows<float>(const int32_t*, int64_t, const float*, int, float*, cudaStream_t);
 template void embed_rows<bf16>(const int32_t*, int64_t, const bf16*, int, float*, cudaStream_t);
-
-void embed_prompt(const int32_t* prompt, int P, int64_t rows, const void* E, int dtype, int d,
-                  float* x, cudaStream_t s) {
-  int64_t n = rows * (d / 4);
-  if (n <= 0) return;
-  unsigned g = (unsigned)((n + 255) / 256);
-  if (dtype == ST_BF16)
-    k_embed<bf16><<<g, 256, 0, s>>>(prompt, P, rows, (const bf16*)E, d, x);
-  else
-    k_embed<float><<<g, 256, 0, s>>>(prompt, P, rows, (const float*)E, d, x);
-}
 
 // ------------------------------------------------------------------ RMSNorm
 __device__ __forceinline__ void store4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -464,59 +504,58 @@ void pool_rows(const float* x, const float* inv_rms, const float* ssq, int parts
 }
 
 // ------------------------------------------------------------------ label head
-// Block per evaluated tuple: final RMSNorm of the last prompt row, label-token
-// logits, and the decision (filter thresholds or classify argmax).
+// Block per (operator, tuple) pair: final RMSNorm of its last prompt row, its
+// operator's label-token logits, and the decision (filter thresholds or
+// classify argmax).
 template <typename w_t>
-__global__ void k_label_head(const float* __restrict__ x, int P, int d, float eps,
-                             const w_t* __restrict__ w_lm, const int32_t* __restrict__ labels,
-                             int n_labels, const float* __restrict__ bias, int kind,
-                             float theta_pos, float theta_neg, float* __restrict__ logits,
-                             int32_t* __restrict__ out_labels) {
+__global__ void k_label_head(const float* __restrict__ x, OpSet os, const int32_t* __restrict__ prow,
+                             const int32_t* __restrict__ pP, const int32_t* __restrict__ pop,
+                             const int32_t* __restrict__ pj, int d, float eps,
+                             const w_t* __restrict__ w_lm) {
   __shared__ float red[32];
   __shared__ float z[8];
   const int i = blockIdx.x;
-  const float* xr = x + ((int64_t)i * P + P - 1) * d;
+  const OpDev& o = os.op[pop[i]];
+  const float* xr = x + ((int64_t)prow[i] + pP[i] - 1) * d;
   float ss = 0.f;
   for (int c = threadIdx.x; c < d; c += blockDim.x) ss += xr[c] * xr[c];
   ss = block_sum<256>(ss, red);
   const float inv = 1.0f / sqrtf(ss / (float)d + eps);
-  for (int k = 0; k < n_labels; ++k) {
-    const w_t* wr = w_lm + (int64_t)labels[k] * d;
+  for (int k = 0; k < o.n_labels; ++k) {
+    const w_t* wr = w_lm + (int64_t)o.labels[k] * d;
     float acc = 0.f;
     for (int c = threadIdx.x; c < d; c += blockDim.x) acc += xr[c] * to_f(wr[c]);
     acc = block_sum<256>(acc, red);
     if (threadIdx.x == 0) z[k] = acc * inv;
   }
   if (threadIdx.x == 0) {
-    for (int k = 0; k < n_labels; ++k) logits[(int64_t)i * n_labels + k] = z[k];
+    const int j = pj[i];
+    for (int k = 0; k < o.n_labels; ++k) o.logits[(int64_t)j * o.n_labels + k] = z[k];
     int dec;
-    if (kind == ST_OP_FILTER) {
+    if (o.kind == ST_OP_FILTER) {
       float sc = z[0] - z[1];
-      float a = sc - theta_pos, rj = theta_neg - sc, u = 0.f;
+      float a = sc - o.theta_pos, rj = o.theta_neg - sc, u = 0.f;
       dec = (u >= a && u >= rj) ? ST_UNSURE : (rj >= a ? ST_REJECT : ST_ACCEPT);
     } else {
       dec = 0;
-      float best = z[0] + (bias ? bias[0] : 0.f);
-      for (int k = 1; k < n_labels; ++k) {
-        float v = z[k] + (bias ? bias[k] : 0.f);
+      float best = z[0] + (o.bias ? o.bias[0] : 0.f);
+      for (int k = 1; k < o.n_labels; ++k) {
+        float v = z[k] + (o.bias ? o.bias[k] : 0.f);
         if (v > best) { best = v; dec = k; }
       }
     }
-    out_labels[i] = dec;
+    o.out_labels[j] = dec;
   }
 }
 
-void label_head(const float* x, int n, int P, int d, float eps, const void* w_lm, int dtype,
-                const int32_t* labels, int n_labels, const float* bias, int kind,
-                float theta_pos, float theta_neg, float* logits, int32_t* out_labels,
+void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, const int32_t* pP,
+                const int32_t* pop, const int32_t* pj, int d, float eps, const void* w_lm, int dtype,
                 cudaStream_t s) {
-  if (n <= 0) return;
+  if (np <= 0) return;
   if (dtype == ST_BF16)
-    k_label_head<bf16><<<n, 256, 0, s>>>(x, P, d, eps, (const bf16*)w_lm, labels, n_labels, bias,
-                                         kind, theta_pos, theta_neg, logits, out_labels);
+    k_label_head<bf16><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const bf16*)w_lm);
   else
-    k_label_head<float><<<n, 256, 0, s>>>(x, P, d, eps, (const float*)w_lm, labels, n_labels,
-                                          bias, kind, theta_pos, theta_neg, logits, out_labels);
+    k_label_head<float><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const float*)w_lm);
 }
 
 // ------------------------------------------------------------------ SwiGLU (float32 path)

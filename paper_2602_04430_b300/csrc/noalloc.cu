@@ -74,11 +74,11 @@ extern "C" int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operato
   if (n == 0) return ST_OK;
   if (!tuple_ids_dev || !logits_dev || !labels_dev) return na_fail(ctx, ST_EINVAL, "st_op_eval_noalloc: NULL buffer");
   if (kv->r <= 0.0) return na_fail(ctx, ST_EINVAL, "st_op_eval_noalloc: no retained profile (call st_kv_retain)");
-  if (op->desc.r > kv->r) return na_fail(ctx, ST_EINVAL, "st_op_eval_noalloc: operator r exceeds the retained profile's r");
-  const st_model_cfg& c = ctx->cfg;
-  if (kv->max_len + op->desc.P > c.max_pos) return na_fail(ctx, ST_EINVAL, "st_op_eval_noalloc: document + prompt exceeds max_pos");
+  OpSet os;
+  int64_t M = 0;
+  int pairs = 0;
+  NA_RC(make_opset(ctx, kv, 1, &op, &tuple_ids_dev, &n, &logits_dev, &labels_dev, &os, &M, &pairs));
   const int P = op->desc.P;
-  const int64_t M = (int64_t)n * P;
   const size_t need = eval_bufs(ctx, M, n, nullptr, nullptr);
   if (need > kScratchBytes)
     return na_fail(ctx, ST_EINVAL,
@@ -89,12 +89,12 @@ extern "C" int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operato
   NA_RC(scratch_address(ctx, &base));
   EvalBufs w;
   eval_bufs(ctx, M, n, (char*)base, &w);
-  // the same layer sequence as st_op_eval, with profiling events switched off so
-  // that this entry creates no CUDA resources (its launches are still counted)
+  // the same layer sequence as st_op_eval (one chunk), with profiling events
+  // switched off so that this entry creates no CUDA resources (its launches
+  // are still counted)
   const bool prof = ctx->prof.on;
   ctx->prof.on = false;
-  const int rc = eval_chunk(ctx, kv, op, tuple_ids_dev, n, w, logits_dev, labels_dev,
-                            reinterpret_cast<cudaStream_t>(stream));
+  const int rc = eval_chunk(ctx, kv, os, 0, n, 0, M, w, reinterpret_cast<cudaStream_t>(stream));
   ctx->prof.on = prof;
   return rc;
 }

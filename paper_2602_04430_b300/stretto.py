@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
         "st_op_free": (None, [VP]),
         "st_op_eval": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
         "st_op_eval_noalloc": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
+        "st_op_eval_multi": (i32, [VP, VP, i32, ctypes.POINTER(VP), ctypes.POINTER(VP),
+                                   ctypes.POINTER(i32), ctypes.POINTER(VP), ctypes.POINTER(VP), VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
         "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
         "st_proxy_create": (i32, [VP, i32, i32, i32, ctypes.POINTER(VP), ctypes.POINTER(VP)]),
@@ -375,6 +377,23 @@ def cascade_merge(model: Model, proxy_label, unsure_pos, count, full_label, out=
     model.check(model.L.st_cascade_merge(model.h, _ptr(proxy_label), n, _ptr(unsure_pos),
                                          _ptr(count), _ptr(full_label), _ptr(out), _stream(stream)))
     return out
+
+
+def eval_multi(model: Model, kv: KVCache, ops, tuple_ids, logits=None, labels=None, stream=None):
+    """Several operators, each over its own device tuple ids, in one batched pass
+    (``st_op_eval_multi``); returns the lists of (logits, labels) device tensors."""
+    import torch
+    k = len(ops)
+    ns = [int(t.numel()) for t in tuple_ids]
+    if logits is None:
+        logits = [torch.empty((n, o.n_labels), dtype=torch.float32, device="cuda") for n, o in zip(ns, ops)]
+    if labels is None:
+        labels = [torch.empty((n,), dtype=torch.int32, device="cuda") for n in ns]
+    arr = lambda xs: (VP * k)(*[_ptr(x) for x in xs])
+    model.check(model.L.st_op_eval_multi(model.h, kv.h, k, (VP * k)(*[o.h for o in ops]), arr(tuple_ids),
+                                         (ctypes.c_int32 * k)(*ns), arr(logits), arr(labels),
+                                         _stream(stream)))
+    return logits, labels
 
 
 def version() -> str:
