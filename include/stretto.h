@@ -228,6 +228,58 @@ int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops, const st_opera
                      const int32_t* const* tuple_ids_dev, const int32_t* n,
                      float* const* logits_dev, int32_t* const* labels_dev, void* stream);
 
+/* ---- a batched evaluation as a CUDA graph ----
+ *
+ * st_graph_create records the whole batched evaluation (the same kernels as
+ * st_op_eval_multi with these arguments) into a CUDA graph once;
+ * st_graph_launch replays it on `stream`, one graph launch instead of one
+ * host launch per kernel.  The graph keeps the DEVICE pointers it was
+ * created with (tuple ids, outputs, the cache): the caller may change the
+ * contents of those buffers between replays (other tuple ids, a new
+ * retention of the same cache), not their addresses or counts, and must keep
+ * them, the cache and the context alive until st_graph_free.  The graph owns
+ * its activation workspace (allocated by st_graph_create, which also runs
+ * the evaluation once uncaptured and synchronises).  Replays on one graph
+ * must not overlap (they share the workspace).
+ * st_graph_launches: kernels per replay.
+ * Errors: as st_op_eval_multi; ST_ECUDA if capture or instantiation fails. */
+typedef struct st_graph st_graph;
+int st_graph_create(st_ctx* ctx, const st_kv* kv, int32_t n_ops, const st_operator* const* ops,
+                    const int32_t* const* tuple_ids_dev, const int32_t* n, float* const* logits_dev,
+                    int32_t* const* labels_dev, st_graph** out);
+int st_graph_launch(st_graph* g, void* stream);
+int64_t st_graph_launches(const st_graph* g);
+void st_graph_free(st_graph* g);
+
+/* ---- schedule of operator evaluation, and its autotuner ----
+ *
+ * eval_rows: prompt rows per pass through the layers (the evaluation is cut
+ * into chunks of at most this many rows; 0 = library default 262144);
+ * attn_nb: BF16-KV attention layout, 1 = two CTAs per SM with single S / P /
+ * O buffers (default), 2 = one CTA per SM with double buffers (E4M3 KV always
+ * uses 2); longest_first: attention work items ordered by retained document
+ * length, longest first (1, default) or in arrival order (0).  ms: measured
+ * time of one evaluation (autotuner output).
+ * st_autotune_eval times the batched evaluation of its arguments (which it
+ * runs, writing the outputs) under candidate schedules — a coordinate search:
+ * layout x order at the current chunk size, then chunk sizes 2^15 .. 2^19 —
+ * each one warm-up and three timed runs (CUDA events on `stream`; it
+ * synchronises), keeps the fastest in the context for later evaluations and
+ * graphs, and returns it in *best; the first max_tried timed candidates go to
+ * tried[] and their count to *n_tried (either may be NULL).
+ * st_set_schedule sets a schedule directly. */
+typedef struct {
+  int64_t eval_rows;
+  int32_t attn_nb;
+  int32_t longest_first;
+  float ms;
+} st_tune_choice;
+int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops, const st_operator* const* ops,
+                     const int32_t* const* tuple_ids_dev, const int32_t* n, float* const* logits_dev,
+                     int32_t* const* labels_dev, void* stream, st_tune_choice* best,
+                     st_tune_choice* tried, int32_t max_tried, int32_t* n_tried);
+int st_set_schedule(st_ctx* ctx, const st_tune_choice* schedule);
+
 /* ---- operator evaluation without device allocation ----
  *
  * The paper has no counterpart to this entry; it exists for callers that

@@ -895,7 +895,7 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
   }
   if (c.dtype == ST_BF16) {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_worklist(w.nk, w.pP, np, G, w.order, s);
+    eval_worklist(w.nk, w.pP, np, G, ctx->longest_first != 0, w.order, s);
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
@@ -948,6 +948,7 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
     a.vp = w.vp;
     a.n = np;
     a.kv_dtype = kv->kv_dtype;
+    a.nb = ctx->attn_nb;
     RC(attention(ctx, a, nullptr, 0, s));
     if (l + 1 < c.layers) {
       EpiParams eo;
@@ -1029,7 +1030,7 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
 
 // Chunks the pairs (operator-major) into batches of at most `cap` prompt rows
 // and runs each through eval_chunk.
-int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s) {
+int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s, DevBuf* ws) {
   const st_model_cfg& c = ctx->cfg;
   int maxP = 1;
   for (int k = 0; k < os.n_ops; ++k) maxP = std::max(maxP, os.op[k].P);
@@ -1052,9 +1053,10 @@ int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStre
     max_rows = std::max(max_rows, opset_rows(os, cuts[q], cuts[q + 1]));
     max_pairs = std::max(max_pairs, cuts[q + 1] - cuts[q]);
   }
-  RC(grow(ctx, ctx->ws_eval, eval_bufs(ctx, max_rows, max_pairs, nullptr, nullptr)));
+  DevBuf& buf = ws ? *ws : ctx->ws_eval;
+  RC(grow(ctx, buf, eval_bufs(ctx, max_rows, max_pairs, nullptr, nullptr)));
   EvalBufs w;
-  eval_bufs(ctx, max_rows, max_pairs, (char*)ctx->ws_eval.p, &w);
+  eval_bufs(ctx, max_rows, max_pairs, (char*)buf.p, &w);
   int64_t row_base = 0;
   for (size_t q = 0; q + 1 < cuts.size(); ++q) {
     const int64_t M = opset_rows(os, cuts[q], cuts[q + 1]);
@@ -1078,7 +1080,7 @@ extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
   int64_t rows = 0;
   int pairs = 0;
   RC(make_opset(ctx, kv, 1, &op, &tuple_ids_dev, &n, &logits_dev, &labels_dev, &os, &rows, &pairs));
-  return run_opset(ctx, kv, os, pairs, S(stream));
+  return run_opset(ctx, kv, os, pairs, S(stream), nullptr);
 }
 
 extern "C" int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
@@ -1091,7 +1093,7 @@ extern "C" int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
   int pairs = 0;
   RC(make_opset(ctx, kv, n_ops, ops, tuple_ids_dev, n, logits_dev, labels_dev, &os, &rows, &pairs));
   if (pairs == 0) return ST_OK;
-  return run_opset(ctx, kv, os, pairs, S(stream));
+  return run_opset(ctx, kv, os, pairs, S(stream), nullptr);
 }
 
 extern "C" int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,

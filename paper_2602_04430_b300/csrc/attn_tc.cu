@@ -39,29 +39,31 @@ constexpr int HD = 64;
 constexpr int TK = 128;          // keys per tile
 constexpr int BOX = 64;          // key rows per TMA box
 constexpr int ROWS = 128;        // query rows per work item
-// BF16 KV: two CTAs per SM (each with one S, P and O buffer in 256 TMEM
-// columns and two K/V stages), so every SM sub-partition runs two independent
-// softmax warps. E4M3 KV: one CTA per SM with double buffers and 4 stages
-// (its raw code stages leave no room for a second CTA).
-constexpr int ctas_per_sm(bool fp8) { return fp8 ? 1 : 2; }
-constexpr int nbuf(bool fp8) { return fp8 ? 2 : 1; }     // S, P and O buffers
-constexpr int NKV_MAX = 4;
-constexpr int nkv(bool fp8) { return fp8 ? 4 : 2; }
+// Two layouts, by the number NB of S, P and O buffers:
+//   NB = 1: two CTAs per SM, each with one S, P and O buffer in 256 TMEM
+//           columns and two K/V stages, so every SM sub-partition runs two
+//           independent softmax warps (BF16 KV default);
+//   NB = 2: one CTA per SM with double buffers in 512 TMEM columns and 5 K/V
+//           stages (4 with E4M3 KV, whose two raw code stages leave no room for
+//           a second CTA; E4M3 always uses it).
+constexpr int ctas_per_sm(int nb) { return nb == 1 ? 2 : 1; }
+constexpr int NKV_MAX = 5;
+constexpr int nkv(bool fp8, int nb) { return nb == 1 ? 2 : (fp8 ? 4 : 5); }
 // warps 0-3 softmax, 4 item decode + Q and K/V loads, 5 MMA issue,
 // (E4M3 KV) 6-7 widen codes to f16
 constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
 constexpr int OFF_Q = 0;                           // 2 x 16 KB
 constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // nkv x 16 KB
-constexpr int off_v(bool fp8) { return OFF_K + nkv(fp8) * TK * 128; }      // nkv x 16 KB
-constexpr int off_raw(bool fp8) { return off_v(fp8) + nkv(fp8) * TK * 128; }  // (E4M3) 2 x 16 KB
+constexpr int off_v(bool fp8, int nb) { return OFF_K + nkv(fp8, nb) * TK * 128; }       // nkv x 16 KB
+constexpr int off_raw(bool fp8, int nb) { return off_v(fp8, nb) + nkv(fp8, nb) * TK * 128; }  // (E4M3) 2 x 16 KB
 constexpr int RAW_BYTES = 2 * TK * HD;             // K + V codes of one tile
-constexpr int off_bar(bool fp8) { return off_raw(fp8) + (fp8 ? 2 * RAW_BYTES : 0); }
-constexpr int off_work(bool fp8) { return off_bar(fp8) + 512; }   // 2 decoded work items
-constexpr size_t smem_bytes(bool fp8) { return (size_t)off_work(fp8) + 256 + 1024; }
+constexpr int off_bar(bool fp8, int nb) { return off_raw(fp8, nb) + (fp8 ? 2 * RAW_BYTES : 0); }
+constexpr int off_work(bool fp8, int nb) { return off_bar(fp8, nb) + 512; }   // 2 decoded work items
+constexpr size_t smem_bytes(bool fp8, int nb) { return (size_t)off_work(fp8, nb) + 256 + 1024; }
 // TMEM columns: S buffers [0, 128 nb), O buffers [128 nb, 192 nb), P buffers [192 nb, 256 nb)
-constexpr uint32_t tmem_cols(bool fp8) { return 256 * nbuf(fp8); }
-constexpr uint32_t col_o(bool fp8) { return TK * nbuf(fp8); }
-constexpr uint32_t col_p(bool fp8) { return (TK + HD) * nbuf(fp8); }
+constexpr uint32_t tmem_cols(int nb) { return 256 * nb; }
+constexpr uint32_t col_o(int nb) { return TK * nb; }
+constexpr uint32_t col_p(int nb) { return (TK + HD) * nb; }
 
 struct Bars {
   // K and V halves of a stage fill and free separately: K after the tile's
@@ -214,8 +216,8 @@ struct Work {
 // MMA, softmax (and E4M3 widening) roles each walk the same sequence,
 // connected by mbarrier rings (decoded item + Q: 2 slots, K/V: 3 stages, S, P
 // and O: 2 TMEM buffers each), so the next item's loads overlap this item's math.
-template <int MODE, bool FP8>
-__global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
+template <int MODE, bool FP8, int NB>
+__global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     k_attn_tc(AttnParams a, const int32_t* __restrict__ items, int n_work, int zb_count,
               const __grid_constant__ CUtensorMap tmQ,
               const __grid_constant__ CUtensorMap tmK, const __grid_constant__ CUtensorMap tmV,
@@ -224,12 +226,13 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(FP8))
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  Bars* bars = reinterpret_cast<Bars*>(smem + off_bar(FP8));
-  Work<MODE>* slots = reinterpret_cast<Work<MODE>*>(smem + off_work(FP8));
+  Bars* bars = reinterpret_cast<Bars*>(smem + off_bar(FP8, NB));
+  Work<MODE>* slots = reinterpret_cast<Work<MODE>*>(smem + off_work(FP8, NB));
   static_assert(sizeof(Work<MODE>) <= 128, "work slot");
   const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
-  constexpr int NKV = nkv(FP8), OFF_V = off_v(FP8), OFF_RAW = off_raw(FP8), NB = nbuf(FP8);
-  constexpr uint32_t TMEM_COLS = tmem_cols(FP8), COL_O = col_o(FP8), COL_P = col_p(FP8);
+  static_assert(NB == 2 || !FP8, "E4M3 KV runs with double buffers");
+  constexpr int NKV = nkv(FP8, NB), OFF_V = off_v(FP8, NB), OFF_RAW = off_raw(FP8, NB);
+  constexpr uint32_t TMEM_COLS = tmem_cols(NB), COL_O = col_o(NB), COL_P = col_p(NB);
   const uint32_t sK0 = ptx::smem_u32(smem + OFF_K), sV0 = ptx::smem_u32(smem + OFF_V);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -826,12 +829,12 @@ bool map2d_u8(CUtensorMap* m, const void* base, uint64_t outer, uint32_t box_out
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MODE, bool FP8>
+template <int MODE, bool FP8, int NB>
 void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_attn_tc<MODE, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_bytes(FP8));
+    cudaFuncSetAttribute(k_attn_tc<MODE, FP8, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_bytes(FP8, NB));
     done = true;
   }
 }
@@ -860,16 +863,22 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   else ok = ok && map2d(&mk, a.Kr, HD, planes, BOX) && map2d(&mv, a.Vr, HD, planes, BOX);
   if (!ok) return ST_ECUDA;
   const int n_work = a.n_work * a.hkv;
-  const int slots = sm_count() * ctas_per_sm(fp8);
+  // buffer layout: E4M3 always double-buffered; BF16 by a.nb (0: two CTAs per SM)
+  const int nb = fp8 ? 2 : (a.nb == 2 ? 2 : 1);
+  const int slots = sm_count() * ctas_per_sm(nb);
   const int grid = n_work < slots ? n_work : slots;
   const int zb = 1;   // unused in eval (the work list carries the row block)
   if (fp8) {
-    set_smem_attr<1, true>();
-    k_attn_tc<1, true><<<grid, nthreads(true), smem_bytes(true), s>>>(a, a.work, n_work, zb, mq, mk,
+    set_smem_attr<1, true, 2>();
+    k_attn_tc<1, true, 2><<<grid, nthreads(true), smem_bytes(true, 2), s>>>(a, a.work, n_work, zb, mq, mk,
                                                                       mv, mkp, mvp, status);
+  } else if (nb == 2) {
+    set_smem_attr<1, false, 2>();
+    k_attn_tc<1, false, 2><<<grid, nthreads(false), smem_bytes(false, 2), s>>>(a, a.work, n_work, zb, mq,
+                                                                              mk, mv, mkp, mvp, status);
   } else {
-    set_smem_attr<1, false>();
-    k_attn_tc<1, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, a.work, n_work, zb, mq,
+    set_smem_attr<1, false, 1>();
+    k_attn_tc<1, false, 1><<<grid, nthreads(false), smem_bytes(false, 1), s>>>(a, a.work, n_work, zb, mq,
                                                                          mk, mv, mkp, mvp, status);
   }
   return ST_OK;
@@ -885,11 +894,11 @@ int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int*
   if (!map_q(&mq, a.q, a.hq, (uint64_t)a.rows, G) || !map2d(&mk, a.K, HD, planes, BOX) ||
       !map2d(&mv, a.V, HD, planes, BOX))
     return ST_ECUDA;
-  set_smem_attr<0, false>();
+  set_smem_attr<0, false, 1>();
   const int n_work = n_items * a.hkv;
-  const int slots = sm_count() * ctas_per_sm(false);
+  const int slots = sm_count() * ctas_per_sm(1);
   const int grid = n_work < slots ? n_work : slots;
-  k_attn_tc<0, false><<<grid, nthreads(false), smem_bytes(false), s>>>(a, items, n_work, 1, mq, mk,
+  k_attn_tc<0, false, 1><<<grid, nthreads(false), smem_bytes(false, 1), s>>>(a, items, n_work, 1, mq, mk,
                                                                        mv, mk, mv, status);
   return ST_OK;
 }

@@ -111,6 +111,10 @@ struct st_ctx {
   // workspaces
   st::DevBuf ws_build, ws_eval;
   int64_t build_rows_cap = 0, eval_rows_cap = 0;
+  // operator-evaluation schedule (st_autotune_eval): BF16-KV attention layout
+  // (0 / 1 = two CTAs per SM, 2 = one CTA per SM) and longest-first work order
+  int attn_nb = 0;
+  int longest_first = 1;
   int32_t* dstatus = nullptr;     // device status word of bounded waits (ST_ETIMEOUT)
   std::string err;
   st::Prof prof;

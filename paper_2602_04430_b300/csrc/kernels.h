@@ -93,7 +93,8 @@ void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const in
                int32_t* pos, int32_t* tok, int32_t* rowpair, cudaStream_t s);
 // Attention work list: (pair, 128-row block) entries, longest retained
 // documents first; G = query heads per kv head.
-void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int32_t* list, cudaStream_t s);
+void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, bool longest_first,
+                   int32_t* list, cudaStream_t s);
 template <typename act_t>
 void qstats(const act_t* q, const int64_t* off, int t0, int t1, int64_t r0, int hq, int hkv,
             int hd, float* mu, float* s2, cudaStream_t s);
@@ -153,6 +154,7 @@ struct AttnParams {
   const int32_t* work = nullptr;  // tensor-core path: (pair, 128-row block) entries
   int n_work = 0;                 // entries in work
   int64_t qrows = 0;              // prompt rows of the call
+  int nb = 0;                     // BF16-KV attention layout: 0 / 1 = two CTAs per SM, 2 = one
   const void* kp = nullptr;       // prompt keys kp[(i*P + p)*hkv*hd + g*hd + c]
   const void* vp = nullptr;
   int n = 0, P = 0;
@@ -187,6 +189,10 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
                int64_t rows, const EvalBufs& w, cudaStream_t s);
 // Prompt rows of pairs [p0, p1) of an operator set.
 int64_t opset_rows(const OpSet& os, int p0, int p1);
+// All pairs of an operator set, in chunks of at most the context's
+// eval_rows_cap prompt rows; ws: the workspace (nullptr: the context's, grown
+// as needed; otherwise grown as needed too, and owned by the caller).
+int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s, DevBuf* ws);
 
 // ---- retention (retain.cu) ----
 struct RetainParams {

@@ -120,17 +120,17 @@ void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const in
 // Attention work list: every pair contributes ceil(P G / 128) entries (pair,
 // 128-row block), grouped longest retained document first (a counting sort on
 // the 128-key tile count, capped at 1023), so that a persistent grid walking
-// the list ends with its shortest items.  One block of 1024 threads; the order
-// within a bucket is arbitrary.
+// the list ends with its shortest items (sorted = 0: one bucket, arrival
+// order).  One block of 1024 threads; the order within a bucket is arbitrary.
 __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restrict__ nk,
                                                         const int32_t* __restrict__ pP, int n, int G,
-                                                        int32_t* list) {
+                                                        int sorted, int32_t* list) {
   __shared__ int cnt[1024];
   __shared__ int wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   cnt[tid] = 0;
   __syncthreads();
-  auto bucket = [&](int i) { return 1023 - min((nk[i] + 127) / 128, 1023); };
+  auto bucket = [&](int i) { return sorted ? 1023 - min((nk[i] + 127) / 128, 1023) : 0; };
   auto blocks = [&](int i) { return (pP[i] * G + 127) / 128; };
   for (int i = tid; i < n; i += 1024) atomicAdd(&cnt[bucket(i)], blocks(i));
   __syncthreads();
@@ -166,9 +166,10 @@ __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restric
   }
 }
 
-void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int32_t* list, cudaStream_t s) {
+void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, bool longest_first,
+                   int32_t* list, cudaStream_t s) {
   if (np <= 0) return;
-  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, np, G, list);
+  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, np, G, longest_first ? 1 : 0, list);
 }
 
 // Retained counts and padded (64-slot) offsets of every tuple, one block.

@@ -53,6 +53,16 @@ _LIB = None
 VP = ctypes.c_void_p
 
 
+class TuneChoice(ctypes.Structure):
+    """st_tune_choice: an operator-evaluation schedule and its measured time."""
+    _fields_ = [("eval_rows", ctypes.c_int64), ("attn_nb", ctypes.c_int32),
+                ("longest_first", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"eval_rows": int(self.eval_rows), "attn_nb": int(self.attn_nb),
+                "longest_first": int(self.longest_first), "ms": float(self.ms)}
+
+
 def lib() -> ctypes.CDLL:
     """Load libstretto.so (raises ImportError if it has not been built)."""
     global _LIB
@@ -82,6 +92,17 @@ def lib() -> ctypes.CDLL:
         "st_op_eval_noalloc": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
         "st_op_eval_multi": (i32, [VP, VP, i32, ctypes.POINTER(VP), ctypes.POINTER(VP),
                                    ctypes.POINTER(i32), ctypes.POINTER(VP), ctypes.POINTER(VP), VP]),
+        "st_graph_create": (i32, [VP, VP, i32, ctypes.POINTER(VP), ctypes.POINTER(VP),
+                                  ctypes.POINTER(i32), ctypes.POINTER(VP), ctypes.POINTER(VP),
+                                  ctypes.POINTER(VP)]),
+        "st_graph_launch": (i32, [VP, VP]),
+        "st_graph_launches": (i64, [VP]),
+        "st_graph_free": (None, [VP]),
+        "st_autotune_eval": (i32, [VP, VP, i32, ctypes.POINTER(VP), ctypes.POINTER(VP),
+                                   ctypes.POINTER(i32), ctypes.POINTER(VP), ctypes.POINTER(VP), VP,
+                                   ctypes.POINTER(TuneChoice), ctypes.POINTER(TuneChoice), i32,
+                                   ctypes.POINTER(i32)]),
+        "st_set_schedule": (i32, [VP, ctypes.POINTER(TuneChoice)]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
         "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
         "st_proxy_create": (i32, [VP, i32, i32, i32, ctypes.POINTER(VP), ctypes.POINTER(VP)]),
@@ -382,6 +403,12 @@ def cascade_merge(model: Model, proxy_label, unsure_pos, count, full_label, out=
 def eval_multi(model: Model, kv: KVCache, ops, tuple_ids, logits=None, labels=None, stream=None):
     """Several operators, each over its own device tuple ids, in one batched pass
     (``st_op_eval_multi``); returns the lists of (logits, labels) device tensors."""
+    args, logits, labels = _multi_args(ops, tuple_ids, logits, labels)
+    model.check(model.L.st_op_eval_multi(model.h, kv.h, *args, _stream(stream)))
+    return logits, labels
+
+
+def _multi_args(ops, tuple_ids, logits, labels):
     import torch
     k = len(ops)
     ns = [int(t.numel()) for t in tuple_ids]
@@ -390,10 +417,55 @@ def eval_multi(model: Model, kv: KVCache, ops, tuple_ids, logits=None, labels=No
     if labels is None:
         labels = [torch.empty((n,), dtype=torch.int32, device="cuda") for n in ns]
     arr = lambda xs: (VP * k)(*[_ptr(x) for x in xs])
-    model.check(model.L.st_op_eval_multi(model.h, kv.h, k, (VP * k)(*[o.h for o in ops]), arr(tuple_ids),
-                                         (ctypes.c_int32 * k)(*ns), arr(logits), arr(labels),
-                                         _stream(stream)))
-    return logits, labels
+    return (k, (VP * k)(*[o.h for o in ops]), arr(tuple_ids), (ctypes.c_int32 * k)(*ns), arr(logits),
+            arr(labels)), logits, labels
+
+
+class Graph:
+    """A batched evaluation recorded as a CUDA graph (``st_graph``).  Keeps the
+    tuple-id and output tensors it was created with (``logits``, ``labels``)."""
+
+    def __init__(self, model: Model, kv: KVCache, ops, tuple_ids, logits=None, labels=None):
+        self.model, self.L = model, model.L
+        args, self.logits, self.labels = _multi_args(ops, tuple_ids, logits, labels)
+        self._keep = (ops, tuple_ids, kv)
+        h = VP()
+        model.check(self.L.st_graph_create(model.h, kv.h, *args, ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        self.model.check(self.L.st_graph_launch(self.h, _stream(stream)))
+
+    def launches(self) -> int:
+        return int(self.L.st_graph_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.st_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(model: Model, kv: KVCache, ops, tuple_ids, logits=None, labels=None, stream=None):
+    """Time candidate evaluation schedules on this batch (``st_autotune_eval``);
+    returns (best, tried) as dicts.  The best schedule stays set in the model."""
+    args, logits, labels = _multi_args(ops, tuple_ids, logits, labels)
+    best = TuneChoice()
+    tried = (TuneChoice * 32)()
+    nt = ctypes.c_int32()
+    model.check(model.L.st_autotune_eval(model.h, kv.h, *args, _stream(stream), ctypes.byref(best), tried,
+                                         32, ctypes.byref(nt)))
+    return best.as_dict(), [tried[i].as_dict() for i in range(nt.value)]
+
+
+def set_schedule(model: Model, eval_rows: int = 0, attn_nb: int = 1, longest_first: int = 1):
+    sc = TuneChoice(int(eval_rows), int(attn_nb), int(longest_first), 0.0)
+    model.check(model.L.st_set_schedule(model.h, ctypes.byref(sc)))
 
 
 def version() -> str:

@@ -108,3 +108,63 @@ def test_multi_rejects_bad_arguments(bf16_env):
         st.eval_multi(e["model"], e["kv"], ops, sets)      # r = 1.0 above the retained 0.5
     with pytest.raises(st.StrettoError):
         st.eval_multi(e["model"], e["kv"], ops[:1] * 9, sets[:1] * 9)   # more than 8 operators
+
+
+def test_graph_replay_equals_eager(bf16_env):
+    """A captured batched evaluation replays to the eager results, also after the
+    tuple-id buffers are rewritten in place, and counts its kernels per replay."""
+    e = bf16_env
+    st, torch = e["stretto"], e["torch"]
+    e["kv"].retain(1.0, st.ST_BF16)
+    model, kv = e["model"], e["kv"]
+    ops = [model.operator(o) for o in _ops(e["synth"], e["cfg"].vocab)]
+    sets = _sets(kv.T, torch)
+    g = st.Graph(model, kv, ops, sets)
+    assert g.launches() > 0
+    n0 = model.launch_count()
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    model.status()
+    assert model.launch_count() - n0 == 2 * g.launches()
+    ref_lg, ref_lb = st.eval_multi(model, kv, ops, sets)
+    torch.cuda.synchronize()
+    for a, b in zip(g.logits, ref_lg):
+        assert torch.equal(a.cpu(), b.cpu())
+    for a, b in zip(g.labels, ref_lb):
+        assert torch.equal(a.cpu(), b.cpu())
+    # other tuples in the same buffers
+    for t in sets:
+        t.copy_(torch.flip(t, [0]) % kv.T)
+    g.launch()
+    ref_lg, ref_lb = st.eval_multi(model, kv, ops, sets)
+    torch.cuda.synchronize()
+    model.status()
+    for a, b in zip(g.logits, ref_lg):
+        assert torch.equal(a.cpu(), b.cpu())
+    g.close()
+
+
+def test_autotune_schedules_agree(bf16_env):
+    """Every schedule the autotuner tries gives the same results bit for bit; the
+    chosen one is the fastest it timed and stays set."""
+    e = bf16_env
+    st, torch = e["stretto"], e["torch"]
+    e["kv"].retain(1.0, st.ST_BF16)
+    model, kv = e["model"], e["kv"]
+    ops = [model.operator(o) for o in _ops(e["synth"], e["cfg"].vocab)]
+    sets = _sets(kv.T, torch)
+    st.set_schedule(model)
+    ref_lg, ref_lb = st.eval_multi(model, kv, ops, sets)
+    torch.cuda.synchronize()
+    best, tried = st.autotune(model, kv, ops, sets)
+    model.status()
+    assert len(tried) >= 4 and best["ms"] == min(t["ms"] for t in tried)
+    for sc in tried:
+        st.set_schedule(model, sc["eval_rows"], sc["attn_nb"], sc["longest_first"])
+        lg, lb = st.eval_multi(model, kv, ops, sets)
+        torch.cuda.synchronize()
+        model.status()
+        for a, b in zip(lg, ref_lg):
+            assert torch.equal(a.cpu(), b.cpu()), f"schedule {sc} changes the logits"
+    st.set_schedule(model)
