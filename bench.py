@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-proxy", action="store_true", help="skip the proxy+FP8 cascade arm")
     ap.add_argument("--proxy-train-tables", type=int, default=15)
     ap.add_argument("--proxy-epochs", type=int, default=6)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-operator arm")
+    ap.add_argument("--batched-tuples", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -319,6 +321,88 @@ def proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch):
             "sweep_on_heldout": sweep}
 
 
+def batched_arm(args, stretto, synth, torch):
+    """Several operators over one retained profile in one batched pass, in the
+    shape of the batching configuration: the 16-layer d 2048 decoder (32 q / 8 kv
+    heads x 64, SwiGLU 5632, random init), Zipf(1.1) document lengths over
+    32..8192, three operators (binary filter, 16-token prompt, r = 0.1; 8-way
+    classify, 48 tokens, r = 0.3; binary filter, 64 tokens, r = 1.0), each over
+    every tuple, reading its own n_keep prefix of one rank-ordered profile
+    retained at r = 1.  Times them as three st_op_eval calls, as one
+    st_op_eval_multi call, and as a replayed CUDA graph after st_autotune_eval,
+    with BF16 and E4M3 retained caches.  Unit: (tuple, operator) evaluations/s."""
+    cfg = synth.MODELS["c3_bf16"]
+    T = args.batched_tuples
+    table = synth.make_table(synth.TABLES["c4"], cfg.vocab, seed=3000, n_tuples=T)
+    model = stretto.Model(cfg, synth.make_weights_device(cfg, seed=4343), max_pos=8192 + 64 + 8)
+    kv = model.kv_alloc(table["offsets"])
+    kv.build(torch.from_numpy(table["tokens"]).cuda())
+    ops_np = [synth.make_prompt(16, cfg.vocab, seed=51, label_ids=(1, 0), r=0.1),
+              synth.make_prompt(48, cfg.vocab, seed=52, label_ids=tuple(range(2, 10)), r=0.3,
+                                kind="classify"),
+              synth.make_prompt(64, cfg.vocab, seed=53, label_ids=(3, 4), r=1.0)]
+    ops = [model.operator(o) for o in ops_np]
+    ids = [torch.arange(T, dtype=torch.int32, device="cuda") for _ in ops]
+    evals = T * len(ops)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+
+    L = table["lengths"]
+    res = {"workload": f"16L d2048 32q/8kv x64 F5632 random-init; {T} tuples, Zipf(1.1) lengths "
+                       f"32..8192; 3 operators (filter P16 r0.1, classify-8 P48 r0.3, filter P64 r1.0) "
+                       "over every tuple, one profile retained at r = 1",
+           "tuples": T, "doc_tokens": int(L.sum()), "mean_len": float(L.mean()),
+           "evals_per_pass": evals, "unit": "(tuple, operator) evaluations/s"}
+    for name, code in (("bf16", stretto.ST_BF16), ("e4m3", stretto.ST_E4M3)):
+        kv.retain(1.0, code)
+        stretto.set_schedule(model)
+        ms_seq = timed(lambda: [op.eval(kv, i) for op, i in zip(ops, ids)], 3)
+        ms_multi = timed(lambda: stretto.eval_multi(model, kv, ops, ids), 3)
+        ref = stretto.eval_multi(model, kv, ops, ids)
+        best, tried = stretto.autotune(model, kv, ops, ids)
+        g = stretto.Graph(model, kv, ops, ids)
+        with ClockSampler() as clk:
+            ms_graph = timed(g.launch, 5)
+        torch.cuda.synchronize()
+        model.status()
+        same = all(torch.equal(a, b) for a, b in zip(g.logits, ref[0])) and \
+            all(torch.equal(a, b) for a, b in zip(g.labels, ref[1]))
+        # small operators (96 tuples each, different tuples): where launches and
+        # partly filled GPUs dominate
+        small = [torch.arange(k * 96, (k + 1) * 96, dtype=torch.int32, device="cuda") % T for k in range(len(ops))]
+        ev_s = 96 * len(ops)
+        ms_seq_s = timed(lambda: [op.eval(kv, i) for op, i in zip(ops, small)], 10)
+        ms_multi_s = timed(lambda: stretto.eval_multi(model, kv, ops, small), 10)
+        gs = stretto.Graph(model, kv, ops, small)
+        ms_graph_s = timed(gs.launch, 10)
+        gs.close()
+        res[name + "_small"] = {"tuples_per_operator": 96, "separate_calls": ev_s / (ms_seq_s / 1e3),
+                                "one_batched_call": ev_s / (ms_multi_s / 1e3),
+                                "graph": ev_s / (ms_graph_s / 1e3),
+                                "gain_graph_vs_separate": ms_seq_s / ms_graph_s,
+                                "ms": {"separate": ms_seq_s, "batched": ms_multi_s, "graph": ms_graph_s}}
+        res[name] = {"separate_calls": evals / (ms_seq / 1e3), "one_batched_call": evals / (ms_multi / 1e3),
+                     "graph_autotuned": evals / (ms_graph / 1e3),
+                     "gain_graph_vs_separate": ms_seq / ms_graph,
+                     "ms": {"separate": ms_seq, "batched": ms_multi, "graph": ms_graph},
+                     "graph_kernels_per_replay": g.launches(), "graph_equals_eager": bool(same),
+                     "schedule": best, "schedules_tried": tried, "clocks": clk.summary()}
+        g.close()
+    kv.close()
+    model.close()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -466,6 +550,9 @@ def main():
                "d2h_bytes_per_step": int(T * 2 * 4 + T * 4),
                "path": "st_run_host: pinned host tokens -> device, kv_build, kv_retain, op_eval, "
                        "logits + labels -> pinned host, synchronised every step"}
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_arm(args, stretto, synth, torch)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_rate(args, cfg, table, op, args.cpu_seconds)
@@ -477,7 +564,7 @@ def main():
                 "config": config_dict(args, cfg, table, op), "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                 "per_family_ms": {k: v["ms"] for k, v in prof.items()},
-                "op_eval": out, "proxy_fp8": proxy}
+                "op_eval": out, "proxy_fp8": proxy, "batched_ops": batched}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

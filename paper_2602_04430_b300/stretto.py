@@ -149,7 +149,8 @@ class Model:
         for lw in weights["layers"]:
             arrays += [lw[k] for k in ("wq", "wk", "wv", "wo", "wg", "wu", "wd")]
         arrays.append(weights["w_lm"])
-        dev = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device).to(dt)
+        dev = [(a if isinstance(a, torch.Tensor) else
+                torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))).to(device).to(dt).contiguous()
                for a in arrays]
         ptrs = (VP * len(dev))(*[t.data_ptr() for t in dev])
         c = ModelCfg(cfg.layers, cfg.d, cfg.hq, cfg.hkv, cfg.hd, cfg.ffn, cfg.vocab,

@@ -143,6 +143,26 @@ def make_weights(cfg: ModelConfig, seed: int = 1234, std: float = 0.02) -> Dict[
     return out
 
 
+def make_weights_device(cfg: ModelConfig, seed: int = 1234, std: float = 0.02) -> Dict[str, object]:
+    """The same layout and distribution as ``make_weights`` (N(0, std^2), bf16 values for
+    a bf16 model) drawn on the GPU with torch's seeded CUDA generator: a different
+    stream of numbers, for throughput runs of large models where host generation
+    would dominate the set-up time."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    dt = torch.bfloat16 if cfg.dtype == "bf16" else torch.float32
+    rnd = lambda shape: (torch.randn(shape, generator=g, device="cuda", dtype=torch.float32) * std).to(dt)
+    d, hq, hkv, hd, f = cfg.d, cfg.hq, cfg.hkv, cfg.hd, cfg.ffn
+    out = {"embed": rnd((cfg.vocab, d)), "layers": []}
+    for _ in range(cfg.layers):
+        out["layers"].append({
+            "wq": rnd((hq * hd, d)), "wk": rnd((hkv * hd, d)), "wv": rnd((hkv * hd, d)),
+            "wo": rnd((d, hq * hd)), "wg": rnd((f, d)), "wu": rnd((f, d)), "wd": rnd((d, f)),
+        })
+    out["w_lm"] = rnd((cfg.vocab, d))
+    return out
+
+
 def make_proxy_weights(d_in: int, h1: int = 512, h2: int = 128, seed: int = 777) -> Dict[str, np.ndarray]:
     """Initial parameters of the proxy MLP: W ~ N(0, 1/fan_in), b = 0 (float32)."""
     rng = np.random.Generator(np.random.PCG64(seed))
