@@ -155,6 +155,15 @@ int st_kv_retain(st_ctx* ctx, st_kv* kv, double r, int32_t kv_dtype, void* strea
  * returned early and its outputs are invalid), and clears it. */
 int st_status(st_ctx* ctx, void* stream);
 
+/* Self-test of the failure path (the paper has no counterpart): launches one
+ * kernel whose single thread waits on a device barrier that nothing completes,
+ * through the same bounded wait as the pipeline kernels, giving up after
+ * limit_cycles (1e3 .. 1e9) SM clock cycles and recording ST_ETIMEOUT in the
+ * context's device status word; the next st_status reports (and clears) it,
+ * and the context stays usable.  Faults and hangs nothing.
+ * Errors: ST_EINVAL (limit out of range). */
+int st_selftest_wait(st_ctx* ctx, int64_t limit_cycles, void* stream);
+
 /* Device status of the last retain on `kv`: synchronises `stream`, returns
  * ST_OK or ST_ENAN (and clears it). */
 int st_kv_status(st_ctx* ctx, st_kv* kv, void* stream);

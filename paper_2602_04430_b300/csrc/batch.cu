@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "ptx.cuh"
 
 using namespace st;
 
@@ -193,5 +194,29 @@ extern "C" int st_set_schedule(st_ctx* ctx, const st_tune_choice* sc) {
   ctx->eval_rows_cap = sc->eval_rows;
   ctx->attn_nb = sc->attn_nb;
   ctx->longest_first = sc->longest_first != 0;
+  return ST_OK;
+}
+
+// ------------------------------------------------------------------ failure self-test
+namespace {
+// One thread waits on an mbarrier that nothing arrives on, through the same
+// bounded wait as the pipeline kernels, and records the time-out.
+__global__ void k_wait_selftest(int* status, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&bar, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !ptx::mbar_wait(&bar, 0, limit)) atomicExch(status, ST_ETIMEOUT);
+}
+}  // namespace
+
+extern "C" int st_selftest_wait(st_ctx* ctx, int64_t limit_cycles, void* stream) {
+  if (!ctx || limit_cycles < 1000 || limit_cycles > 1000000000LL)
+    return bfail(ctx, ST_EINVAL, "st_selftest_wait: limit must lie in 1e3 .. 1e9 cycles");
+  k_wait_selftest<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(ctx->dstatus, (long long)limit_cycles);
+  BCK(cudaGetLastError());
+  ctx->launches += 1;
   return ST_OK;
 }

@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(TuneChoice), ctypes.POINTER(TuneChoice), i32,
                                    ctypes.POINTER(i32)]),
         "st_set_schedule": (i32, [VP, ctypes.POINTER(TuneChoice)]),
+        "st_selftest_wait": (i32, [VP, i64, VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
         "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
         "st_proxy_create": (i32, [VP, i32, i32, i32, ctypes.POINTER(VP), ctypes.POINTER(VP)]),
@@ -180,6 +181,10 @@ class Model:
 
     def reserve(self, build_rows: int = 0, eval_rows: int = 0):
         self.check(self.L.st_reserve(self.h, int(build_rows), int(eval_rows)))
+
+    def selftest_wait(self, limit_cycles: int = 1000000, stream=None):
+        """Run the bounded-wait failure self-test (its time-out shows in status())."""
+        self.check(self.L.st_selftest_wait(self.h, int(limit_cycles), _stream(stream)))
 
     def status(self, stream=None):
         self.check(self.L.st_status(self.h, _stream(stream)))

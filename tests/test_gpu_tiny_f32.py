@@ -146,3 +146,28 @@ def test_subset_and_order_of_tuple_ids(run):
     part, _ = opr.eval(kv, sub)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(part.cpu().numpy(), full.cpu().numpy()[[63, 0, 17, 17, 5]])
+
+
+def test_bounded_wait_timeout_is_reported_and_recoverable(run):
+    """The failure path without a fault: a device wait on a barrier that nothing
+    completes gives up after its cycle limit, st_status reports ST_ETIMEOUT once,
+    and the context keeps working (the same operator evaluation afterwards)."""
+    import torch
+    from paper_2602_04430_b300 import stretto, synth
+    model, kv = run["model"], run["kv"]
+    model.status()                                   # clean before
+    model.selftest_wait(limit_cycles=2_000_000)
+    torch.cuda.synchronize()
+    with pytest.raises(stretto.StrettoError) as e:
+        model.status()
+    assert e.value.code == stretto.ST_ETIMEOUT
+    model.status()                                   # reported once, then clear
+    kv.retain(1.0)
+    op = model.operator(synth.make_prompt(16, run["cfg"].vocab, seed=5, r=1.0))
+    ids = torch.arange(kv.T, dtype=torch.int32, device="cuda")
+    lg, lb = op.eval(kv, ids)
+    torch.cuda.synchronize()
+    model.status()
+    assert torch.isfinite(lg).all()
+    with pytest.raises(stretto.StrettoError):
+        model.selftest_wait(limit_cycles=10)         # limit out of range
