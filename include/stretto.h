@@ -260,6 +260,31 @@ int st_graph_launch(st_graph* g, void* stream);
 int64_t st_graph_launches(const st_graph* g);
 void st_graph_free(st_graph* g);
 
+/* ---- multi-stage cascade ----
+ *
+ * Sec. 4.1 cascades, any number of stages: stage k runs its filter operator
+ * (its own context = model, cache, r, and thresholds theta+ / theta-) on the
+ * tuples every earlier stage left unsure; a tuple leaves at the first stage
+ * that accepts or rejects it; the last stage's unsure tuples stay ST_UNSURE.
+ * All stages run on `stream` on one device.  For each input position i:
+ * labels_dev[i] (DEVICE int32 [n]) = the deciding stage's decision,
+ * stage_dev[i] (DEVICE int32 [n]) = that stage's index.  counts_host[k] (host,
+ * n_stages entries, may be NULL) = tuples sent to stage k; ms_host[k] (may be
+ * NULL) = its time (CUDA events: evaluation + routing).  Results equal running
+ * st_op_eval stage by stage on the unsure tuples.  Synchronises `stream` once
+ * per stage (to size the next stage's evaluation).  The routing buffers (about
+ * 30 bytes per tuple) live in stage 0's context.
+ * Errors: ST_EINVAL (no stage, a classify operator, a cache of another
+ * context), and the errors of st_op_eval (message prefixed with the stage). */
+typedef struct {
+  st_ctx* ctx;
+  const st_kv* kv;
+  const st_operator* op;
+} st_stage;
+int st_cascade_run(int32_t n_stages, const st_stage* stages, const int32_t* tuple_ids_dev, int32_t n,
+                   int32_t* labels_dev, int32_t* stage_dev, int32_t* counts_host, float* ms_host,
+                   void* stream);
+
 /* ---- schedule of operator evaluation, and its autotuner ----
  *
  * eval_rows: prompt rows per pass through the layers (the evaluation is cut

@@ -197,6 +197,26 @@ def decide(op, z) -> int:
     return decide_filter(float(z[0]), float(z[1]), op.theta_pos, op.theta_neg)
 
 
+def cascade_stages(decisions: List[List[int]]):
+    """Multi-stage cascade (Sec. 4.1 with any number of stages): stage k is
+    consulted for a tuple only if every earlier stage left it UNSURE; the first
+    stage that accepts or rejects decides; the last stage's UNSURE stays UNSURE.
+
+    ``decisions[k][i]`` is stage k's decision for input position i (only read
+    for the tuples that reach stage k).  Returns (labels, deciding stage,
+    number of tuples sent to each stage)."""
+    n = len(decisions[0]) if decisions else 0
+    labels, stage = [UNSURE] * n, [0] * n
+    counts = [0] * len(decisions)
+    for i in range(n):
+        for k, dk in enumerate(decisions):
+            counts[k] += 1
+            labels[i], stage[i] = dk[i], k
+            if dk[i] != UNSURE:
+                break
+    return labels, stage, counts
+
+
 def run_table(cfg, w, table, op, tuples: Optional[List[int]] = None, kv_fp8: bool = False,
               caches: Optional[dict] = None):
     """kv_build -> retain(r) -> op_eval -> decision for the selected tuples of a table.

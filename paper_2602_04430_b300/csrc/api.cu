@@ -362,6 +362,7 @@ extern "C" void st_destroy(st_ctx* ctx) {
   cudaFree(ctx->dstatus);
   cudaFree(ctx->ws_build.p);
   cudaFree(ctx->ws_eval.p);
+  cudaFree(ctx->ws_casc.p);
   for (auto& r : ctx->prof.pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

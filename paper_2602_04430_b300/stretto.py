@@ -63,6 +63,11 @@ class TuneChoice(ctypes.Structure):
                 "longest_first": int(self.longest_first), "ms": float(self.ms)}
 
 
+class StageDesc(ctypes.Structure):
+    """st_stage: one cascade stage (context, cache, operator handles)."""
+    _fields_ = [("ctx", ctypes.c_void_p), ("kv", ctypes.c_void_p), ("op", ctypes.c_void_p)]
+
+
 def lib() -> ctypes.CDLL:
     """Load libstretto.so (raises ImportError if it has not been built)."""
     global _LIB
@@ -104,6 +109,8 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(i32)]),
         "st_set_schedule": (i32, [VP, ctypes.POINTER(TuneChoice)]),
         "st_selftest_wait": (i32, [VP, i64, VP]),
+        "st_cascade_run": (i32, [i32, ctypes.POINTER(StageDesc), VP, i32, VP, VP, ctypes.POINTER(i32),
+                                 ctypes.POINTER(ctypes.c_float), VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
         "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
         "st_proxy_create": (i32, [VP, i32, i32, i32, ctypes.POINTER(VP), ctypes.POINTER(VP)]),
@@ -472,6 +479,23 @@ def autotune(model: Model, kv: KVCache, ops, tuple_ids, logits=None, labels=None
 def set_schedule(model: Model, eval_rows: int = 0, attn_nb: int = 1, longest_first: int = 1):
     sc = TuneChoice(int(eval_rows), int(attn_nb), int(longest_first), 0.0)
     model.check(model.L.st_set_schedule(model.h, ctypes.byref(sc)))
+
+
+def cascade_run(stages, tuple_ids, labels=None, stage=None, stream=None):
+    """Multi-stage cascade over device tuple ids; stages = [(model, kv, operator)].
+    Returns (labels, deciding stage, tuples sent to each stage, ms per stage)."""
+    import torch
+    n = int(tuple_ids.numel())
+    k = len(stages)
+    labels = torch.empty(n, dtype=torch.int32, device="cuda") if labels is None else labels
+    stage = torch.empty(n, dtype=torch.int32, device="cuda") if stage is None else stage
+    arr = (StageDesc * k)(*[StageDesc(m.h, kv.h, op.h) for m, kv, op in stages])
+    counts = (ctypes.c_int32 * k)()
+    ms = (ctypes.c_float * k)()
+    m0 = stages[0][0]
+    m0.check(m0.L.st_cascade_run(k, arr, _ptr(tuple_ids), n, _ptr(labels), _ptr(stage), counts, ms,
+                                 _stream(stream)))
+    return labels, stage, list(counts), list(ms)
 
 
 def version() -> str:

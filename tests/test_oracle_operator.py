@@ -225,3 +225,21 @@ def test_pruned_cache_equals_masked_full_sequence(setup):
         x = M.attn_out_and_ffn(cfg, lw, x, o)
     z_masked = M.label_logits(w, M.rmsnorm(x[-1], cfg.eps), op.label_ids)
     np.testing.assert_allclose(z_cached, z_masked, rtol=1e-12, atol=1e-13)
+
+
+def test_cascade_stages_definition():
+    """Multi-stage cascade oracle: the first sure stage decides, later stages
+    are not consulted, the last stage's unsure stays unsure (Sec. 4.1)."""
+    from oracle.operator import ACCEPT, REJECT, UNSURE, cascade_stages
+    d0 = [ACCEPT, UNSURE, REJECT, UNSURE, UNSURE]
+    d1 = [REJECT, REJECT, ACCEPT, UNSURE, ACCEPT]
+    d2 = [ACCEPT, ACCEPT, ACCEPT, UNSURE, REJECT]
+    labels, stage, counts = cascade_stages([d0, d1, d2])
+    assert labels == [ACCEPT, REJECT, REJECT, UNSURE, ACCEPT]
+    assert stage == [0, 1, 0, 2, 1]
+    assert counts == [5, 3, 1]
+    # one stage: its own decisions, unsure included
+    assert cascade_stages([d0]) == (d0, [0] * 5, [5])
+    # a stage that is never unsure ends the cascade
+    labels, stage, counts = cascade_stages([d1[:3], d0[:3], d2[:3]])
+    assert counts == [3, 0, 0] and stage == [0, 0, 0] and labels == d1[:3]
