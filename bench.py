@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--proxy-epochs", type=int, default=6)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-operator arm")
     ap.add_argument("--batched-tuples", type=int, default=2048)
+    ap.add_argument("--no-map", action="store_true", help="skip the map-operator (greedy decode) arm")
+    ap.add_argument("--map-tuples", type=int, default=1024)
+    ap.add_argument("--map-gen", type=int, default=16)
     return ap.parse_args()
 
 
@@ -403,6 +406,37 @@ def batched_arm(args, stretto, synth, torch):
     return res
 
 
+def map_arm(args, model, kv, cfg, T, stretto, synth, torch):
+    """Map operator (greedy decode of n_gen tokens per tuple) on the bench's own
+    cache at the bench's r: the first map_tuples tuples, one 32-token prompt;
+    one warm-up call, then three calls timed with CUDA events."""
+    n = min(T, args.map_tuples)
+    pr = synth.make_prompt(32, cfg.vocab, seed=78, label_ids=(1, 0), r=args.r)
+    opm = model.operator(pr)
+    ids = torch.arange(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    opm.map(kv, ids, args.map_gen)
+    torch.cuda.synchronize()
+    model.status()
+    model.prof_reset()
+    model.prof_enable(True)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a0.record(stream)
+    for _ in range(reps):
+        toks = opm.map(kv, ids, args.map_gen)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    model.prof_enable(False)
+    pf = model.prof_read()
+    model.status()
+    ms = a0.elapsed_time(a1) / reps
+    assert int(toks.min()) >= 0 and int(toks.max()) < cfg.vocab
+    return {"tuples": n, "prompt_tokens": 32, "n_gen": args.map_gen, "r": args.r, "ms": ms,
+            "tuples_per_s": n / (ms / 1000.0), "generated_tokens_per_s": n * args.map_gen / (ms / 1000.0),
+            "per_family_ms": {k: v["ms"] / reps for k, v in pf.items()}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -524,6 +558,9 @@ def main():
                            "gemm_ms": gg["ms"] / reps,
                            "gemm_TFLOPs": gg["flops"] / (gg["ms"] / 1000.0) / 1e12 if gg["ms"] else 0}
         kv.retain(op.r, kvd)
+    mapr = None
+    if not args.no_map and rank == 0:
+        mapr = map_arm(args, model, kv, cfg, T, stretto, synth, torch)
     proxy = None
     if not args.no_proxy and rank == 0:
         proxy = proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch)
@@ -564,7 +601,7 @@ def main():
                 "config": config_dict(args, cfg, table, op), "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                 "per_family_ms": {k: v["ms"] for k, v in prof.items()},
-                "op_eval": out, "proxy_fp8": proxy, "batched_ops": batched}
+                "op_eval": out, "map": mapr, "proxy_fp8": proxy, "batched_ops": batched}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

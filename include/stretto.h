@@ -53,7 +53,7 @@ extern "C" {
 #define ST_ENOMEM 2        /* device allocation failed */
 #define ST_ECUDA 3         /* a CUDA runtime call failed */
 #define ST_ETIMEOUT 4      /* a bounded device wait gave up */
-#define ST_ENAN 5          /* a NaN retention score was found */
+#define ST_ENAN 5          /* a NaN retention score, or NaN map-operator logits */
 #define ST_EUNSUPPORTED 6  /* shape not supported by the compiled kernels */
 
 /* ---- element types ---- */
@@ -150,9 +150,12 @@ int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, void* stream)
  * st_kv_status (ST_ENAN). Errors: ST_EINVAL (r outside (0,1], kv_dtype). */
 int st_kv_retain(st_ctx* ctx, st_kv* kv, double r, int32_t kv_dtype, void* stream);
 
-/* Device status of the context's bounded waits: synchronises `stream`,
- * returns ST_OK or ST_ETIMEOUT (a tcgen05 pipeline wait gave up; the kernel
- * returned early and its outputs are invalid), and clears it. */
+/* Device status word of the context: synchronises `stream`, returns the first
+ * error a kernel recorded since the last call, and clears it: ST_OK;
+ * ST_ETIMEOUT (a tcgen05 pipeline wait gave up; the kernel returned early and
+ * its outputs are invalid); ST_EINVAL (a token id outside [0, vocab) was
+ * embedded as zeros); ST_ENAN (a map-operator step had no finite logit; its
+ * token was set to 0). */
 int st_status(st_ctx* ctx, void* stream);
 
 /* Self-test of the failure path (the paper has no counterpart): launches one
@@ -215,6 +218,24 @@ void st_op_free(st_operator* op);
 int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
                const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
                int32_t* labels_dev, void* stream);
+
+/* ---- map operator (greedy decode) ----
+ *
+ * The paper's second operator type (Sec. 6 "Operators": a map generates a
+ * value per item): the operator's prompt is forwarded against each tuple's
+ * retained cache as in st_op_eval, then n_gen tokens are generated greedily —
+ * token t is the argmax over the whole vocabulary (ties to the lowest id) of
+ * the logits at the last position of prompt + tokens 0..t-1, and sits at the
+ * next position (L + P + t).  Every step attends to the tuple's retained
+ * slots (the operator's r) and to all prompt and generated keys, kept per
+ * tuple in a decode cache.  op's label ids, kind and thresholds are unused.
+ * tokens_dev: DEVICE int32 [n][n_gen]; logits_dev: NULL or DEVICE float32
+ * [n][n_gen][vocab] (every step's logits, for inspection).
+ * Errors: ST_EINVAL (n_gen outside 1..256, document + P + n_gen > max_pos,
+ * op->r above the retained profile's), ST_EUNSUPPORTED (vocab not a multiple of
+ * 256 for bf16 / 128 for f32 models). */
+int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op, const int32_t* tuple_ids_dev,
+                int32_t n, int32_t n_gen, int32_t* tokens_dev, float* logits_dev, void* stream);
 
 /* ---- batched evaluation of several operators ----
  *

@@ -143,6 +143,13 @@ def op_eval(cfg, w: dict, L: int, Kr, Vr, prompt, label_ids) -> np.ndarray:
     (any order); ``L``: the document length (the prompt sits at positions
     L..L+P-1 whatever was pruned).  Returns the label logits ``[n_labels]``.
     """
+    return label_logits(w, prompt_state(cfg, w, L, Kr, Vr, prompt), label_ids)
+
+
+def prompt_state(cfg, w: dict, L: int, Kr, Vr, prompt) -> np.ndarray:
+    """Final-normed hidden state of the last prompt position, the prompt sitting
+    at positions L..L+P-1 after the retained cache (visible to every prompt row)
+    and attending causally to itself."""
     prompt = np.asarray(prompt, dtype=np.int64)
     P = prompt.shape[0]
     x = w["embed"][prompt].astype(F64)
@@ -157,8 +164,34 @@ def op_eval(cfg, w: dict, L: int, Kr, Vr, prompt, label_ids) -> np.ndarray:
                              axis=1)
         o = attention(q, kc, vc, vis)
         x = attn_out_and_ffn(cfg, lw, x, o)
-    xf_last = rmsnorm(x[-1], cfg.eps)
-    return label_logits(w, xf_last, label_ids)
+    return rmsnorm(x[-1], cfg.eps)
+
+
+def map_eval(cfg, w: dict, L: int, Kr, Vr, prompt, n_gen: int):
+    """The map operator (Sec. 6 "Operators": generate a value per item), greedy:
+    token t is the argmax over the vocabulary (ties to the lowest id) of the
+    logits at the last position of prompt + tokens 0..t-1; it sits at the next
+    position.  Returns (tokens [n_gen], logits [n_gen, V])."""
+    seq, toks, logs = list(np.asarray(prompt, dtype=np.int64)), [], []
+    w_lm = w["w_lm"].astype(F64)
+    for _ in range(n_gen):
+        z = w_lm @ prompt_state(cfg, w, L, Kr, Vr, seq)
+        t = int(np.argmax(z))
+        toks.append(t), logs.append(z), seq.append(t)
+    return toks, np.stack(logs)
+
+
+def map_eval_from_scratch(cfg, w: dict, doc_tokens, prompt, n_gen: int):
+    """The same greedy decode without any cache: each step runs document, prompt
+    and the tokens so far in one causal pass."""
+    seq = list(np.asarray(doc_tokens, dtype=np.int64)) + list(np.asarray(prompt, dtype=np.int64))
+    toks, logs = [], []
+    w_lm = w["w_lm"].astype(F64)
+    for _ in range(n_gen):
+        z = w_lm @ forward(cfg, w, np.asarray(seq))[-1]
+        t = int(np.argmax(z))
+        toks.append(t), logs.append(z), seq.append(t)
+    return toks, np.stack(logs)
 
 
 def op_eval_from_scratch(cfg, w: dict, doc_tokens, prompt, label_ids) -> np.ndarray:

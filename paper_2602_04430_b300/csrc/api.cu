@@ -161,7 +161,7 @@ Launch::~Launch() {
 }  // namespace st
 
 // ------------------------------------------------------------------ internal step helpers
-namespace {
+namespace st {
 
 // One projection: dispatches to the tensor-core GEMM (bf16) or the CUDA-core GEMM (f32).
 int project(st_ctx* ctx, const void* A, const void* W, int M, int N, int K, EpiParams ep,
@@ -226,20 +226,18 @@ int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_item
     if (rc_ != ST_OK) return rc_;   \
   } while (0)
 
-// The projection reads bf16(x) and scales its rows by 1/rms from `ssq`.
 void set_norm_in(EpiParams& ep, const float* ssq, const st_model_cfg& c) {
   ep.ssq_in = ssq;
   ep.ssq_parts = c.d / 128;
   ep.norm_d = c.d;
   ep.eps = c.eps;
 }
-// The residual epilogue also writes bf16(x) to xb and the partial sums of squares.
 void set_norm_out(EpiParams& ep, void* xb, float* ssq) {
   ep.xb = xb;
   ep.ssq_out = ssq;
 }
 
-}  // namespace
+}  // namespace st
 
 // ================================================================== context
 extern "C" const char* st_version(void) { return "stretto-b300 0.1 (sm_103a)"; }
@@ -363,6 +361,7 @@ extern "C" void st_destroy(st_ctx* ctx) {
   cudaFree(ctx->ws_build.p);
   cudaFree(ctx->ws_eval.p);
   cudaFree(ctx->ws_casc.p);
+  cudaFree(ctx->ws_map.p);
   for (auto& r : ctx->prof.pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -508,8 +507,8 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
     }
     {
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      if (c.dtype == ST_BF16) embed_rows<bf16>(tokens_dev + ch.r0, ch.rows, (const bf16*)ctx->embed, c.d, w.x, s);
-      else embed_rows<float>(tokens_dev + ch.r0, ch.rows, (const float*)ctx->embed, c.d, w.x, s);
+      if (c.dtype == ST_BF16) embed_rows<bf16>(tokens_dev + ch.r0, ch.rows, (const bf16*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
+      else embed_rows<float>(tokens_dev + ch.r0, ch.rows, (const float*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
     }
     CKLAUNCH();
     // bf16 path: only layer 0 runs a standalone RMSNorm; afterwards every residual
@@ -685,7 +684,11 @@ extern "C" int st_status(st_ctx* ctx, void* stream) {
   CK(cudaStreamSynchronize(S(stream)));
   CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int32_t), S(stream)));
   CK(cudaStreamSynchronize(S(stream)));
-  if (h != ST_OK) return fail(ctx, h, "device status: a bounded wait timed out");
+  if (h != ST_OK)
+    return fail(ctx, h, h == ST_ETIMEOUT ? "device status: a bounded wait timed out"
+                        : h == ST_ENAN   ? "device status: non-finite logits in a map operator step"
+                        : h == ST_EINVAL ? "device status: a token id outside the vocabulary"
+                                         : "device status: error");
   return ST_OK;
 }
 
@@ -871,8 +874,10 @@ int64_t opset_rows(const OpSet& os, int p0, int p1) {
   return r;
 }
 
+int map_head(st_ctx* ctx, int np, int t, const EvalBufs& w, const MapCtx& mp, cudaStream_t s);
+
 int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, int64_t row_base,
-               int64_t M, const EvalBufs& w, cudaStream_t s) {
+               int64_t M, const EvalBufs& w, cudaStream_t s, const MapCtx* mp) {
   const st_model_cfg& c = ctx->cfg;
   const int np = p1 - p0;
   if (np <= 0) return ST_OK;
@@ -896,12 +901,12 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
   }
   if (c.dtype == ST_BF16) {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_worklist(w.nk, w.pP, np, G, ctx->longest_first != 0, w.order, s);
+    eval_worklist(w.nk, w.pP, np, G, 0, ctx->longest_first != 0, w.order, s);
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    if (c.dtype == ST_BF16) embed_rows<bf16>(w.tok, M, (const bf16*)ctx->embed, c.d, w.x, s);
-    else embed_rows<float>(w.tok, M, (const float*)ctx->embed, c.d, w.x, s);
+    if (c.dtype == ST_BF16) embed_rows<bf16>(w.tok, M, (const bf16*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
+    else embed_rows<float>(w.tok, M, (const float*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
   }
   CKLAUNCH();
   for (int l = 0; l < c.layers; ++l) {
@@ -924,6 +929,17 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
     ep.hd = c.hd;
     ep.qkv_f16 = kv->kv_dtype == ST_E4M3 ? 1 : 0;
     RC(project(ctx, w.xn, LW.wqkv, M, nqkv, c.d, ep, w.tmp, nullptr, s));
+    if (mp) {
+      // map operator: the prompt's keys and values of this layer into the decode cache
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      copy_prompt_kv(w.kp, (char*)mp->K + (size_t)l * mp->layer_elems * ctx->esz, np, os.op[0].P, mp->S, kd,
+                     ctx->esz, s);
+      CKLAUNCH();
+      Launch L2(ctx, s, ST_PROF_OTHER, 0, 0);
+      copy_prompt_kv(w.vp, (char*)mp->V + (size_t)l * mp->layer_elems * ctx->esz, np, os.op[0].P, mp->S, kd,
+                     ctx->esz, s);
+      CKLAUNCH();
+    }
     AttnParams a;
     a.mode = 1;
     a.q = w.q;
@@ -1021,12 +1037,143 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
       RC(project(ctx, h_k, LW.wd, Mr, c.d, c.ffn, ed, w.tmp, nullptr, s));
     }
   }
+  if (mp) {
+    // map operator: the first greedy token from the last prompt row's logits
+    // over the whole vocabulary (one operator: pair i's last row is i*P + P-1)
+    const int P = os.op[0].P;
+    {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      if (c.dtype == ST_BF16)
+        rmsnorm_rows<bf16>(w.x + (size_t)(P - 1) * c.d, np, c.d, c.eps, (bf16*)mp->xn, nullptr, s, (int64_t)P * c.d);
+      else
+        rmsnorm_rows<float>(w.x + (size_t)(P - 1) * c.d, np, c.d, c.eps, (float*)mp->xn, nullptr, s, (int64_t)P * c.d);
+      CKLAUNCH();
+    }
+    RC(map_head(ctx, np, 0, w, *mp, s));
+    return ST_OK;
+  }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
     label_head(w.x, os, np, w.prow, w.pP, w.pop, w.pj, c.d, c.eps, ctx->w_lm, c.dtype, s);
   }
   CKLAUNCH();
   return ST_OK;
+}
+
+// Greedy token t of every pair: logits of the final-normed rows mp.xn over the
+// whole vocabulary (one GEMM against the LM head) and their argmax.
+int map_head(st_ctx* ctx, int np, int t, const EvalBufs& w, const MapCtx& mp, cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  EpiParams el;
+  el.mode = EPI_STORE_F32;
+  el.out = mp.logits;
+  el.ld = c.vocab;
+  RC(project(ctx, mp.xn, ctx->w_lm, np, c.vocab, c.d, el, w.tmp, nullptr, s));
+  Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+  argmax_rows(mp.logits, np, c.vocab, t, mp.n_gen, mp.tokens, mp.logits_out, ctx->dstatus, s);
+  CKLAUNCH();
+  return ST_OK;
+}
+
+// Decode step t >= 1 of the map operator: one row per pair (the token of step
+// t - 1 at position L + P + t - 1) through every layer, its keys and values
+// appended to the decode cache, attending to the retained slots and to the
+// pair's P + t prompt / generated keys; then the greedy token t.
+int decode_step(st_ctx* ctx, const st_kv* kv, int P, int np, int t, const EvalBufs& w, const MapCtx& mp,
+                cudaStream_t s) {
+  const st_model_cfg& c = ctx->cfg;
+  const int qd = c.hq * c.hd, kd = c.hkv * c.hd, nqkv = qd + 2 * kd;
+  const size_t kr_e = kv->kv_dtype == ST_E4M3 ? 1 : ctx->esz;
+  const bool fused = c.dtype == ST_BF16;
+  const int M = np;
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    decode_plan(np, mp.S, P, t, mp.n_gen, w.len, mp.tokens, w.prow, w.pP, mp.pq0, w.rowpair, w.pos, w.tok, s);
+  }
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    if (c.dtype == ST_BF16) embed_rows<bf16>(w.tok, M, (const bf16*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
+    else embed_rows<float>(w.tok, M, (const float*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
+  }
+  CKLAUNCH();
+  for (int l = 0; l < c.layers; ++l) {
+    const LayerW& LW = ctx->layers[l];
+    char* Kl = (char*)mp.K + (size_t)l * mp.layer_elems * ctx->esz;
+    char* Vl = (char*)mp.V + (size_t)l * mp.layer_elems * ctx->esz;
+    if (!fused || l == 0) RC(rmsnorm(ctx, w.x, M, w.xn, nullptr, s));
+    EpiParams ep;
+    if (fused && l > 0) set_norm_in(ep, w.ssq, c);
+    ep.mode = EPI_QKV;
+    ep.q = w.q;
+    ep.kbase = Kl + (size_t)(P + t - 1) * kd * ctx->esz;
+    ep.vbase = Vl + (size_t)(P + t - 1) * kd * ctx->esz;
+    ep.kv_sg = c.hd;
+    ep.kv_sr = (int64_t)mp.S * kd;
+    ep.pos = w.pos;
+    ep.rope = ctx->rope;
+    ep.rope_t = ctx->rope_t;
+    ep.rope_np = c.max_pos;
+    ep.hq = c.hq;
+    ep.hkv = c.hkv;
+    ep.hd = c.hd;
+    ep.qkv_f16 = kv->kv_dtype == ST_E4M3 ? 1 : 0;
+    RC(project(ctx, w.xn, LW.wqkv, M, nqkv, c.d, ep, w.tmp, nullptr, s));
+    AttnParams a;
+    a.mode = 1;
+    a.q = w.q;
+    a.o = w.o;
+    a.hq = c.hq;
+    a.hkv = c.hkv;
+    a.hd = c.hd;
+    a.scale = 1.0f / std::sqrt((float)c.hd);
+    a.Kr = (const char*)kv->Kr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
+    a.Vr = (const char*)kv->Vr + (size_t)l * c.hkv * kv->Rp_cap * c.hd * kr_e;
+    a.scales = kv->scales + (size_t)l * c.hkv * (kv->Rp_cap / 64) * 2;
+    a.Rp_cap = kv->Rp_cap;
+    a.offp = kv->offp;
+    a.tup = w.tup;
+    a.nk = w.nk;
+    a.prow = w.prow;
+    a.pP = w.pP;
+    a.rowpair = w.rowpair;
+    a.work = mp.work;
+    a.n_work = np;
+    a.qrows = np;
+    a.kvrows = (int64_t)np * mp.S;
+    a.nq = 1;
+    a.pq0 = mp.pq0;
+    a.kp = Kl;
+    a.vp = Vl;
+    a.n = np;
+    a.kv_dtype = kv->kv_dtype;
+    a.nb = ctx->attn_nb;
+    RC(attention(ctx, a, nullptr, 0, s));
+    EpiParams eo;
+    eo.mode = EPI_RESID;
+    eo.x = w.x;
+    eo.ld = c.d;
+    if (fused) set_norm_out(eo, w.xn, w.ssq);
+    RC(project(ctx, w.o, LW.wo, M, c.d, qd, eo, w.tmp, nullptr, s));
+    if (!fused) {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      rmsnorm_rows<float>(w.x, M, c.d, c.eps, (float*)w.xn, nullptr, s);
+      CKLAUNCH();
+    }
+    EpiParams eg;
+    eg.mode = EPI_SWIGLU;
+    eg.h = w.h;
+    eg.ld = c.ffn;
+    if (fused) set_norm_in(eg, w.ssq, c);
+    RC(project(ctx, w.xn, LW.wgu, M, 2 * c.ffn, c.d, eg, w.tmp, w.h, s));
+    EpiParams ed;
+    ed.mode = EPI_RESID;
+    ed.x = w.x;
+    ed.ld = c.d;
+    if (fused && l + 1 < c.layers) set_norm_out(ed, w.xn, w.ssq);
+    RC(project(ctx, w.h, LW.wd, M, c.d, c.ffn, ed, w.tmp, nullptr, s));
+  }
+  RC(rmsnorm(ctx, w.x, M, mp.xn, nullptr, s));
+  return map_head(ctx, np, t, w, mp, s);
 }
 
 // Chunks the pairs (operator-major) into batches of at most `cap` prompt rows
@@ -1095,6 +1242,69 @@ extern "C" int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
   RC(make_opset(ctx, kv, n_ops, ops, tuple_ids_dev, n, logits_dev, labels_dev, &os, &rows, &pairs));
   if (pairs == 0) return ST_OK;
   return run_opset(ctx, kv, os, pairs, S(stream), nullptr);
+}
+
+extern "C" int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
+                           const int32_t* tuple_ids_dev, int32_t n, int32_t n_gen, int32_t* tokens_dev,
+                           float* logits_dev, void* stream) {
+  if (!ctx || !kv || !op || kv->ctx != ctx || n < 0) return fail(ctx, ST_EINVAL, "st_map_eval: bad argument");
+  if (n_gen < 1 || n_gen > 256) return fail(ctx, ST_EINVAL, "st_map_eval: n_gen must lie in 1..256");
+  if (n == 0) return ST_OK;
+  if (!tuple_ids_dev || !tokens_dev) return fail(ctx, ST_EINVAL, "st_map_eval: NULL buffer");
+  const st_model_cfg& c = ctx->cfg;
+  const int P = op->desc.P;
+  if (kv->max_len + P + n_gen > c.max_pos)
+    return fail(ctx, ST_EINVAL, "st_map_eval: document + prompt + generated tokens exceed max_pos");
+  if ((c.dtype == ST_BF16 && c.vocab % 256) || (c.dtype == ST_F32 && c.vocab % 128))
+    return fail(ctx, ST_EUNSUPPORTED, "st_map_eval: the vocabulary must be a multiple of 256 (bf16) / 128 (f32)");
+  OpSet os;
+  int64_t rows = 0;
+  int pairs = 0;
+  float* dummy_l = reinterpret_cast<float*>(tokens_dev);   // no label head in the map operator
+  RC(make_opset(ctx, kv, 1, &op, &tuple_ids_dev, &n, &dummy_l, &tokens_dev, &os, &rows, &pairs));
+  cudaStream_t s = S(stream);
+  const int64_t cap = std::max<int64_t>(ctx->eval_rows_cap > 0 ? ctx->eval_rows_cap : kDefaultEvalRows, P);
+  const int per = (int)std::max<int64_t>(1, std::min<int64_t>(n, cap / P));
+  const int kd = c.hkv * c.hd, G = c.hq / c.hkv, S = P + n_gen;
+  RC(grow(ctx, ctx->ws_eval, eval_bufs(ctx, (int64_t)per * P, per, nullptr, nullptr)));
+  EvalBufs w;
+  eval_bufs(ctx, (int64_t)per * P, per, (char*)ctx->ws_eval.p, &w);
+  // decode cache, per-pair arrays, logits and final-normed rows of one chunk
+  const int64_t layer_elems = (int64_t)per * S * kd;
+  auto layout = [&](char* base, MapCtx* m) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      off = (off + 255) & ~(size_t)255;
+      char* p = base + off;
+      off += bytes;
+      return (void*)p;
+    };
+    m->K = take((size_t)c.layers * layer_elems * ctx->esz);
+    m->V = take((size_t)c.layers * layer_elems * ctx->esz);
+    m->pq0 = (int32_t*)take((size_t)per * 4);
+    m->work = (int32_t*)take((size_t)per * 8);
+    m->logits = (float*)take((size_t)per * c.vocab * 4);
+    m->xn = take((size_t)per * c.d * ctx->esz);
+    return off + 256;
+  };
+  MapCtx mp;
+  RC(grow(ctx, ctx->ws_map, layout(nullptr, &mp)));
+  layout((char*)ctx->ws_map.p, &mp);
+  mp.n_gen = n_gen;
+  mp.S = S;
+  mp.layer_elems = layer_elems;
+  for (int i0 = 0; i0 < n; i0 += per) {
+    const int nc = std::min(per, n - i0);
+    mp.tokens = tokens_dev + (size_t)i0 * n_gen;
+    mp.logits_out = logits_dev ? logits_dev + (size_t)i0 * n_gen * c.vocab : nullptr;
+    RC(eval_chunk(ctx, kv, os, i0, i0 + nc, (int64_t)i0 * P, (int64_t)nc * P, w, s, &mp));
+    if (c.dtype == ST_BF16) {
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      eval_worklist(w.nk, w.pP, nc, G, 1, ctx->longest_first != 0, mp.work, s);
+    }
+    for (int t = 1; t < n_gen; ++t) RC(decode_step(ctx, kv, P, nc, t, w, mp, s));
+  }
+  return ST_OK;
 }
 
 extern "C" int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,

@@ -31,7 +31,10 @@ __global__ void __launch_bounds__(256) k_attn_simt(AttnParams a) {
     vA = reinterpret_cast<const T*>(a.V) + base;
     nA = a.pos[qrow] + 1;
   } else {
-    const int i = a.rowpair[qrow], p = (int)(qrow - a.prow[i]);
+    // query position among the pair's prompt keys: the last nq positions
+    const int i = a.rowpair[qrow];
+    const int64_t qb = a.pq0 ? a.pq0[i] : a.prow[i];
+    const int p = (a.pP[i] - (a.nq > 0 ? a.nq : a.pP[i])) + (int)(qrow - qb);
     const int t = a.tup[i];
     const int64_t base = ((int64_t)g * a.Rp_cap + a.offp[t]) * HD;
     kA = reinterpret_cast<const T*>(a.Kr) + base;

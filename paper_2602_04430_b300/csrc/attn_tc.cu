@@ -160,7 +160,8 @@ struct Work {
   int i, n_doc, P;          // eval
   int t, j0, L;             // prefill
   int lim_max;              // largest causal limit (query position) among the rows
-  int64_t doc_row0, prompt_row0, qrow0;
+  int qoff;                 // (eval) position of the first query among the prompt keys
+  int64_t doc_row0, prompt_row0, qrow0, qbase;
 
   __device__ void decode(const AttnParams& a, const int32_t* items, int w, int zb_count) {
     G = a.hq / a.hkv;
@@ -170,15 +171,18 @@ struct Work {
       g = w % a.hkv;
       i = items[2 * e];
       const int zb = items[2 * e + 1];
-      P = a.pP[i];
+      P = a.pP[i];                                 // prompt keys of the pair
+      const int nq = a.nq > 0 ? a.nq : P;          // its queries: the last nq positions
+      qoff = P - nq;
       row_base = zb * ROWS;
-      rows = min(ROWS, P * G - row_base);
-      lim_max = (row_base + rows - 1) / G;
+      rows = min(ROWS, nq * G - row_base);
+      lim_max = qoff + (row_base + rows - 1) / G;
       const int tt = a.tup[i];
       n_doc = a.nk[i];
       doc_row0 = (int64_t)g * a.Rp_cap + a.offp[tt];
       prompt_row0 = a.prow[i];
-      qrow0 = prompt_row0 + row_base / G;
+      qbase = a.pq0 ? a.pq0[i] : prompt_row0;
+      qrow0 = qbase + row_base / G;
       n_doc_tiles = (n_doc + TK - 1) / TK;
       n_tiles = n_doc_tiles + (min(P, lim_max + 1) + TK - 1) / TK;
     } else {
@@ -194,6 +198,8 @@ struct Work {
       lim_max = min(j0 + ROWS / G, L) - 1;
       n_doc_tiles = lim_max / TK + 1;
       n_tiles = n_doc_tiles;
+      qoff = 0;
+      qbase = 0;
     }
   }
   __device__ TileInfo tile(int ti) const {
@@ -600,7 +606,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       float m = -INFINITY, l = 0.f;
       const int ob = qc % NB;
       const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD;
-      const int lim = MODE == 0 ? W.j0 + pos : pos;   // causal limit of this row
+      const int lim = MODE == 0 ? W.j0 + pos : W.qoff + pos;   // causal limit of this row
       for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
         const int b = c % NB;
         const TileInfo T = W.tile(ti);
@@ -727,7 +733,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         const int rr = W.row_base + r, hh = rr % W.G;
         const bool row_ok = r < W.rows && (MODE == 1 || (W.j0 + pos) < W.L);
         if (row_ok) {
-          if (MODE == 1) orow = (W.prompt_row0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
+          if (MODE == 1) orow = (W.qbase + pos) * a.hq + (int64_t)W.g * W.G + hh;
           else orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
         }
       }
@@ -854,9 +860,9 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   const int G = a.hq / a.hkv;
   CUtensorMap mq, mk, mv, mkp, mvp;
   const uint64_t planes = (uint64_t)a.hkv * a.Rp_cap;
-  const uint64_t prow = (uint64_t)a.qrows;
+  const uint64_t prow = (uint64_t)(a.kvrows > 0 ? a.kvrows : a.qrows);
   const CUtensorMapDataType qt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  bool ok = map_q(&mq, a.q, a.hq, prow, G, qt) &&
+  bool ok = map_q(&mq, a.q, a.hq, (uint64_t)a.qrows, G, qt) &&
             map2d(&mkp, a.kp, (uint64_t)a.hkv * HD, prow, BOX, qt) &&
             map2d(&mvp, a.vp, (uint64_t)a.hkv * HD, prow, BOX, qt);
   if (fp8) ok = ok && map2d_u8(&mk, a.Kr, planes, BOX) && map2d_u8(&mv, a.Vr, planes, BOX);

@@ -109,7 +109,7 @@ struct st_ctx {
   float2* rope = nullptr;         // [max_pos][hd/2] (cos, sin)
   float2* rope_t = nullptr;       // the same, [hd/2][max_pos]
   // workspaces
-  st::DevBuf ws_build, ws_eval, ws_casc;
+  st::DevBuf ws_build, ws_eval, ws_casc, ws_map;
   int64_t build_rows_cap = 0, eval_rows_cap = 0;
   // operator-evaluation schedule (st_autotune_eval): BF16-KV attention layout
   // (0 / 1 = two CTAs per SM, 2 = one CTA per SM) and longest-first work order

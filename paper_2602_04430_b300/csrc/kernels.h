@@ -76,7 +76,8 @@ struct OpSet {
 
 // ---- misc kernels (kernels_misc.cu) ----
 template <typename act_t>
-void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, float* x, cudaStream_t s);
+void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, int vocab, float* x, int* status,
+                cudaStream_t s);
 template <typename act_t>
 void rmsnorm_rows(const float* x, int64_t rows, int d, float eps, act_t* xn, float* inv_rms,
                   cudaStream_t s, int64_t x_ld = 0);
@@ -93,7 +94,8 @@ void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const in
                int32_t* pos, int32_t* tok, int32_t* rowpair, cudaStream_t s);
 // Attention work list: (pair, 128-row block) entries, longest retained
 // documents first; G = query heads per kv head.
-void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, bool longest_first,
+// nq: query positions per pair (0: its prompt length).
+void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int nq, bool longest_first,
                    int32_t* list, cudaStream_t s);
 template <typename act_t>
 void qstats(const act_t* q, const int64_t* off, int t0, int t1, int64_t r0, int hq, int hkv,
@@ -106,6 +108,14 @@ void ea_scores(const act_t* K, const act_t* V, int64_t R, int hkv, int hd, int64
 // when inv_rms is nullptr, from the partial sums of squares ssq[m][parts]
 void pool_rows(const float* x, const float* inv_rms, const float* ssq, int parts, float eps,
                const int64_t* off, int t0, int t1, int64_t r0, int d, float* pooled, cudaStream_t s);
+// Map operator (greedy decode): prompt K/V of one layer into the decode cache
+// [pair][S][kd]; the plan of decode step t; the greedy token of each row.
+void copy_prompt_kv(const void* src, void* dst, int n, int P, int S, int kd, size_t esz, cudaStream_t s);
+void decode_plan(int n, int S, int P, int t, int n_gen, const int32_t* len, const int32_t* tokens,
+                 int32_t* prow, int32_t* pP, int32_t* pq0, int32_t* rowpair, int32_t* pos, int32_t* tok,
+                 cudaStream_t s);
+void argmax_rows(const float* logits, int n, int V, int t, int n_gen, int32_t* tokens, float* logits_out,
+                 int* status, cudaStream_t s);
 // Final RMSNorm of each pair's last prompt row, its operator's label logits and decision.
 void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, const int32_t* pP,
                 const int32_t* pop, const int32_t* pj, int d, float eps, const void* w_lm, int dtype,
@@ -155,6 +165,12 @@ struct AttnParams {
   int n_work = 0;                 // entries in work
   int64_t qrows = 0;              // prompt rows of the call
   int nb = 0;                     // BF16-KV attention layout: 0 / 1 = two CTAs per SM, 2 = one
+  // Decode steps: a pair's queries are its last nq prompt positions (0 = all
+  // pP), their Q rows start at pq0[i] (nullptr: prow[i]); the prompt K/V
+  // tensors have kvrows rows (0: qrows).
+  int nq = 0;
+  const int32_t* pq0 = nullptr;
+  int64_t kvrows = 0;
   const void* kp = nullptr;       // prompt keys kp[(i*P + p)*hkv*hd + g*hd + c]
   const void* vp = nullptr;
   int n = 0, P = 0;
@@ -166,6 +182,16 @@ bool attn_tc_supported(int hq, int hkv, int hd);
 int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s);
 int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int* status,
                     cudaStream_t s);
+
+// ---- host sequencing helpers (api.cu): one projection / RMSNorm / attention step
+int project(st_ctx* ctx, const void* A, const void* W, int M, int N, int K, EpiParams ep, float* tmp,
+            void* h_out, cudaStream_t s);
+int rmsnorm(st_ctx* ctx, const float* x, int64_t rows, void* xn, float* inv, cudaStream_t s);
+int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_items, cudaStream_t s);
+// The projection reads bf16(x) and scales its rows by 1/rms from `ssq`.
+void set_norm_in(EpiParams& ep, const float* ssq, const st_model_cfg& c);
+// The residual epilogue also writes bf16(x) to xb and the partial sums of squares.
+void set_norm_out(EpiParams& ep, void* xb, float* ssq);
 
 // ---- operator evaluation sequence (api.cu), shared by st_op_eval and st_op_eval_noalloc ----
 struct EvalBufs {
@@ -185,8 +211,24 @@ int make_opset(st_ctx* ctx, const st_kv* kv, int n_ops, const st_operator* const
                int32_t* const* labels, OpSet* os, int64_t* rows_total, int* pairs_total);
 // Pairs [p0, p1) of an operator set (their prompt rows start at row_base, `rows`
 // of them) through every layer and the label head.
+// Greedy decode of one chunk of pairs (the map operator): decode cache, per-pair
+// decode arrays and scratch, all device memory.
+struct MapCtx {
+  int n_gen = 0, S = 0;          // tokens to generate; decode-cache rows per pair (P + n_gen)
+  void* K = nullptr;             // [layers][pairs][S][kd] prompt + generated keys (model dtype / f16)
+  void* V = nullptr;
+  int64_t layer_elems = 0;       // elements per layer of K / V
+  int32_t* pq0 = nullptr;        // [pairs]
+  int32_t* work = nullptr;       // [pairs][2] attention work list (one query row per pair)
+  float* logits = nullptr;       // [pairs][vocab]
+  void* xn = nullptr;            // [pairs][d] final-normed rows
+  int32_t* tokens = nullptr;     // [pairs][n_gen] output of the chunk
+  float* logits_out = nullptr;   // optional [pairs][n_gen][vocab]
+};
+// mp: the map operator's prompt pass (keeps every layer's prompt K/V, ends
+// with the first greedy token instead of the label head); nullptr otherwise.
 int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, int64_t row_base,
-               int64_t rows, const EvalBufs& w, cudaStream_t s);
+               int64_t rows, const EvalBufs& w, cudaStream_t s, const MapCtx* mp = nullptr);
 // Prompt rows of pairs [p0, p1) of an operator set.
 int64_t opset_rows(const OpSet& os, int p0, int p1);
 // All pairs of an operator set, in chunks of at most the context's

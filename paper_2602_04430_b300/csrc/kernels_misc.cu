@@ -124,14 +124,14 @@ void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const in
 // order).  One block of 1024 threads; the order within a bucket is arbitrary.
 __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restrict__ nk,
                                                         const int32_t* __restrict__ pP, int n, int G,
-                                                        int sorted, int32_t* list) {
+                                                        int nq, int sorted, int32_t* list) {
   __shared__ int cnt[1024];
   __shared__ int wsum[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   cnt[tid] = 0;
   __syncthreads();
   auto bucket = [&](int i) { return sorted ? 1023 - min((nk[i] + 127) / 128, 1023) : 0; };
-  auto blocks = [&](int i) { return (pP[i] * G + 127) / 128; };
+  auto blocks = [&](int i) { return ((nq > 0 ? nq : pP[i]) * G + 127) / 128; };
   for (int i = tid; i < n; i += 1024) atomicAdd(&cnt[bucket(i)], blocks(i));
   __syncthreads();
   // exclusive prefix sum over the buckets
@@ -166,10 +166,10 @@ __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restric
   }
 }
 
-void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, bool longest_first,
+void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int nq, bool longest_first,
                    int32_t* list, cudaStream_t s) {
   if (np <= 0) return;
-  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, np, G, longest_first ? 1 : 0, list);
+  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, np, G, nq, longest_first ? 1 : 0, list);
 }
 
 // Retained counts and padded (64-slot) offsets of every tuple, one block.
@@ -209,28 +209,36 @@ void nkeep_offp(const int64_t* off, int T, double r, int32_t* nkeep, int64_t* of
 }
 
 // ------------------------------------------------------------------ embedding
+// x[m] = E[tok[m]] (float32 residual stream).  A token id outside
+// [0, vocab) embeds as zeros and records ST_EINVAL in *status.
 template <typename act_t>
-__global__ void k_embed(const int32_t* __restrict__ tok, int64_t rows,
-                        const act_t* __restrict__ E, int d, float* __restrict__ x) {
+__global__ void k_embed(const int32_t* __restrict__ tok, int64_t rows, const act_t* __restrict__ E, int d,
+                        int vocab, float* __restrict__ x, int* status) {
   const int per = d / 4;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * per) return;
   int64_t m = i / per;
   int c = (int)(i % per) * 4;
   const int t = tok[m];
-  const act_t* e = E + (int64_t)t * d + c;
-  float4 v = make_float4(to_f(e[0]), to_f(e[1]), to_f(e[2]), to_f(e[3]));
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (t >= 0 && t < vocab) {
+    const act_t* e = E + (int64_t)t * d + c;
+    v = make_float4(to_f(e[0]), to_f(e[1]), to_f(e[2]), to_f(e[3]));
+  } else if (c == 0) {
+    atomicCAS(status, ST_OK, ST_EINVAL);
+  }
   *reinterpret_cast<float4*>(x + m * d + c) = v;
 }
 
 template <typename act_t>
-void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, float* x, cudaStream_t s) {
+void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, int vocab, float* x, int* status,
+                cudaStream_t s) {
   int64_t n = rows * (d / 4);
   if (n <= 0) return;
-  k_embed<act_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tok, rows, E, d, x);
+  k_embed<act_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tok, rows, E, d, vocab, x, status);
 }
-template void embed_rows<float>(const int32_t*, int64_t, const float*, int, float*, cudaStream_t);
-template void embed_rows<bf16>(const int32_t*, int64_t, const bf16*, int, float*, cudaStream_t);
+template void embed_rows<float>(const int32_t*, int64_t, const float*, int, int, float*, int*, cudaStream_t);
+template void embed_rows<bf16>(const int32_t*, int64_t, const bf16*, int, int, float*, int*, cudaStream_t);
 
 // ------------------------------------------------------------------ RMSNorm
 __device__ __forceinline__ void store4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -557,6 +565,107 @@ void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, co
     k_label_head<bf16><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const bf16*)w_lm);
   else
     k_label_head<float><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const float*)w_lm);
+}
+
+// ------------------------------------------------------------------ map operator (decode)
+// Prompt K/V of one layer from the evaluation layout [pair * P + p][kd] into
+// the decode cache [pair][S][kd], 16 bytes per thread: rows p < P copied, rows
+// P .. S-1 (the generated tokens' keys, written by later steps) zeroed.  The
+// zeros matter: the attention's P.V product runs over whole 32-key chunks of
+// the cache, and a zero probability times a non-finite stale value would be NaN.
+__global__ void k_copy_prompt_kv(const uint4* __restrict__ src, uint4* __restrict__ dst, int n, int P,
+                                 int S, int row_vecs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)n * S * row_vecs;
+  if (i >= total) return;
+  const int64_t row = i / row_vecs;
+  const int c = (int)(i % row_vecs);
+  const int64_t pr = row / S, p = row % S;
+  dst[i] = p < P ? src[(pr * P + p) * row_vecs + c] : make_uint4(0u, 0u, 0u, 0u);
+}
+
+void copy_prompt_kv(const void* src, void* dst, int n, int P, int S, int kd, size_t esz, cudaStream_t s) {
+  const int row_vecs = (int)(kd * esz / 16);
+  const int64_t total = (int64_t)n * S * row_vecs;
+  if (total <= 0) return;
+  k_copy_prompt_kv<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const uint4*)src, (uint4*)dst, n, P, S,
+                                                                   row_vecs);
+}
+
+// Decode step t >= 1 (one query row per pair): pair i's keys are the rows
+// i*S .. i*S + P + t - 1 of the decode cache, its query is Q row i at RoPE
+// position L_i + P + t - 1, fed the token generated at step t - 1.
+__global__ void k_decode_plan(int n, int S, int P, int t, int n_gen, const int32_t* __restrict__ len,
+                              const int32_t* __restrict__ tokens, int32_t* prow, int32_t* pP,
+                              int32_t* pq0, int32_t* rowpair, int32_t* pos, int32_t* tok) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  prow[i] = i * S;
+  pP[i] = P + t;
+  pq0[i] = i;
+  rowpair[i] = i;
+  pos[i] = len[i] + P + t - 1;
+  tok[i] = tokens[(int64_t)i * n_gen + t - 1];
+}
+
+void decode_plan(int n, int S, int P, int t, int n_gen, const int32_t* len, const int32_t* tokens,
+                 int32_t* prow, int32_t* pP, int32_t* pq0, int32_t* rowpair, int32_t* pos, int32_t* tok,
+                 cudaStream_t s) {
+  if (n <= 0) return;
+  k_decode_plan<<<(n + 255) / 256, 256, 0, s>>>(n, S, P, t, n_gen, len, tokens, prow, pP, pq0, rowpair,
+                                                pos, tok);
+}
+
+// Block per row: the greedy token argmax_v logits[i][v] (ties to the lowest
+// v), into tokens[i * n_gen + t]; optionally the row of logits into
+// logits_out[(i * n_gen + t) * V ...].  A row without a finite maximum (NaN
+// logits) yields token 0 and ST_ENAN in *status, so the next step's embedding
+// never reads outside the table.
+__global__ void __launch_bounds__(256) k_argmax_rows(const float* __restrict__ logits, int V, int t,
+                                                     int n_gen, int32_t* tokens, float* logits_out,
+                                                     int* status) {
+  __shared__ float bv[256];
+  __shared__ int bi[256];
+  const int i = blockIdx.x;
+  const float* z = logits + (int64_t)i * V;
+  float best = -INFINITY;
+  int arg = 0x7fffffff;
+  for (int v = threadIdx.x; v < V; v += blockDim.x) {
+    const float x = z[v];
+    if (x > best || (x == best && v < arg)) {
+      best = x;
+      arg = v;
+    }
+    if (logits_out) logits_out[((int64_t)i * n_gen + t) * V + v] = x;
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const float x = bv[threadIdx.x + o];
+      const int a2 = bi[threadIdx.x + o];
+      if (x > bv[threadIdx.x] || (x == bv[threadIdx.x] && a2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = x;
+        bi[threadIdx.x] = a2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int tok = bi[0];
+    if (tok < 0 || tok >= V) {
+      tok = 0;
+      atomicCAS(status, ST_OK, ST_ENAN);
+    }
+    tokens[(int64_t)i * n_gen + t] = tok;
+  }
+}
+
+void argmax_rows(const float* logits, int n, int V, int t, int n_gen, int32_t* tokens, float* logits_out,
+                 int* status, cudaStream_t s) {
+  if (n <= 0) return;
+  k_argmax_rows<<<n, 256, 0, s>>>(logits, V, t, n_gen, tokens, logits_out, status);
 }
 
 // ------------------------------------------------------------------ SwiGLU (float32 path)

@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(i32)]),
         "st_set_schedule": (i32, [VP, ctypes.POINTER(TuneChoice)]),
         "st_selftest_wait": (i32, [VP, i64, VP]),
+        "st_map_eval": (i32, [VP, VP, VP, VP, i32, i32, VP, VP, VP]),
         "st_cascade_run": (i32, [i32, ctypes.POINTER(StageDesc), VP, i32, VP, VP, ctypes.POINTER(i32),
                                  ctypes.POINTER(ctypes.c_float), VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
@@ -322,6 +323,19 @@ class Operator:
         self.model.check(self.L.st_op_eval(self.model.h, kv.h, self.h, _ptr(tuple_ids), n,
                                            _ptr(logits), _ptr(labels), _stream(stream)))
         return logits, labels
+
+    def map(self, kv: KVCache, tuple_ids, n_gen: int, with_logits: bool = False, stream=None):
+        """Greedy decode of n_gen tokens per tuple (``st_map_eval``); returns the
+        [n][n_gen] token tensor (and the [n][n_gen][vocab] logits if asked)."""
+        import torch
+        n = int(tuple_ids.numel())
+        tokens = torch.empty((n, n_gen), dtype=torch.int32, device="cuda")
+        logits = (torch.empty((n, n_gen, self.model.cfg.vocab), dtype=torch.float32, device="cuda")
+                  if with_logits else None)
+        self.model.check(self.L.st_map_eval(self.model.h, kv.h, self.h, _ptr(tuple_ids), n, int(n_gen),
+                                            _ptr(tokens), _ptr(logits) if logits is not None else None,
+                                            _stream(stream)))
+        return (tokens, logits) if with_logits else tokens
 
     def eval_noalloc(self, kv: KVCache, tuple_ids, logits, labels, stream=None):
         """Same as ``eval`` through the entry that allocates no device memory (its

@@ -171,3 +171,30 @@ def test_bounded_wait_timeout_is_reported_and_recoverable(run):
     assert torch.isfinite(lg).all()
     with pytest.raises(stretto.StrettoError):
         model.selftest_wait(limit_cycles=10)         # limit out of range
+
+
+def test_out_of_range_token_is_reported_not_read(run):
+    """A token id outside [0, vocab) in the table is caught by the embedding's
+    own bounds check: it embeds as zeros, st_status reports ST_EINVAL once, and
+    the context keeps working."""
+    import torch
+    from paper_2602_04430_b300 import stretto, synth
+    cfg, model = run["cfg"], run["model"]
+    table = synth.make_table(synth.TABLES["tiny"], cfg.vocab, seed=7, n_tuples=4)
+    tok = table["tokens"].copy()
+    tok[3], tok[-1] = cfg.vocab, -1
+    model.status()
+    kv = model.kv_alloc(table["offsets"])
+    kv.build(torch.from_numpy(tok).cuda())
+    torch.cuda.synchronize()
+    with pytest.raises(stretto.StrettoError) as e:
+        model.status()
+    assert e.value.code == stretto.ST_EINVAL
+    model.status()
+    kv.build(torch.from_numpy(table["tokens"]).cuda())
+    kv.retain(1.0)
+    op = model.operator(synth.make_prompt(16, cfg.vocab, seed=8, r=1.0))
+    lg, _ = op.eval(kv, torch.arange(kv.T, dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    model.status()
+    assert torch.isfinite(lg).all()

@@ -243,3 +243,25 @@ def test_cascade_stages_definition():
     # a stage that is never unsure ends the cascade
     labels, stage, counts = cascade_stages([d1[:3], d0[:3], d2[:3]])
     assert counts == [3, 0, 0] and stage == [0, 0, 0] and labels == d1[:3]
+
+
+def test_map_eval_cached_equals_from_scratch():
+    """Greedy decode over the cached document (r = 1) equals decoding document +
+    prompt + generated tokens from scratch: the same tokens and logits (positions
+    L + P + t, causal visibility of the generated tokens)."""
+    from oracle.operator import kv_build, map_eval, map_eval_from_scratch, retained_kv
+    from paper_2602_04430_b300 import synth
+    cfg = synth.MODELS["tiny_f32"]
+    w = synth.make_weights(cfg, seed=81)
+    rng = np.random.Generator(np.random.PCG64(82))
+    prompt = rng.integers(0, cfg.vocab, size=6)
+    for L in (1, 9, 33):
+        doc = rng.integers(0, cfg.vocab, size=L)
+        Kr, Vr, _ = retained_kv(kv_build(cfg, w, doc), 1.0)
+        toks, logs = map_eval(cfg, w, L, Kr, Vr, prompt, 5)
+        toks2, logs2 = map_eval_from_scratch(cfg, w, doc, prompt, 5)
+        assert toks == toks2
+        np.testing.assert_allclose(logs, logs2, rtol=1e-10, atol=1e-12)
+        assert all(0 <= t < cfg.vocab for t in toks)
+        # every token is the argmax of its step's logits
+        assert all(int(np.argmax(z)) == t for z, t in zip(logs, toks))
