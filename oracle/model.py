@@ -74,13 +74,19 @@ def attention(q: np.ndarray, k: np.ndarray, v: np.ndarray, visible: np.ndarray) 
     return out
 
 
-def qkv(cfg, lw: dict, x: np.ndarray, pos: np.ndarray):
-    """Pre-norm projections of one layer with RoPE applied to q and k."""
+def qkv_pre(cfg, lw: dict, x: np.ndarray):
+    """Pre-norm projections of one layer, before RoPE: q [n, Hq, hd], k and v [n, Hkv, hd]."""
     h = rmsnorm(x, cfg.eps)
     n = x.shape[0]
     q = (h @ lw["wq"].T.astype(F64)).reshape(n, cfg.hq, cfg.hd)
     k = (h @ lw["wk"].T.astype(F64)).reshape(n, cfg.hkv, cfg.hd)
     v = (h @ lw["wv"].T.astype(F64)).reshape(n, cfg.hkv, cfg.hd)
+    return q, k, v
+
+
+def qkv(cfg, lw: dict, x: np.ndarray, pos: np.ndarray):
+    """Pre-norm projections of one layer with RoPE applied to q and k."""
+    q, k, v = qkv_pre(cfg, lw, x)
     return rope(q, pos, cfg.rope_theta), rope(k, pos, cfg.rope_theta), v
 
 
@@ -98,11 +104,12 @@ def causal_mask(n: int) -> np.ndarray:
     return np.tril(np.ones((n, n), dtype=bool))
 
 
-def forward(cfg, w: dict, tokens: np.ndarray, collect: bool = False):
+def forward(cfg, w: dict, tokens: np.ndarray, collect: bool = False, pre_rope_q: bool = False):
     """Causal forward pass over ``tokens`` at positions 0..n-1.
 
     Returns the final-normed hidden states ``[n][d]``; with ``collect`` also the
-    per-layer post-RoPE (q, k, v).
+    per-layer post-RoPE (q, k, v), and with ``pre_rope_q`` as well the
+    per-layer queries before RoPE: entries (q, k, v, q_pre).
     """
     tokens = np.asarray(tokens, dtype=np.int64)
     n = tokens.shape[0]
@@ -111,9 +118,10 @@ def forward(cfg, w: dict, tokens: np.ndarray, collect: bool = False):
     mask = causal_mask(n)
     per_layer = []
     for lw in w["layers"]:
-        q, k, v = qkv(cfg, lw, x, pos)
+        q_pre, k_pre, v = qkv_pre(cfg, lw, x)
+        q, k = rope(q_pre, pos, cfg.rope_theta), rope(k_pre, pos, cfg.rope_theta)
         if collect:
-            per_layer.append((q, k, v))
+            per_layer.append((q, k, v, q_pre) if pre_rope_q else (q, k, v))
         o = attention(q, k, v, mask)
         x = attn_out_and_ffn(cfg, lw, x, o)
     xf = rmsnorm(x, cfg.eps)
