@@ -141,6 +141,40 @@ void st_kv_free(st_kv* kv);
  * tuple.  Processed in chunks of whole tuples. */
 int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, void* stream);
 
+/* ---- retention scoring (ablation of Sec. 5's query-agnostic choice) ----
+ *
+ * ST_SCORE_EA_LITE (default): the score documented at st_kv_build.
+ * ST_SCORE_EA_FULL: Expected Attention with the RoPE rotation averaged over
+ *   the future positions: per tuple, layer and kv head, mu and Sigma are the
+ *   mean and full population covariance of the group's PRE-RoPE queries over
+ *   the document; Rbar = (1/F) sum_{p=L}^{L+F-1} R(p) is the mean RoPE
+ *   rotation over the horizon of F positions after the document;
+ *   m = Rbar mu, M = Rbar Sigma Rbar^T, and slot j scores
+ *     m.k_j/sqrt(hd) + k_j^T M k_j/(2 hd) + ln(||v_j|| + 1e-12)
+ *   (the log of E[exp(q.k_j/sqrt(hd))] ||v_j|| for q ~ N(m, M)).
+ * Query-specific scores: st_kv_score_query. */
+#define ST_SCORE_EA_LITE 0
+#define ST_SCORE_EA_FULL 1
+
+/* Selects the score of later st_kv_build calls on this context.  horizon: F
+ * for ST_SCORE_EA_FULL (1 .. 4096), ignored for EA-lite.  Builds then need
+ * hd in {32, 64} (ST_EUNSUPPORTED otherwise) and every document length + F
+ * <= max_pos (ST_EINVAL).  Errors: ST_EINVAL (mode, horizon >= max_pos),
+ * ST_ENOMEM. */
+int st_set_scoring(st_ctx* ctx, int32_t mode, int32_t horizon);
+
+/* Query-specific scores (the contrast of Sec. 5, which keeps a query-agnostic
+ * cache): forwards op's prompt against every tuple's whole cache (every slot,
+ * whatever op's own r), which must hold a retained profile at r = 1 in the
+ * model dtype, and replaces the cache's
+ * scores by the attention probability that the prompt's queries (every prompt
+ * position and query head of the group) put on each document slot, softmax
+ * over the document slots and the visible prompt keys, per layer and kv head.
+ * A following st_kv_retain ranks by these scores; st_kv_build restores the
+ * query-agnostic ones.  hd must be 32 or 64.
+ * Errors: ST_EINVAL (no r = 1 profile in the model dtype), ST_EUNSUPPORTED. */
+int st_kv_score_query(st_ctx* ctx, st_kv* kv, const st_operator* op, void* stream);
+
 /* Query-agnostic retention (Sec. 5): per tuple, layer and kv head, rank all
  * slots by (score descending, slot index ascending; -0 == +0) and keep the
  * first n_keep(L, r) = clamp(floor(r*L + 0.5), 1, L) (IEEE double arithmetic)

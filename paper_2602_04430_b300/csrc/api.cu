@@ -98,6 +98,7 @@ std::vector<Chunk> plan_chunks(const std::vector<int64_t>& off, int64_t cap) {
 
 struct BuildWs {
   float *x, *inv_rms, *mu, *s2, *tmp, *ssq;
+  float *qm, *qM;   // full Expected Attention moments of the chunk's tuples (else null)
   void *xn, *q, *o, *h;
   int32_t *rowtup, *pos;
 };
@@ -119,6 +120,11 @@ size_t build_ws_bytes(const st_ctx* ctx, int64_t rows, int64_t tuples, BuildWs* 
   ws.ssq = cv.take<float>(rows * (c.d / 128));
   ws.rowtup = cv.take<int32_t>(rows);
   ws.pos = cv.take<int32_t>(rows);
+  ws.qm = ws.qM = nullptr;
+  if (ctx->score_mode == ST_SCORE_EA_FULL) {
+    ws.qm = cv.take<float>(tuples * c.hkv * c.hd);
+    ws.qM = cv.take<float>(tuples * c.hkv * c.hd * c.hd);
+  }
   if (w) *w = ws;
   return cv.off + 256;
 }
@@ -362,6 +368,8 @@ extern "C" void st_destroy(st_ctx* ctx) {
   cudaFree(ctx->ws_eval.p);
   cudaFree(ctx->ws_casc.p);
   cudaFree(ctx->ws_map.p);
+  cudaFree(ctx->ws_score.p);
+  cudaFree(ctx->rope_avg);
   for (auto& r : ctx->prof.pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -486,6 +494,11 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
   if (!ctx || !kv || !tokens_dev || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_build: bad argument");
   const st_model_cfg& c = ctx->cfg;
   cudaStream_t s = S(stream);
+  const bool ea_full = ctx->score_mode == ST_SCORE_EA_FULL;
+  if (ea_full && !ea_full_supported(c.hd))
+    return fail(ctx, ST_EUNSUPPORTED, "st_kv_build: full Expected Attention scores need hd 32 or 64");
+  if (ea_full && (int64_t)kv->max_len + ctx->score_horizon > c.max_pos)
+    return fail(ctx, ST_EINVAL, "st_kv_build: document length + scoring horizon exceeds max_pos");
   const int64_t cap = std::max<int64_t>(ctx->build_rows_cap > 0 ? ctx->build_rows_cap : kDefaultBuildRows,
                                         kv->max_len);
   std::vector<Chunk> chunks = plan_chunks(kv->off_h, cap);
@@ -556,7 +569,16 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
       const int64_t i0 = kv->item_start[ch.t0], i1 = kv->item_start[ch.t1];
       RC(attention(ctx, a, kv->items + 2 * i0, (int)(i1 - i0), s));
       // retention statistics and scores of this layer
-      {
+      if (ea_full) {
+        Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+        float* sl = kv->scores + (size_t)l * c.hkv * kv->R;
+        if (c.dtype == ST_BF16)
+          ea_full_scores<bf16>((const bf16*)w.q, (const bf16*)Kl, (const bf16*)Vl, kv->R, kv->off, ch.t0, ch.t1,
+                               ch.r0, c.hq, c.hkv, c.hd, ctx->rope, ctx->rope_avg, w.qm, w.qM, sl, s);
+        else
+          ea_full_scores<float>((const float*)w.q, (const float*)Kl, (const float*)Vl, kv->R, kv->off, ch.t0,
+                                ch.t1, ch.r0, c.hq, c.hkv, c.hd, ctx->rope, ctx->rope_avg, w.qm, w.qM, sl, s);
+      } else {
         Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
         if (c.dtype == ST_BF16) {
           qstats<bf16>((const bf16*)w.q, kv->off, ch.t0, ch.t1, ch.r0, c.hq, c.hkv, c.hd, w.mu, w.s2, s);
@@ -564,7 +586,7 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
           qstats<float>((const float*)w.q, kv->off, ch.t0, ch.t1, ch.r0, c.hq, c.hkv, c.hd, w.mu, w.s2, s);
         }
       }
-      {
+      if (!ea_full) {
         Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
         float* sl = kv->scores + (size_t)l * c.hkv * kv->R;
         if (c.dtype == ST_BF16)
@@ -877,7 +899,7 @@ int64_t opset_rows(const OpSet& os, int p0, int p1) {
 int map_head(st_ctx* ctx, int np, int t, const EvalBufs& w, const MapCtx& mp, cudaStream_t s);
 
 int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, int64_t row_base,
-               int64_t M, const EvalBufs& w, cudaStream_t s, const MapCtx* mp) {
+               int64_t M, const EvalBufs& w, cudaStream_t s, const MapCtx* mp, float* qscore) {
   const st_model_cfg& c = ctx->cfg;
   const int np = p1 - p0;
   if (np <= 0) return ST_OK;
@@ -967,6 +989,19 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
     a.kv_dtype = kv->kv_dtype;
     a.nb = ctx->attn_nb;
     RC(attention(ctx, a, nullptr, 0, s));
+    if (qscore) {
+      // query-specific scores: this layer's prompt attention mass on the document slots
+      Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+      const size_t kl = (size_t)l * c.hkv * kv->R * c.hd;
+      float* sl = qscore + (size_t)l * c.hkv * kv->R;
+      if (c.dtype == ST_BF16)
+        query_mass<bf16>((const bf16*)w.q, (const bf16*)w.kp, (const bf16*)kv->K + kl, kv->R, kv->off, w.tup,
+                         w.prow, os.op[0].P, np, c.hq, c.hkv, c.hd, a.scale, sl, s);
+      else
+        query_mass<float>((const float*)w.q, (const float*)w.kp, (const float*)kv->K + kl, kv->R, kv->off,
+                          w.tup, w.prow, os.op[0].P, np, c.hq, c.hkv, c.hd, a.scale, sl, s);
+      CKLAUNCH();
+    }
     if (l + 1 < c.layers) {
       EpiParams eo;
       eo.mode = EPI_RESID;
@@ -1178,7 +1213,8 @@ int decode_step(st_ctx* ctx, const st_kv* kv, int P, int np, int t, const EvalBu
 
 // Chunks the pairs (operator-major) into batches of at most `cap` prompt rows
 // and runs each through eval_chunk.
-int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s, DevBuf* ws) {
+int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s, DevBuf* ws,
+              float* qscore) {
   const st_model_cfg& c = ctx->cfg;
   int maxP = 1;
   for (int k = 0; k < os.n_ops; ++k) maxP = std::max(maxP, os.op[k].P);
@@ -1209,7 +1245,7 @@ int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStre
   for (size_t q = 0; q + 1 < cuts.size(); ++q) {
     const int64_t M = opset_rows(os, cuts[q], cuts[q + 1]);
     if (M == 0) continue;
-    RC(eval_chunk(ctx, kv, os, cuts[q], cuts[q + 1], row_base, M, w, s));
+    RC(eval_chunk(ctx, kv, os, cuts[q], cuts[q + 1], row_base, M, w, s, nullptr, qscore));
     row_base += M;
   }
   (void)c;
@@ -1304,6 +1340,66 @@ extern "C" int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
     }
     for (int t = 1; t < n_gen; ++t) RC(decode_step(ctx, kv, P, nc, t, w, mp, s));
   }
+  return ST_OK;
+}
+
+extern "C" int st_set_scoring(st_ctx* ctx, int32_t mode, int32_t horizon) {
+  if (!ctx) return fail(nullptr, ST_EINVAL, "st_set_scoring: NULL context");
+  const st_model_cfg& c = ctx->cfg;
+  if (mode == ST_SCORE_EA_LITE) {
+    ctx->score_mode = mode;
+    return ST_OK;
+  }
+  if (mode != ST_SCORE_EA_FULL || horizon < 1 || horizon > 4096 || horizon >= c.max_pos)
+    return fail(ctx, ST_EINVAL, "st_set_scoring: mode or horizon out of range");
+  // averaged rotation of every document length L <= max_pos - F, in double:
+  // (1/F) sum over p = L .. L+F-1 of (cos, sin)(p theta^(-2i/hd))
+  const int half = c.hd / 2;
+  std::vector<float2> tab((size_t)c.max_pos * half, make_float2(0.f, 0.f));
+  for (int i = 0; i < half; ++i) {
+    const double w = std::pow((double)c.rope_theta, -2.0 * i / c.hd);
+    for (int L = 0; L + horizon <= c.max_pos; ++L) {
+      double cs = 0.0, sn = 0.0;
+      for (int p = L; p < L + horizon; ++p) {
+        cs += std::cos((double)p * w);
+        sn += std::sin((double)p * w);
+      }
+      tab[(size_t)L * half + i] = make_float2((float)(cs / horizon), (float)(sn / horizon));
+    }
+  }
+  if (!ctx->rope_avg) RC(dev_alloc(ctx, (void**)&ctx->rope_avg, tab.size() * sizeof(float2)));
+  CK(cudaMemcpy(ctx->rope_avg, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  ctx->score_mode = mode;
+  ctx->score_horizon = horizon;
+  return ST_OK;
+}
+
+extern "C" int st_kv_score_query(st_ctx* ctx, st_kv* kv, const st_operator* op, void* stream) {
+  if (!ctx || !kv || !op || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_score_query: bad argument");
+  const st_model_cfg& c = ctx->cfg;
+  if (!kv->built || kv->r != 1.0 || kv->kv_dtype != c.dtype)
+    return fail(ctx, ST_EINVAL, "st_kv_score_query: the cache needs a retained profile at r = 1 in the model dtype");
+  if (!ea_full_supported(c.hd)) return fail(ctx, ST_EUNSUPPORTED, "st_kv_score_query: hd must be 32 or 64");
+  const int T = kv->T, nl = op->desc.n_labels;
+  if (T == 0) return ST_OK;
+  const size_t need = (size_t)T * 4 + 256 + (size_t)T * nl * 4 + 256 + (size_t)T * 4 + 256;
+  RC(grow(ctx, ctx->ws_score, need));
+  Carve cv(ctx->ws_score.p);
+  int32_t* ids = cv.take<int32_t>(T);
+  float* logits = cv.take<float>((int64_t)T * nl);
+  int32_t* labels = cv.take<int32_t>(T);
+  cudaStream_t s = S(stream);
+  std::vector<int32_t> h(T);
+  for (int t = 0; t < T; ++t) h[t] = t;
+  CK(cudaMemcpyAsync(ids, h.data(), (size_t)T * 4, cudaMemcpyHostToDevice, s));
+  OpSet os;
+  int64_t rows = 0;
+  int pairs = 0, n = T;
+  const int32_t* idp = ids;
+  RC(make_opset(ctx, kv, 1, &op, &idp, &n, &logits, &labels, &os, &rows, &pairs));
+  os.op[0].r = 1.0;   // the prompt attends to every document slot, whatever the operator's own r
+  RC(run_opset(ctx, kv, os, pairs, s, nullptr, kv->scores));
+  CK(cudaStreamSynchronize(s));   // the host id buffer
   return ST_OK;
 }
 

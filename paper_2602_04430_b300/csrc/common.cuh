@@ -115,6 +115,13 @@ struct st_ctx {
   // (0 / 1 = two CTAs per SM, 2 = one CTA per SM) and longest-first work order
   int attn_nb = 0;
   int longest_first = 1;
+  // retention scores of st_kv_build (st_set_scoring): ST_SCORE_EA_LITE or
+  // ST_SCORE_EA_FULL with its horizon F and the averaged rotation table
+  // rope_avg[L][hd/2] = (mean cos, mean sin) over positions L .. L+F-1
+  int score_mode = ST_SCORE_EA_LITE;
+  int score_horizon = 0;
+  float2* rope_avg = nullptr;
+  st::DevBuf ws_score;            // st_kv_score_query: tuple ids, logits, labels
   int32_t* dstatus = nullptr;     // device status word of bounded waits (ST_ETIMEOUT)
   std::string err;
   st::Prof prof;

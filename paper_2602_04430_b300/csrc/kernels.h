@@ -104,6 +104,21 @@ template <typename act_t>
 void ea_scores(const act_t* K, const act_t* V, int64_t R, int hkv, int hd, int64_t r0,
                int64_t rows, const int32_t* rowtup, int t0, const float* mu, const float* s2,
                float* scores, cudaStream_t s);
+// Scoring ablation (scoring.cu).  Full Expected Attention scores of the chunk's
+// tuples [t0, t1) at one layer (hd 32 or 64): query moments into m_ws
+// [tuples][hkv][hd] and M_ws [tuples][hkv][hd][hd], then every slot's score.
+bool ea_full_supported(int hd);
+template <typename act_t>
+void ea_full_scores(const act_t* q, const act_t* K, const act_t* V, int64_t R, const int64_t* off, int t0,
+                    int t1, int64_t r0, int hq, int hkv, int hd, const float2* rope, const float2* ravg,
+                    float* m_ws, float* M_ws, float* scores, cudaStream_t s);
+// Query-specific scores of one layer: for each of the np pairs (tuple tup[i],
+// prompt rows prow[i] .. + P of q / kp), the attention probability its prompt
+// queries put on every document slot, written to scores[g][off[t] + j].
+template <typename act_t>
+void query_mass(const act_t* q, const act_t* kp, const act_t* K, int64_t R, const int64_t* off,
+                const int32_t* tup, const int32_t* prow, int P, int np, int hq, int hkv, int hd, float scale,
+                float* scores, cudaStream_t s);
 // pooled[t] = mean of x[m] / rms(x[m]) over tuple t's rows; 1/rms from inv_rms or,
 // when inv_rms is nullptr, from the partial sums of squares ssq[m][parts]
 void pool_rows(const float* x, const float* inv_rms, const float* ssq, int parts, float eps,
@@ -227,14 +242,19 @@ struct MapCtx {
 };
 // mp: the map operator's prompt pass (keeps every layer's prompt K/V, ends
 // with the first greedy token instead of the label head); nullptr otherwise.
+// qscore: the query-specific scoring pass (one operator, r = 1 cache): every
+// layer's prompt attention mass on the document slots into qscore
+// [layers][hkv][R]; nullptr otherwise.
 int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, int64_t row_base,
-               int64_t rows, const EvalBufs& w, cudaStream_t s, const MapCtx* mp = nullptr);
+               int64_t rows, const EvalBufs& w, cudaStream_t s, const MapCtx* mp = nullptr,
+               float* qscore = nullptr);
 // Prompt rows of pairs [p0, p1) of an operator set.
 int64_t opset_rows(const OpSet& os, int p0, int p1);
 // All pairs of an operator set, in chunks of at most the context's
 // eval_rows_cap prompt rows; ws: the workspace (nullptr: the context's, grown
 // as needed; otherwise grown as needed too, and owned by the caller).
-int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s, DevBuf* ws);
+int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStream_t s, DevBuf* ws,
+              float* qscore = nullptr);
 
 // ---- retention (retain.cu) ----
 struct RetainParams {

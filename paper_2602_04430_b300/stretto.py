@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstretto.so")
 
 ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ENAN, ST_EUNSUPPORTED = range(7)
+ST_SCORE_EA_LITE, ST_SCORE_EA_FULL = 0, 1
 ST_F32, ST_BF16, ST_E4M3 = 0, 1, 2
 ST_OP_FILTER, ST_OP_CLASSIFY = 0, 1
 ST_REJECT, ST_ACCEPT, ST_UNSURE = 0, 1, 2
@@ -110,6 +111,8 @@ def lib() -> ctypes.CDLL:
         "st_set_schedule": (i32, [VP, ctypes.POINTER(TuneChoice)]),
         "st_selftest_wait": (i32, [VP, i64, VP]),
         "st_map_eval": (i32, [VP, VP, VP, VP, i32, i32, VP, VP, VP]),
+        "st_set_scoring": (i32, [VP, i32, i32]),
+        "st_kv_score_query": (i32, [VP, VP, VP, VP]),
         "st_cascade_run": (i32, [i32, ctypes.POINTER(StageDesc), VP, i32, VP, VP, ctypes.POINTER(i32),
                                  ctypes.POINTER(ctypes.c_float), VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
@@ -197,6 +200,10 @@ class Model:
     def status(self, stream=None):
         self.check(self.L.st_status(self.h, _stream(stream)))
 
+    def set_scoring(self, mode: int, horizon: int = 64):
+        """Retention score of later ``KVCache.build`` calls (``st_set_scoring``)."""
+        self.check(self.L.st_set_scoring(self.h, int(mode), int(horizon)))
+
     def kv_alloc(self, offsets: np.ndarray) -> "KVCache":
         return KVCache(self, offsets)
 
@@ -264,6 +271,11 @@ class KVCache:
 
     def status(self, stream=None):
         self.model.check(self.L.st_kv_status(self.model.h, self.h, _stream(stream)))
+
+    def score_query(self, op: "Operator", stream=None):
+        """Replace the scores by ``op``'s query-specific ones (``st_kv_score_query``;
+        needs a retained profile at r = 1 in the model dtype)."""
+        self.model.check(self.L.st_kv_score_query(self.model.h, self.h, op.h, _stream(stream)))
 
     def view_bytes(self, which: int) -> int:
         p, n = VP(), ctypes.c_size_t()
