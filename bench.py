@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-operator arm")
     ap.add_argument("--batched-tuples", type=int, default=2048)
     ap.add_argument("--no-map", action="store_true", help="skip the map-operator (greedy decode) arm")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the retention-scoring ablation arm")
     ap.add_argument("--map-tuples", type=int, default=1024)
     ap.add_argument("--map-gen", type=int, default=16)
     return ap.parse_args()
@@ -437,6 +438,69 @@ def map_arm(args, model, kv, cfg, T, stretto, synth, torch):
             "per_family_ms": {k: v["ms"] / reps for k, v in pf.items()}}
 
 
+def scoring_ablation_arm(args, model, kv, cfg, T, tok, op, stretto, synth, torch):
+    """Retention-scoring ablation on the bench's table and operator prompt:
+    EA-lite (the default), full Expected Attention (future-position RoPE
+    averaging, horizon 64) and query-specific scores (the operator's own prompt
+    attention at r = 1).  For each, at r in {0.5, 0.25, 0.1}: agreement of the
+    decisions with the uncompressed (r = 1) decisions and the normwise error of
+    the label logits; and what each costs (build with its scores, query
+    scoring pass), CUDA events after a warm-up."""
+    import dataclasses
+    ids = torch.arange(T, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ops = {r: model.operator(dataclasses.replace(op, r=r)) for r in (1.0, 0.5, 0.25, 0.1)}
+
+    def timed(fn):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1)
+
+    def evaluate(r):
+        lg, lb = ops[r].eval(kv, ids)
+        torch.cuda.synchronize()
+        return lg.cpu().numpy().astype(np.float64), lb.cpu().numpy()
+
+    kv.build(tok)
+    kv.retain(1.0)
+    z1, d1 = evaluate(1.0)
+    den = float(np.abs(z1).max())
+    out = {"tuples": T, "horizon": 64, "reference": "same operator on the uncompressed cache (r = 1)"}
+
+    def fidelity(tag):
+        res = {}
+        for r in (0.5, 0.25, 0.1):
+            kv.retain(r)
+            z, d = evaluate(r)
+            res[str(r)] = {"decision_agreement": float(np.mean(d == d1)),
+                           "logit_normwise_err": float(np.abs(z - z1).max() / den),
+                           "margin_mean_abs_err": float(np.mean(np.abs((z[:, 0] - z[:, 1]) - (z1[:, 0] - z1[:, 1]))))}
+        out[tag] = res
+
+    ms_lite = timed(lambda: kv.build(tok))
+    fidelity("ea_lite")
+    model.set_scoring(stretto.ST_SCORE_EA_FULL, 64)
+    kv.build(tok)
+    ms_full = timed(lambda: kv.build(tok))
+    fidelity("ea_full")
+    kv.retain(1.0)
+    kv.score_query(ops[1.0])
+    kv.retain(1.0)
+    ms_query = timed(lambda: kv.score_query(ops[1.0]))
+    fidelity("query_specific")
+    model.set_scoring(stretto.ST_SCORE_EA_LITE)
+    kv.build(tok)
+    kv.retain(op.r)
+    torch.cuda.synchronize()
+    model.status()
+    out["cost_ms"] = {"kv_build_ea_lite": ms_lite, "kv_build_ea_full": ms_full,
+                      "query_scoring_pass_per_operator": ms_query}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -561,6 +625,9 @@ def main():
     mapr = None
     if not args.no_map and rank == 0:
         mapr = map_arm(args, model, kv, cfg, T, stretto, synth, torch)
+    ablation = None
+    if not args.no_ablation and rank == 0:
+        ablation = scoring_ablation_arm(args, model, kv, cfg, T, tok, op, stretto, synth, torch)
     proxy = None
     if not args.no_proxy and rank == 0:
         proxy = proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch)
@@ -601,7 +668,8 @@ def main():
                 "config": config_dict(args, cfg, table, op), "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                 "per_family_ms": {k: v["ms"] for k, v in prof.items()},
-                "op_eval": out, "map": mapr, "proxy_fp8": proxy, "batched_ops": batched}
+                "op_eval": out, "map": mapr, "scoring_ablation": ablation, "proxy_fp8": proxy,
+                "batched_ops": batched}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

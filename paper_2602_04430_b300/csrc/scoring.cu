@@ -26,15 +26,17 @@ constexpr int kB = 32;   // query vectors staged per batch (k_qmoments)
 // (pre = R(j)^T post).  One pass, shifted by the group's first query (at
 // position 0 RoPE is the identity): S1 = sum(d), S2 = sum(d d^T) with
 // d = q_pre - shift; mu = shift + S1/N, Sigma = S2/N - (S1/N)(S1/N)^T.
-// Thread (a, c0) owns entries Sigma[a][c0 .. c0+EPT).
+// S2 in register blocks: thread (rb, cb) of a 16 x 16 grid owns the BLK x BLK
+// block at rows BLK*rb, columns BLK*cb (BLK = HD/16), two vector loads of the
+// staged item per BLK*BLK FMAs.
 template <typename act_t, int HD>
 __global__ void __launch_bounds__(256) k_qmoments(const act_t* __restrict__ q, const int64_t* __restrict__ off,
                                                   int t0, int64_t r0, int hq, int hkv,
                                                   const float2* __restrict__ rope,
                                                   const float2* __restrict__ ravg, float* __restrict__ m_out,
                                                   float* __restrict__ M_out) {
-  constexpr int H2 = HD / 2, TPR = 256 / HD, EPT = HD / TPR;
-  __shared__ float d[kB][HD];
+  constexpr int H2 = HD / 2, TPR = 256 / HD, EPT = HD / TPR, BLK = HD / 16;
+  __shared__ __align__(16) float d[kB][HD];
   __shared__ float shift[HD], mean_d[HD];
   __shared__ float sig[HD][HD + 1];
   const int lt = blockIdx.x / hkv, g = blockIdx.x % hkv, t = t0 + lt;
@@ -44,10 +46,12 @@ __global__ void __launch_bounds__(256) k_qmoments(const act_t* __restrict__ q, c
   const act_t* base = q + (off[t] - r0) * hq * HD + (int64_t)g * G * HD;
   if (tid < HD) shift[tid] = to_f(base[tid]);
   __syncthreads();
-  const int a = tid / TPR, c0 = (tid % TPR) * EPT;
-  float acc[EPT];
+  const int rb = tid / 16, cb = tid % 16;
+  float acc[BLK][BLK];
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) acc[e] = 0.f;
+  for (int x = 0; x < BLK; ++x)
+#pragma unroll
+    for (int y = 0; y < BLK; ++y) acc[x][y] = 0.f;
   float s1 = 0.f;
   for (int64_t n0 = 0; n0 < N; n0 += kB) {
     for (int idx = tid; idx < kB * H2; idx += 256) {
@@ -69,9 +73,23 @@ __global__ void __launch_bounds__(256) k_qmoments(const act_t* __restrict__ q, c
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < kB; ++k) {
-      const float da = d[k][a];
+      float ra[BLK], ca[BLK];
+      if (BLK == 4) {
+        const float4 u = *reinterpret_cast<const float4*>(&d[k][BLK * rb]);
+        const float4 w = *reinterpret_cast<const float4*>(&d[k][BLK * cb]);
+        ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w;
+        ca[0] = w.x; ca[1] = w.y; ca[2] = w.z; ca[3] = w.w;
+      } else {
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) acc[e] = fmaf(da, d[k][c0 + e], acc[e]);
+        for (int x = 0; x < BLK; ++x) {
+          ra[x] = d[k][BLK * rb + x];
+          ca[x] = d[k][BLK * cb + x];
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < BLK; ++x)
+#pragma unroll
+        for (int y = 0; y < BLK; ++y) acc[x][y] = fmaf(ra[x], ca[y], acc[x][y]);
     }
     if (tid < HD)
       for (int k = 0; k < kB; ++k) s1 += d[k][tid];
@@ -81,11 +99,18 @@ __global__ void __launch_bounds__(256) k_qmoments(const act_t* __restrict__ q, c
   if (tid < HD) mean_d[tid] = s1 * invN;
   __syncthreads();
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) sig[a][c0 + e] = acc[e] * invN - mean_d[a] * mean_d[c0 + e];
-  const float2* rb = ravg + (int64_t)L * H2;   // (mean cos, mean sin) of the horizon after L
+  for (int x = 0; x < BLK; ++x)
+#pragma unroll
+    for (int y = 0; y < BLK; ++y) {
+      const int ra = BLK * rb + x, ca = BLK * cb + y;
+      sig[ra][ca] = acc[x][y] * invN - mean_d[ra] * mean_d[ca];
+    }
+  const int a = tid / TPR, c0 = (tid % TPR) * EPT;   // entries of the rotation steps
+  __syncthreads();
+  const float2* rv = ravg + (int64_t)L * H2;   // (mean cos, mean sin) of the horizon after L
   float* mo = m_out + ((int64_t)lt * hkv + g) * HD;
   if (tid < H2) {
-    const float2 r = rb[tid];
+    const float2 r = rv[tid];
     const float ua = shift[tid] + mean_d[tid], ub = shift[tid + H2] + mean_d[tid + H2];
     mo[tid] = r.x * ua - r.y * ub;
     mo[tid + H2] = r.y * ua + r.x * ub;
@@ -95,7 +120,7 @@ __global__ void __launch_bounds__(256) k_qmoments(const act_t* __restrict__ q, c
   float tmp[EPT];
   {
     const int i = a < H2 ? a : a - H2;
-    const float2 r = rb[i];
+    const float2 r = rv[i];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const float lo = sig[i][c0 + e], hi = sig[i + H2][c0 + e];
@@ -110,7 +135,7 @@ __global__ void __launch_bounds__(256) k_qmoments(const act_t* __restrict__ q, c
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     const int c = c0 + e, i = c < H2 ? c : c - H2;
-    const float2 r = rb[i];
+    const float2 r = rv[i];
     const float lo = sig[a][i], hi = sig[a][i + H2];
     Mo[c] = c < H2 ? r.x * lo - r.y * hi : r.y * lo + r.x * hi;
   }
@@ -166,9 +191,26 @@ __global__ void __launch_bounds__(256) k_quad_scores(const act_t* __restrict__ K
   }
 }
 
+// q . k for a query in registers and a staged key row (16-byte aligned), four
+// independent partial sums.
+template <int HD>
+__device__ __forceinline__ float dot_row(const float (&qr)[HD], const float* kr) {
+  float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int c = 0; c < HD; c += 4) {
+    const float4 k4 = *reinterpret_cast<const float4*>(kr + c);
+    s[0] = fmaf(qr[c], k4.x, s[0]);
+    s[1] = fmaf(qr[c + 1], k4.y, s[1]);
+    s[2] = fmaf(qr[c + 2], k4.z, s[2]);
+    s[3] = fmaf(qr[c + 3], k4.w, s[3]);
+  }
+  return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
 // Block per (pair, kv head), one thread per prompt query row (p, head of the
-// group), 256 rows per pass.  Pass 1: the row's softmax maximum and
-// normaliser over the document slots and its visible prompt keys; pass 2:
+// group), blockDim.x (<= 256, a multiple of 32) rows per pass.  Pass 1: the
+// row's softmax maximum and normaliser over the document slots and its
+// visible prompt keys; pass 2:
 // each document slot's probability, summed over the rows (warp sums, then
 // shared-memory atomics), added into scores.  Keys are staged 64 at a time.
 template <typename act_t, int HD>
@@ -179,7 +221,7 @@ __global__ void __launch_bounds__(256) k_query_mass(const act_t* __restrict__ q,
                                                     const int32_t* __restrict__ prow, int P, int hq, int hkv,
                                                     float scale, float* __restrict__ scores) {
   constexpr int TK = 64;
-  __shared__ float ks[TK][HD + 1];
+  __shared__ __align__(16) float ks[TK][HD];   // every thread reads the same key: broadcast
   __shared__ float msum[TK];
   const int i = blockIdx.x / hkv, g = blockIdx.x % hkv, G = hq / hkv;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -215,9 +257,7 @@ __global__ void __launch_bounds__(256) k_query_mass(const act_t* __restrict__ q,
       for (int kk = 0; kk < nk; ++kk) {
         const int key = k0 + kk;
         if (live && (key < L || key - L <= p)) {
-          float s = 0.f;
-#pragma unroll
-          for (int c = 0; c < HD; ++c) s = fmaf(qr[c], ks[kk][c], s);
+          const float s = dot_row<HD>(qr, ks[kk]);
           if (s > m) {
             l = l * expf(m - s) + 1.f;
             m = s;
@@ -232,23 +272,18 @@ __global__ void __launch_bounds__(256) k_query_mass(const act_t* __restrict__ q,
     for (int k0 = 0; k0 < L; k0 += TK) {
       const int nk = min(TK, L - k0);
       stage(k0, nk);
-      if (tid < TK) msum[tid] = 0.f;
+      for (int e = tid; e < TK; e += blockDim.x) msum[e] = 0.f;
       __syncthreads();
       for (int kk = 0; kk < nk; ++kk) {
         float pv = 0.f;
-        if (live) {
-          float s = 0.f;
-#pragma unroll
-          for (int c = 0; c < HD; ++c) s = fmaf(qr[c], ks[kk][c], s);
-          pv = expf(s - m) * inv_l;
-        }
+        if (live) pv = expf(dot_row<HD>(qr, ks[kk]) - m) * inv_l;
         pv = warp_sum(pv);
         if (lane == 0) atomicAdd(&msum[kk], pv);
       }
       __syncthreads();
-      if (tid < nk) {
-        float* o = scores + (int64_t)g * R + d0 + k0 + tid;
-        *o = (rb == 0 ? 0.f : *o) + msum[tid];
+      for (int e = tid; e < nk; e += blockDim.x) {
+        float* o = scores + (int64_t)g * R + d0 + k0 + e;
+        *o = (rb == 0 ? 0.f : *o) + msum[e];
       }
       __syncthreads();
     }
@@ -286,10 +321,12 @@ void query_mass(const act_t* q, const act_t* kp, const act_t* K, int64_t R, cons
                 float* scores, cudaStream_t s) {
   const int nb = np * hkv;
   if (nb <= 0) return;
+  const int rows = P * (hq / hkv);
+  const int threads = rows >= 256 ? 256 : (rows + 31) / 32 * 32;
   if (hd == 64)
-    k_query_mass<act_t, 64><<<nb, 256, 0, s>>>(q, kp, K, R, off, tup, prow, P, hq, hkv, scale, scores);
+    k_query_mass<act_t, 64><<<nb, threads, 0, s>>>(q, kp, K, R, off, tup, prow, P, hq, hkv, scale, scores);
   else
-    k_query_mass<act_t, 32><<<nb, 256, 0, s>>>(q, kp, K, R, off, tup, prow, P, hq, hkv, scale, scores);
+    k_query_mass<act_t, 32><<<nb, threads, 0, s>>>(q, kp, K, R, off, tup, prow, P, hq, hkv, scale, scores);
 }
 template void query_mass<float>(const float*, const float*, const float*, int64_t, const int64_t*,
                                 const int32_t*, const int32_t*, int, int, int, int, int, float, float*,
