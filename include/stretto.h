@@ -141,6 +141,13 @@ void st_kv_free(st_kv* kv);
  * tuple.  Processed in chunks of whole tuples. */
 int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, void* stream);
 
+/* Process-wide choice of the BF16 projection GEMM for more than 128 rows:
+ * on != 0 (default) runs CTA pairs with the 2-SM MMA (256 x 256 tiles, each
+ * SM staging half of the A and W tiles); 0 runs one CTA per 128 x 256 tile.
+ * Results are identical up to the order of the f32 accumulation (the same K
+ * steps in the same order: bit-identical in practice).  Always ST_OK. */
+int st_set_gemm_pairs(int32_t on);
+
 /* ---- retention scoring (ablation of Sec. 5's query-agnostic choice) ----
  *
  * ST_SCORE_EA_LITE (default): the score documented at st_kv_build.

@@ -1343,6 +1343,11 @@ extern "C" int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
   return ST_OK;
 }
 
+extern "C" int st_set_gemm_pairs(int32_t on) {
+  set_gemm_pairs(on != 0);
+  return ST_OK;
+}
+
 extern "C" int st_set_scoring(st_ctx* ctx, int32_t mode, int32_t horizon) {
   if (!ctx) return fail(nullptr, ST_EINVAL, "st_set_scoring: NULL context");
   const st_model_cfg& c = ctx->cfg;

@@ -378,6 +378,163 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- CTA-pair variant
+// A cluster of two CTAs (on two SMs) computes 256 x 256 output tiles with the
+// 2-SM MMA (tcgen05.mma.cta_group::2, M = 256): CTA rank r stages rows
+// [128 r, 128 r + 128) of the A tile and of the W tile, so each SM moves
+// 32 KB per 64-deep stage instead of 48 KB for the same tensor work, and
+// holds its 128 accumulator rows in its own TMEM (both CTAs' allocations are
+// one collective 512-column allocation).  The leader (rank 0) issues the MMAs;
+// both CTAs' TMA loads count their bytes on the leader's full barrier; each
+// MMA commit arrives on the stage-empty (or accumulator-full) barrier of both
+// CTAs; both CTAs' epilogue warps release an accumulator with a remote arrive
+// on the leader's barrier.  Same warp roles and epilogues as k_gemm_tc.
+constexpr int P_BM = 256, P_HALF = 128, P_STAGES = 6;
+constexpr int P_STAGE_BYTES = 2 * P_HALF * BK * 2;   // A half + W half, 32 KB
+constexpr size_t P_SMEM_BYTES = (size_t)P_STAGES * P_STAGE_BYTES + 8 * STG_BYTES + 1024 + 256;
+static_assert(P_SMEM_BYTES <= 232448, "CTA-pair GEMM shared memory");
+
+struct PairBars {
+  uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2];
+  uint32_t tmem_base;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_gemm_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               int M, int N, int K, EpiParams ep, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  constexpr int HALF_BYTES = P_HALF * BK * 2;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + P_STAGES * HALF_BYTES;
+  uint8_t* stg = smem + P_STAGES * P_STAGE_BYTES;
+  PairBars* bars = reinterpret_cast<PairBars*>(stg + 8 * STG_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = ptx::cluster_ctarank();
+  const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+  const int m_blocks = (M + P_BM - 1) / P_BM, n_blocks = N / BN;
+  const int tiles = m_blocks * n_blocks, nk = K / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      ptx::mbar_init(&bars->full[s], 1);
+      ptx::mbar_init(&bars->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&bars->tfull[b], 1);
+      ptx::mbar_init(&bars->tempty[b], 16);   // 8 epilogue warps in each CTA
+    }
+    ptx::fence_mbar_init();
+    ptx::tma_prefetch_desc(&tmA);
+    ptx::tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc2(&bars->tmem_base, TMEM_COLS);
+    ptx::tmem_relinquish2();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  // both CTAs' barriers are initialised and the pair's TMEM allocated before
+  // any remote arrive, load completion or MMA
+  ptx::cluster_sync();
+  ptx::tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int last_par[P_STAGES];
+      for (int s = 0; s < P_STAGES; ++s) last_par[s] = -1;
+      bool ok = true;
+      for (int tile = cluster; tile < tiles && ok; tile += n_clusters) {
+        const int mb = tile / n_blocks, nb = tile % n_blocks;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!ptx::mbar_wait(&bars->empty[stage], phase ^ 1)) { ok = false; break; }
+          if (rank == 0) ptx::mbar_arrive_expect_tx(&bars->full[stage], 2 * P_STAGE_BYTES);
+          const uint32_t full_cl = ptx::mapa(ptx::smem_u32(&bars->full[stage]), 0);
+          ptx::tma_load_2d_pair(sA + stage * HALF_BYTES, &tmA, full_cl, kb * BK, mb * P_BM + (int)rank * P_HALF);
+          ptx::tma_load_2d_pair(sB + stage * HALF_BYTES, &tmB, full_cl, kb * BK, nb * BN + (int)rank * P_HALF);
+          last_par[stage] = (int)phase;
+          if (++stage == P_STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      // every load this CTA issued has landed once the leader's MMAs that read
+      // it have completed (their commit arrives on this CTA's empty barrier)
+      for (int s = 0; s < P_STAGES; ++s)
+        if (last_par[s] >= 0 && !ptx::mbar_wait(&bars->empty[s], (uint32_t)last_par[s], 100000000LL))
+          ok = false;
+      if (!ok) atomicExch(status, ST_ETIMEOUT);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc = ptx::idesc_bf16_f32(P_BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int it = 0;
+      for (int tile = cluster; tile < tiles && ok; tile += n_clusters, ++it) {
+        const int buf = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!ptx::mbar_wait(&bars->tempty[buf], (use & 1) ^ 1)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(buf * BN);
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!ptx::mbar_wait(&bars->full[stage], phase)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t a0 = ptx::smem_u32(sA + stage * HALF_BYTES);
+          const uint32_t b0 = ptx::smem_u32(sB + stage * HALF_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            ptx::mma_f16_pair(dt, ptx::desc_kmajor_sw128(a0 + k * 32), ptx::desc_kmajor_sw128(b0 + k * 32),
+                              idesc, (kb | k) != 0);
+          ptx::mma_commit_pair(&bars->empty[stage], 0x3);
+          if (++stage == P_STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
+        ptx::mma_commit_pair(&bars->tfull[buf], 0x3);
+      }
+      if (!ok) atomicExch(status, ST_ETIMEOUT);
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3;          // TMEM lanes 32*quarter .. (warp % 4 rule)
+    const int half = (warp - 2) >> 2;      // which half of the tile's columns
+    const uint32_t tempty_cl[2] = {ptx::mapa(ptx::smem_u32(&bars->tempty[0]), 0),
+                                   ptx::mapa(ptx::smem_u32(&bars->tempty[1]), 0)};
+    int it = 0;
+    uint4 pre[8];
+    for (int tile = cluster; tile < tiles; tile += n_clusters, ++it) {
+      const int buf = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      const int mb = tile / n_blocks, nb = tile % n_blocks;
+      const int row0 = mb * P_BM + (int)rank * P_HALF + quarter * 32;
+      if (EPI == EPI_RESID)
+        resid_load(ep, pre, row0, M - row0 < 32 ? M - row0 : 32, nb * BN + half * (BN / 2), lane);
+      if (!ptx::mbar_wait(&bars->tfull[buf], use & 1)) {
+        atomicExch(status, ST_ETIMEOUT);
+        break;
+      }
+      ptx::tc_fence_after();
+      const uint32_t taddr = tmem + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
+      epilogue_tile<EPI>(ep, stg + (warp - 2) * STG_BYTES, row0, nb * BN, taddr, M, half, lane, pre);
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive_cluster(tempty_cl[buf]);
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  // neither CTA leaves while the pair's MMAs, loads or arrives may still touch it
+  ptx::cluster_sync();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc2(tmem, TMEM_COLS);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -414,16 +571,70 @@ bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, u
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool g_gemm_pairs = true;   // st_set_gemm_pairs: CTA-pair kernel for M > 128
+
 }  // namespace
+
+void set_gemm_pairs(bool on) { g_gemm_pairs = on; }
+bool gemm_pair_enabled() { return g_gemm_pairs; }
 
 bool gemm_tc_supported(int M, int N, int K) {
   return M > 0 && N > 0 && K > 0 && N % BN == 0 && K % BK == 0;
+}
+
+// CTA-pair launch: clusters of two, as many as can be resident at once (the
+// tile loop is persistent, so a cluster that waited for a free SM pair would
+// add a second wave).
+template <int EPI>
+cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const EpiParams& ep,
+                        int* status, cudaStream_t s) {
+  static int max_clusters = 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = P_SMEM_BYTES;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (!max_clusters) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc2<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(2 * (num_sms() / 2));
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc2<EPI>, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    max_clusters = n;
+  }
+  const int tiles = ((M + P_BM - 1) / P_BM) * (N / BN);
+  cfg.gridDim = dim3(2 * (tiles < max_clusters ? tiles : max_clusters));
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc2<EPI>, ma, mb, M, N, K, ep, status);
 }
 
 int gemm_tc(const bf16* A, const bf16* W, int M, int N, int K, const EpiParams& ep, int* status,
             cudaStream_t s) {
   if (M <= 0) return ST_OK;
   if (!gemm_tc_supported(M, N, K)) return ST_EUNSUPPORTED;
+  if (M > BM && gemm_pair_enabled()) {
+    // 2-SM MMA: W and A tiles of 128 rows per CTA
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, P_HALF, (uint64_t)ep.a_ld) ||
+        !make_map(&mb, W, (uint64_t)K, (uint64_t)N, P_HALF))
+      return ST_ECUDA;
+    cudaError_t e;
+    switch (ep.mode) {
+      case EPI_QKV: e = launch_pair<EPI_QKV>(ma, mb, M, N, K, ep, status, s); break;
+      case EPI_RESID: e = launch_pair<EPI_RESID>(ma, mb, M, N, K, ep, status, s); break;
+      case EPI_SWIGLU: e = launch_pair<EPI_SWIGLU>(ma, mb, M, N, K, ep, status, s); break;
+      default: e = launch_pair<EPI_STORE_F32>(ma, mb, M, N, K, ep, status, s); break;
+    }
+    return e == cudaSuccess ? ST_OK : ST_ECUDA;
+  }
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, BM, (uint64_t)ep.a_ld) ||
       !make_map(&mb, W, (uint64_t)K, (uint64_t)N, BN))

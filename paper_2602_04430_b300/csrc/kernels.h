@@ -144,6 +144,9 @@ template <typename act_t>
 void gemm_simt(const act_t* A, const act_t* W, int M, int N, int K, const EpiParams& ep,
                cudaStream_t s);
 bool gemm_tc_supported(int M, int N, int K);
+// Process-wide choice of the tcgen05 GEMM for M > 128: CTA pairs (2-SM MMA,
+// the default) or single CTAs.
+void set_gemm_pairs(bool on);
 int gemm_tc(const bf16* A, const bf16* W, int M, int N, int K, const EpiParams& ep, int* status,
             cudaStream_t s);
 

@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
         "st_selftest_wait": (i32, [VP, i64, VP]),
         "st_map_eval": (i32, [VP, VP, VP, VP, i32, i32, VP, VP, VP]),
         "st_set_scoring": (i32, [VP, i32, i32]),
+        "st_set_gemm_pairs": (i32, [i32]),
         "st_kv_score_query": (i32, [VP, VP, VP, VP]),
         "st_cascade_run": (i32, [i32, ctypes.POINTER(StageDesc), VP, i32, VP, VP, ctypes.POINTER(i32),
                                  ctypes.POINTER(ctypes.c_float), VP]),
@@ -522,6 +523,11 @@ def cascade_run(stages, tuple_ids, labels=None, stage=None, stream=None):
     m0.check(m0.L.st_cascade_run(k, arr, _ptr(tuple_ids), n, _ptr(labels), _ptr(stage), counts, ms,
                                  _stream(stream)))
     return labels, stage, list(counts), list(ms)
+
+
+def set_gemm_pairs(on: bool):
+    """Process-wide GEMM kernel choice (``st_set_gemm_pairs``)."""
+    lib().st_set_gemm_pairs(1 if on else 0)
 
 
 def version() -> str:
