@@ -31,11 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tuples/s: proxy+FP8 vs plain BF16 at >=99% label agreement; % HBM roofline"
-# DRAM bytes per k_gemm_tc launch on this workload, from the ncu capture of the
-# current kernel (25.2 GB over the four projections of one layer of the
-# 1024-tuple table, 610,382 rows each, scaled to the 652,000 rows of this
-# workload's average launch).  Set to None whenever the kernel changes.
-GEMM_TRAFFIC_PER_LAUNCH = 6.73e9
+# DRAM bytes per projection-GEMM launch on this workload (the CTA-pair kernel
+# k_gemm_tc2, which runs every launch of more than 128 rows), from the ncu
+# capture of the current kernel (27.86 GB over the four projections of one
+# layer of the 1024-tuple table, 610,382 rows each, scaled to the 652,000 rows
+# of this workload's average launch).  Set to None whenever the kernel changes.
+GEMM_TRAFFIC_PER_LAUNCH = 7.44e9
 
 
 def parse():
@@ -580,7 +581,7 @@ def main():
     peak_src = "measured" if peaks else "fallback"
     g = prof["gemm"]
     gemm_tf = g["flops"] / (g["ms"] / 1000.0) / 1e12 if g["ms"] > 0 else 0.0
-    roofline = {"kernel": "k_gemm_tc (tcgen05 BF16 projection GEMM)", "bound": "tensor",
+    roofline = {"kernel": "k_gemm_tc2 (tcgen05 BF16 projection GEMM, 2-SM MMA on CTA pairs)", "bound": "tensor",
                 "achieved": gemm_tf, "peak": tf_peak, "unit": "TFLOP/s",
                 "frac": gemm_tf / tf_peak, "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "traffic": GEMM_TRAFFIC_PER_LAUNCH,
