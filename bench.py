@@ -65,11 +65,11 @@ def parse():
 
 
 def workload(args, rank=0):
-    from paper_2602_04430_b300 import synth
+    from paper_2602_04430_b300 import multigpu, synth
     cfg = synth.MODELS["c2_bf16"]
     tcfg = synth.TABLES["c2"]
     T = args.tuples or tcfg.n_tuples
-    table = synth.make_table(tcfg, cfg.vocab, seed=1000 + 17 * rank, n_tuples=T)
+    table = synth.make_table(tcfg, cfg.vocab, seed=multigpu.rank_seed(1000, rank), n_tuples=T)
     op = synth.make_prompt(32, cfg.vocab, seed=77, label_ids=(1, 0), r=args.r)
     return cfg, tcfg, table, op
 
@@ -515,7 +515,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2602_04430_b300 import stretto, synth
+    from paper_2602_04430_b300 import multigpu, stretto, synth
     from paper_2602_04430_b300 import build as _b
     _b.build()
     cfg, tcfg, table, op = workload(args, rank)
@@ -561,12 +561,9 @@ def main():
     prof = model.prof_read()
     launches = model.launch_count()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = multigpu.reduce_max(ms, dist, device="cuda")
     total_tuples = T * world * args.steps
-    value = total_tuples / (ms_max / 1000.0)
+    value = multigpu.job_rate([T * args.steps] * world, ms_max)
     clocks = clk.summary()
     model.status()
 
@@ -646,11 +643,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             opr.run_host(kv, tok_h, lg_h, lb_h, kvd)
-        el = time.perf_counter() - t0
-        te = torch.tensor([el], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": total_tuples / float(te.item()), "unit": "tuples/s",
+        el_max = multigpu.reduce_max((time.perf_counter() - t0) * 1000.0, dist, device="cuda")
+        e2e = {"value": multigpu.job_rate([T * args.steps] * world, el_max), "unit": "tuples/s",
                "h2d_bytes_per_step": int(tok_h.numel() * 4),
                "d2h_bytes_per_step": int(T * 2 * 4 + T * 4),
                "path": "st_run_host: pinned host tokens -> device, kv_build, kv_retain, op_eval, "
