@@ -208,6 +208,27 @@ int st_status(st_ctx* ctx, void* stream);
  * Errors: ST_EINVAL (limit out of range). */
 int st_selftest_wait(st_ctx* ctx, int64_t limit_cycles, void* stream);
 
+/* ---- retained-profile repository (Sec. 5: caches computed offline, stored,
+ * and loaded per profile = model + compression ratio at query time) ----
+ *
+ * A profile blob holds what operator evaluation reads: the rank-ordered
+ * retained K / V (used slots only), the E4M3 block scales, the per-tuple
+ * retained counts and padded offsets, the pooled document states, and a
+ * header (model shape and dtype, retained dtype, r, the table's size and
+ * document offsets).  Blobs are plain host memory; the caller stores them.
+ * st_kv_profile_bytes: size of the blob of kv's current profile
+ *   (ST_EINVAL if kv has none).
+ * st_kv_export: writes it to `host` (>= that many bytes); synchronises `stream`.
+ * st_kv_import: makes the blob kv's retained profile.  kv must come from
+ *   st_kv_alloc with the same document offsets; its full cache is not needed
+ *   (operators at r' <= the profile's r evaluate right away), but st_kv_retain
+ *   afterwards needs a new st_kv_build.  Synchronises `stream`.
+ *   Errors: ST_EINVAL (not a blob, truncated, another model / table, corrupt
+ *   counts), ST_ECUDA. */
+int st_kv_profile_bytes(const st_kv* kv, size_t* bytes);
+int st_kv_export(st_ctx* ctx, const st_kv* kv, void* host, size_t bytes, void* stream);
+int st_kv_import(st_ctx* ctx, st_kv* kv, const void* host, size_t bytes, void* stream);
+
 /* Device status of the last retain on `kv`: synchronises `stream`, returns
  * ST_OK or ST_ENAN (and clears it). */
 int st_kv_status(st_ctx* ctx, st_kv* kv, void* stream);

@@ -254,6 +254,7 @@ extern "C" const char* st_last_error(const st_ctx* ctx) {
 
 extern "C" int st_create(const st_model_cfg* cfg, const void* const* weights, void* stream,
                          st_ctx** out) {
+  ST_TRACE("st_create");
   st_ctx* ctx = nullptr;
   if (!cfg || !weights || !out) return fail(nullptr, ST_EINVAL, "st_create: NULL argument");
   *out = nullptr;
@@ -491,6 +492,7 @@ extern "C" void st_kv_free(st_kv* kv) {
 }
 
 extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, void* stream) {
+  ST_TRACE("st_kv_build");
   if (!ctx || !kv || !tokens_dev || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_build: bad argument");
   const st_model_cfg& c = ctx->cfg;
   cudaStream_t s = S(stream);
@@ -634,6 +636,7 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
 }
 
 extern "C" int st_kv_retain(st_ctx* ctx, st_kv* kv, double r, int32_t kv_dtype, void* stream) {
+  ST_TRACE("st_kv_retain");
   if (!ctx || !kv || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_retain: bad argument");
   if (!(r > 0.0 && r <= 1.0)) return fail(ctx, ST_EINVAL, "st_kv_retain: r must lie in (0, 1]");
   const st_model_cfg& c = ctx->cfg;
@@ -748,6 +751,7 @@ extern "C" int st_kv_read(const st_kv* kv, int32_t which, void* dst_dev, size_t 
 
 extern "C" int st_gemm(st_ctx* ctx, const void* A_dev, const void* W_dev, int32_t M, int32_t N,
                        int32_t K, float* C_dev, void* stream) {
+  ST_TRACE("st_gemm");
   if (!ctx || !A_dev || !W_dev || !C_dev || M < 0 || N <= 0 || K <= 0)
     return fail(ctx, ST_EINVAL, "st_gemm: bad argument");
   if (ctx->cfg.dtype == ST_BF16 && !gemm_tc_supported(M > 0 ? M : 1, N, K))
@@ -1257,6 +1261,7 @@ int run_opset(st_ctx* ctx, const st_kv* kv, const OpSet& os, int pairs, cudaStre
 extern "C" int st_op_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
                           const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
                           int32_t* labels_dev, void* stream) {
+  ST_TRACE("st_op_eval");
   if (!ctx || !kv || !op || kv->ctx != ctx || n < 0) return fail(ctx, ST_EINVAL, "st_op_eval: bad argument");
   if (n == 0) return ST_OK;
   if (!tuple_ids_dev || !logits_dev || !labels_dev) return fail(ctx, ST_EINVAL, "st_op_eval: NULL buffer");
@@ -1271,6 +1276,7 @@ extern "C" int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
                                 const st_operator* const* ops, const int32_t* const* tuple_ids_dev,
                                 const int32_t* n, float* const* logits_dev, int32_t* const* labels_dev,
                                 void* stream) {
+  ST_TRACE("st_op_eval_multi");
   if (!ctx) return fail(nullptr, ST_EINVAL, "st_op_eval_multi: NULL context");
   OpSet os;
   int64_t rows = 0;
@@ -1283,6 +1289,7 @@ extern "C" int st_op_eval_multi(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
 extern "C" int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
                            const int32_t* tuple_ids_dev, int32_t n, int32_t n_gen, int32_t* tokens_dev,
                            float* logits_dev, void* stream) {
+  ST_TRACE("st_map_eval");
   if (!ctx || !kv || !op || kv->ctx != ctx || n < 0) return fail(ctx, ST_EINVAL, "st_map_eval: bad argument");
   if (n_gen < 1 || n_gen > 256) return fail(ctx, ST_EINVAL, "st_map_eval: n_gen must lie in 1..256");
   if (n == 0) return ST_OK;
@@ -1349,6 +1356,7 @@ extern "C" int st_set_gemm_pairs(int32_t on) {
 }
 
 extern "C" int st_set_scoring(st_ctx* ctx, int32_t mode, int32_t horizon) {
+  ST_TRACE("st_set_scoring");
   if (!ctx) return fail(nullptr, ST_EINVAL, "st_set_scoring: NULL context");
   const st_model_cfg& c = ctx->cfg;
   if (mode == ST_SCORE_EA_LITE) {
@@ -1380,6 +1388,7 @@ extern "C" int st_set_scoring(st_ctx* ctx, int32_t mode, int32_t horizon) {
 }
 
 extern "C" int st_kv_score_query(st_ctx* ctx, st_kv* kv, const st_operator* op, void* stream) {
+  ST_TRACE("st_kv_score_query");
   if (!ctx || !kv || !op || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_score_query: bad argument");
   const st_model_cfg& c = ctx->cfg;
   if (!kv->built || kv->r != 1.0 || kv->kv_dtype != c.dtype)
@@ -1411,6 +1420,7 @@ extern "C" int st_kv_score_query(st_ctx* ctx, st_kv* kv, const st_operator* op, 
 extern "C" int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,
                            const int32_t* tokens_host, float* logits_host, int32_t* labels_host,
                            void* stream) {
+  ST_TRACE("st_run_host");
   if (!ctx || !kv || !op || !tokens_host || !logits_host || !labels_host)
     return fail(ctx, ST_EINVAL, "st_run_host: bad argument");
   cudaStream_t s = S(stream);

@@ -50,6 +50,7 @@ extern "C" int st_graph_create(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
                                const st_operator* const* ops, const int32_t* const* tuple_ids_dev,
                                const int32_t* n, float* const* logits_dev, int32_t* const* labels_dev,
                                st_graph** out) {
+  ST_TRACE("st_graph_create");
   if (!ctx || !out) return bfail(ctx, ST_EINVAL, "st_graph_create: bad argument");
   *out = nullptr;
   OpSet os;
@@ -98,6 +99,7 @@ extern "C" int st_graph_create(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
 }
 
 extern "C" int st_graph_launch(st_graph* g, void* stream) {
+  ST_TRACE("st_graph_launch");
   if (!g || !g->exec) return ST_EINVAL;
   st_ctx* ctx = g->ctx;
   BCK(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)));
@@ -119,6 +121,7 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
                                 const int32_t* n, float* const* logits_dev, int32_t* const* labels_dev,
                                 void* stream, st_tune_choice* best, st_tune_choice* tried,
                                 int32_t max_tried, int32_t* n_tried) {
+  ST_TRACE("st_autotune_eval");
   if (!ctx || !best) return bfail(ctx, ST_EINVAL, "st_autotune_eval: bad argument");
   OpSet os;
   int64_t rows = 0;

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(1024) k_stage_route(const int32_t* __restrict_
 extern "C" int st_cascade_run(int32_t n_stages, const st_stage* stages, const int32_t* tuple_ids_dev,
                               int32_t n, int32_t* labels_dev, int32_t* stage_dev, int32_t* counts_host,
                               float* ms_host, void* stream) {
+  ST_TRACE("st_cascade_run");
   st_ctx* ctx = (n_stages >= 1 && stages) ? stages[0].ctx : nullptr;
   if (!ctx || n < 0 || (n > 0 && (!tuple_ids_dev || !labels_dev || !stage_dev)))
     return cfail(ctx, ST_EINVAL, "st_cascade_run: bad argument");

@@ -10,9 +10,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/stretto.h"
 
 namespace st {
+
+// NVTX range around one public call (visible in Nsight timelines; a no-op
+// when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define ST_TRACE(name) ::st::TraceRange st_trace_range_(name)
 
 typedef __nv_bfloat16 bf16;
 

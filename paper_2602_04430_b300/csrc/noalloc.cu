@@ -69,6 +69,7 @@ int scratch_address(st_ctx* ctx, void** out) {
 extern "C" int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operator* op,
                                   const int32_t* tuple_ids_dev, int32_t n, float* logits_dev,
                                   int32_t* labels_dev, void* stream) {
+  ST_TRACE("st_op_eval_noalloc");
   if (!ctx) return ST_EINVAL;
   if (!kv || !op || kv->ctx != ctx || n < 0) return na_fail(ctx, ST_EINVAL, "st_op_eval_noalloc: bad argument");
   if (n == 0) return ST_OK;

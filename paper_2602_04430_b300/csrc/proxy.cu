@@ -327,6 +327,7 @@ extern "C" void st_proxy_free(st_proxy* p) {
 extern "C" int st_proxy_train_step(st_ctx* ctx, st_proxy* p, const float* x_dev,
                                    const int32_t* y_dev, const int32_t* batch_dev, int32_t B,
                                    float lr, float* loss_dev, void* stream) {
+  ST_TRACE("st_proxy_train_step");
   if (!ctx || !p || p->ctx != ctx || !x_dev || !y_dev || !batch_dev || B < 1)
     return pfail(ctx, ST_EINVAL, "st_proxy_train_step: bad argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -371,6 +372,7 @@ extern "C" int st_proxy_train_step(st_ctx* ctx, st_proxy* p, const float* x_dev,
 
 extern "C" int st_proxy_eval(st_ctx* ctx, st_proxy* p, const float* x_dev, const int32_t* rows_dev,
                              int32_t n, float* conf_dev, int32_t* label_dev, void* stream) {
+  ST_TRACE("st_proxy_eval");
   if (!ctx || !p || p->ctx != ctx || !x_dev || !conf_dev || !label_dev || n < 0)
     return pfail(ctx, ST_EINVAL, "st_proxy_eval: bad argument");
   if (n == 0) return ST_OK;
@@ -391,6 +393,7 @@ extern "C" int st_proxy_eval(st_ctx* ctx, st_proxy* p, const float* x_dev, const
 extern "C" int st_cascade_compact(st_ctx* ctx, const float* conf_dev, const int32_t* ids_dev,
                                   int32_t n, float tau, int32_t* unsure_dev, int32_t* count_dev,
                                   void* stream) {
+  ST_TRACE("st_cascade_compact");
   if (!ctx || !conf_dev || !unsure_dev || !count_dev || n < 0)
     return pfail(ctx, ST_EINVAL, "st_cascade_compact: bad argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -404,6 +407,7 @@ extern "C" int st_cascade_compact(st_ctx* ctx, const float* conf_dev, const int3
 extern "C" int st_cascade_merge(st_ctx* ctx, const int32_t* proxy_label_dev, int32_t n,
                                 const int32_t* unsure_pos_dev, const int32_t* count_dev,
                                 const int32_t* full_label_dev, int32_t* out_dev, void* stream) {
+  ST_TRACE("st_cascade_merge");
   if (!ctx || !proxy_label_dev || !unsure_pos_dev || !count_dev || !full_label_dev || !out_dev || n < 0)
     return pfail(ctx, ST_EINVAL, "st_cascade_merge: bad argument");
   if (n == 0) return ST_OK;

@@ -113,6 +113,9 @@ def lib() -> ctypes.CDLL:
         "st_map_eval": (i32, [VP, VP, VP, VP, i32, i32, VP, VP, VP]),
         "st_set_scoring": (i32, [VP, i32, i32]),
         "st_set_gemm_pairs": (i32, [i32]),
+        "st_kv_profile_bytes": (i32, [VP, ctypes.POINTER(ctypes.c_size_t)]),
+        "st_kv_export": (i32, [VP, VP, VP, ctypes.c_size_t, VP]),
+        "st_kv_import": (i32, [VP, VP, VP, ctypes.c_size_t, VP]),
         "st_kv_score_query": (i32, [VP, VP, VP, VP]),
         "st_cascade_run": (i32, [i32, ctypes.POINTER(StageDesc), VP, i32, VP, VP, ctypes.POINTER(i32),
                                  ctypes.POINTER(ctypes.c_float), VP]),
@@ -272,6 +275,27 @@ class KVCache:
 
     def status(self, stream=None):
         self.model.check(self.L.st_kv_status(self.model.h, self.h, _stream(stream)))
+
+    def export_profile(self, stream=None) -> np.ndarray:
+        """The current retained profile as a host byte array (``st_kv_export``)."""
+        n = ctypes.c_size_t()
+        self.model.check(self.L.st_kv_profile_bytes(self.h, ctypes.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self.model.check(self.L.st_kv_export(self.model.h, self.h, buf.ctypes.data_as(VP), n.value,
+                                             _stream(stream)))
+        return buf
+
+    def import_profile(self, blob: np.ndarray, stream=None):
+        """Make a blob from ``export_profile`` this cache's retained profile (``st_kv_import``)."""
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        self.model.check(self.L.st_kv_import(self.model.h, self.h, blob.ctypes.data_as(VP), blob.nbytes,
+                                             _stream(stream)))
+
+    def save_profile(self, path: str):
+        self.export_profile().tofile(path)
+
+    def load_profile(self, path: str):
+        self.import_profile(np.fromfile(path, dtype=np.uint8))
 
     def score_query(self, op: "Operator", stream=None):
         """Replace the scores by ``op``'s query-specific ones (``st_kv_score_query``;
