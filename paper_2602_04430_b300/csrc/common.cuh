@@ -49,8 +49,21 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // Load / store n consecutive elements as float (n a multiple of 4 for float, 8 for bf16).
 template <typename T> struct Vec;
+// 16 bytes through the read-only path, not kept in L1 (streamed once).
+__device__ __forceinline__ uint4 ldg_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
 template <> struct Vec<float> {
   static constexpr int N = 4;
+  __device__ __forceinline__ static void unpack(const uint4& v, float* out) {
+    out[0] = __uint_as_float(v.x); out[1] = __uint_as_float(v.y);
+    out[2] = __uint_as_float(v.z); out[3] = __uint_as_float(v.w);
+  }
   __device__ __forceinline__ static void load(const float* p, float* out) {
     float4 v = *reinterpret_cast<const float4*>(p);
     out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
@@ -61,6 +74,14 @@ template <> struct Vec<float> {
 };
 template <> struct Vec<bf16> {
   static constexpr int N = 8;
+  __device__ __forceinline__ static void unpack(const uint4& v, float* out) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(h[i]);
+      out[2 * i] = f.x; out[2 * i + 1] = f.y;
+    }
+  }
   __device__ __forceinline__ static void load(const bf16* p, float* out) {
     uint4 v = *reinterpret_cast<const uint4*>(p);
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);

@@ -313,34 +313,34 @@ __global__ void __launch_bounds__(256) k_qstats(const act_t* __restrict__ q,
   Vec<act_t>::load(base, shift);               // the group's first query vector
 #pragma unroll
   for (int e = 0; e < VN; ++e) a1[e] = a2[e] = 0.f;
-  // four items per thread per step, their loads issued together
-  int64_t it = il;
-  for (; it + 3 * lanes < items; it += 4 * lanes) {
-    float w4[4][VN];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t iu = it + u * lanes, j = iu / G, hh = iu % G;
-      Vec<act_t>::load(base + j * hq * hd + hh * hd, w4[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int e = 0; e < VN; ++e) {
-        const float dv = w4[u][e] - shift[e];
-        a1[e] += dv;
-        a2[e] = fmaf(dv, dv, a2[e]);
-      }
-  }
-  for (; it < items; it += lanes) {
-    const int64_t j = it / G, hh = it % G;
-    Vec<act_t>::load(base + j * hq * hd + hh * hd, v);
+  // eight 16-byte loads per thread in flight (kept raw until accumulated):
+  // the kernel is bound by the bytes in flight per SM
+  auto acc = [&](const uint4& raw) {
+    float w[VN];
+    Vec<act_t>::unpack(raw, w);
 #pragma unroll
     for (int e = 0; e < VN; ++e) {
-      const float dv = v[e] - shift[e];
+      const float dv = w[e] - shift[e];
       a1[e] += dv;
       a2[e] = fmaf(dv, dv, a2[e]);
     }
+  };
+  int64_t it = il;
+  for (; it + 7 * lanes < items; it += 8 * lanes) {
+    uint4 raw[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t iu = it + u * lanes, j = iu / G, hh = iu % G;
+      raw[u] = ldg_stream(reinterpret_cast<const uint4*>(base + j * hq * hd + hh * hd));
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc(raw[u]);
   }
+  for (; it < items; it += lanes) {
+    const int64_t j = it / G, hh = it % G;
+    acc(ldg_stream(reinterpret_cast<const uint4*>(base + j * hq * hd + hh * hd)));
+  }
+  (void)v;
 #pragma unroll
   for (int e = 0; e < VN; ++e) {
     red[0][threadIdx.x][e] = a1[e];
@@ -377,7 +377,8 @@ template void qstats<bf16>(const bf16*, const int64_t*, int, int, int64_t, int, 
 
 // score = mu.k/sqrt(hd) + sum sigma2 k^2/(2hd) + ln(||v|| + 1e-12) per (kv head,
 // slot).  TPR = hd / VN threads share a slot, each reading one 16-byte vector of
-// its K and V rows (a warp reads whole rows), partial sums reduced by shuffles.
+// its K and V rows (a warp reads whole rows); the two terms that are linear in
+// the partial sums are combined per thread, so two sums are shuffle-reduced.
 template <typename act_t>
 __global__ void __launch_bounds__(256) k_scores(const act_t* __restrict__ K, const act_t* __restrict__ V,
                                                 int64_t R, int hkv, int hd, int64_t r0, int64_t rows,
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(256) k_scores(const act_t* __restrict__ K, con
   const int c = (threadIdx.x % tpr) * VN;
   const bool live = i < rows * hkv;
   float d1 = 0.f, d2 = 0.f, vv = 0.f;
+  const float c1 = 1.f / sqrtf((float)hd), c2 = 1.f / (2.0f * (float)hd);
   int g = 0;
   int64_t m = 0;
   if (live) {
@@ -408,14 +410,12 @@ __global__ void __launch_bounds__(256) k_scores(const act_t* __restrict__ K, con
       vv += vx[e] * vx[e];
     }
   }
+  float lin = d1 * c1 + d2 * c2;
   for (int o = tpr / 2; o > 0; o >>= 1) {
-    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    lin += __shfl_xor_sync(0xffffffffu, lin, o);
     vv += __shfl_xor_sync(0xffffffffu, vv, o);
   }
-  if (live && c == 0)
-    scores[(int64_t)g * R + r0 + m] =
-        d1 / sqrtf((float)hd) + d2 / (2.0f * (float)hd) + logf(sqrtf(vv) + 1e-12f);
+  if (live && c == 0) scores[(int64_t)g * R + r0 + m] = lin + logf(sqrtf(vv) + 1e-12f);
 }
 
 template <typename act_t>
