@@ -17,6 +17,10 @@
 //               move whole 128-byte row segments (coalesced).
 // The two accumulators let the epilogue of tile i overlap the main loop of
 // tile i+1.  Every mbarrier wait is bounded; a timeout sets the status word.
+//
+// Launches of more than 128 rows run the CTA-pair variant k_gemm_tc2 (2-SM
+// MMA on 256 x 256 tiles, described at its definition); k_gemm_tc serves
+// the small launches (and st_set_gemm_pairs(0)).
 #include <cudaTypedefs.h>
 
 #include "epilogue.cuh"
