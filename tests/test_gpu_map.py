@@ -3,7 +3,7 @@
 Every step's full-vocabulary logits are compared with the oracle's greedy
 decode over the same retained slots (the GPU's own retained index sets, so the
 comparison isolates the decode), normwise: float32 model <= 1e-4, BF16 model
-<= 2e-2.  Tokens must agree until the first step whose oracle logits have a
+<= 2e-2, E4M3 cache <= 5e-2.  Tokens must agree until the first step whose oracle logits have a
 near-tie at the top (gap below the tolerance times the largest logit): from
 there on the sequences may legitimately differ, and the comparison stops for
 that tuple.  Also: decoding n tokens gives the first n tokens of a longer
@@ -33,13 +33,13 @@ def _env(model_name, table_cfg, n_tuples, seed, max_pos):
     return dict(cfg=cfg, w=w, table=table, model=model, kv=kv, caches=caches, stretto=stretto, synth=synth)
 
 
-def _compare(e, r, P, n_gen, tol):
+def _compare(e, r, P, n_gen, tol, fp8=False):
     import torch
     from oracle import operator as O
     cfg, w, kv, model, st = e["cfg"], e["w"], e["kv"], e["model"], e["stretto"]
     off = e["table"]["offsets"]
     T = len(off) - 1
-    kv.retain(r)
+    kv.retain(r, st.ST_E4M3 if fp8 else None)
     R = int(off[-1])
     rank = kv.read(st.ST_VIEW_RANK, torch.int32, (cfg.layers, cfg.hkv, R)).cpu().numpy()
     op = model.operator(e["synth"].make_prompt(P, cfg.vocab, seed=91, r=r))
@@ -53,7 +53,7 @@ def _compare(e, r, P, n_gen, tol):
         c = e["caches"][t]
         n = O.n_keep(c.L, r)
         idx = [[rank[l, g, off[t]:off[t] + n] for g in range(cfg.hkv)] for l in range(cfg.layers)]
-        Kg, Vg, _ = O.retained_kv(c, r, idx=idx)
+        Kg, Vg, _ = O.retained_kv(c, r, idx=idx, kv_fp8=fp8)
         ref_t, ref_z = O.map_eval(cfg, w, c.L, Kg, Vg, op.op.prompt, n_gen)
         ok = True
         for s in range(n_gen):
@@ -81,6 +81,15 @@ def test_map_bf16_matches_oracle():
     e = _env("c2_bf16", "c2", 6, 93, 2200)
     full, T, steps = _compare(e, 1.0, P=16, n_gen=4, tol=2e-2)
     print(f"bf16: {full}/{T} tuples decoded identically, {steps} steps compared")
+    assert steps >= T
+
+
+def test_map_e4m3_matches_oracle():
+    """E4M3 retained cache: the oracle decodes over the same slots dequantised
+    per 64-slot block; logits within the E4M3 tolerance 5e-2."""
+    e = _env("c2_bf16", "c2", 6, 96, 2200)
+    full, T, steps = _compare(e, 0.5, P=16, n_gen=4, tol=5e-2, fp8=True)
+    print(f"e4m3: {full}/{T} tuples decoded identically, {steps} steps compared")
     assert steps >= T
 
 
