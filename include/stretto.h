@@ -261,6 +261,9 @@ int st_kv_view(const st_kv* kv, int32_t which, void** ptr, size_t* bytes);
 /* Copy min(bytes, size of the view) bytes of a view into caller DEVICE memory
  * dst_dev, enqueued on `stream`. */
 int st_kv_read(const st_kv* kv, int32_t which, void* dst_dev, size_t bytes, void* stream);
+/* Copy bytes [offset, offset + bytes) of a view into caller DEVICE memory.
+ * Errors: ST_EINVAL (range outside the view). */
+int st_kv_read_at(const st_kv* kv, int32_t which, size_t offset, void* dst_dev, size_t bytes, void* stream);
 
 /* ---- operators ---- */
 

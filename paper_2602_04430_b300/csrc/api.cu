@@ -171,16 +171,17 @@ namespace st {
 
 // One projection: dispatches to the tensor-core GEMM (bf16) or the CUDA-core GEMM (f32).
 int project(st_ctx* ctx, const void* A, const void* W, int M, int N, int K, EpiParams ep,
-            float* tmp, void* h_out, cudaStream_t s) {
+            float* tmp, void* h_out, cudaStream_t s, bool f16_ops) {
   const st_model_cfg& c = ctx->cfg;
   ep.M = M;
   ep.N = N;
+  ep.act_f16 = f16_ops ? 1 : 0;
   if (M <= 0) return ST_OK;
   const double flops = 2.0 * M * (double)N * K;
   const double bytes = ((double)M * K + (double)N * K) * ctx->esz;
   if (c.dtype == ST_BF16) {
     Launch L(ctx, s, ST_PROF_GEMM, flops, bytes);
-    int rc = gemm_tc((const bf16*)A, (const bf16*)W, M, N, K, ep, ctx->dstatus, s);
+    int rc = gemm_tc(A, W, M, N, K, ep, ctx->dstatus, s, f16_ops);
     if (rc != ST_OK) return fail(ctx, rc, "tcgen05 GEMM: unsupported shape or tensor-map encoding failed");
   } else if (ep.mode == EPI_SWIGLU) {
     EpiParams e2 = ep;
@@ -204,7 +205,7 @@ int project(st_ctx* ctx, const void* A, const void* W, int M, int N, int K, EpiP
 int rmsnorm(st_ctx* ctx, const float* x, int64_t rows, void* xn, float* inv, cudaStream_t s) {
   const st_model_cfg& c = ctx->cfg;
   Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-  if (c.dtype == ST_BF16) rmsnorm_rows<bf16>(x, rows, c.d, c.eps, (bf16*)xn, inv, s);
+  if (c.dtype == ST_BF16) rmsnorm_rows<__half>(x, rows, c.d, c.eps, (__half*)xn, inv, s);
   else rmsnorm_rows<float>(x, rows, c.d, c.eps, (float*)xn, inv, s);
   CKLAUNCH();
   return ST_OK;
@@ -311,6 +312,19 @@ extern "C" int st_create(const st_model_cfg* cfg, const void* const* weights, vo
     cudaMemcpy2DAsync((char*)L.wgu + 128 * d * e, 256 * d * e, w[5], 128 * d * e, 128 * d * e,
                       f / 128, cudaMemcpyDefault, s);
     copy(L.wd, w[6], d * f * e);
+  }
+  // BF16 model: the projection and LM-head weights are held as IEEE half (every
+  // bf16 value of a weight's magnitude converts exactly), the operand type of
+  // the tcgen05 GEMMs, whose activation operands are half too (3 more mantissa
+  // bits than bf16 where most of the rounding error arises).
+  if (c.dtype == ST_BF16) {
+    bf16_to_f16(ctx->w_lm, (size_t)c.vocab * d, s);
+    for (auto& L : ctx->layers) {
+      bf16_to_f16(L.wqkv, (qd + 2 * kd) * d, s);
+      bf16_to_f16(L.wo, d * qd, s);
+      bf16_to_f16(L.wgu, 2 * f * d, s);
+      bf16_to_f16(L.wd, d * f, s);
+    }
   }
   // RoPE table: cos / sin of pos * theta^(-2i/hd), computed in double on the host.
   const int half = c.hd / 2;
@@ -749,6 +763,18 @@ extern "C" int st_kv_read(const st_kv* kv, int32_t which, void* dst_dev, size_t 
   return ST_OK;
 }
 
+extern "C" int st_kv_read_at(const st_kv* kv, int32_t which, size_t offset, void* dst_dev, size_t bytes,
+                             void* stream) {
+  if (!kv || !dst_dev) return fail(nullptr, ST_EINVAL, "st_kv_read_at: bad argument");
+  void* p = nullptr;
+  size_t n = 0;
+  RC(st_kv_view(kv, which, &p, &n));
+  if (offset > n || bytes > n - offset) return fail(kv->ctx, ST_EINVAL, "st_kv_read_at: range outside the view");
+  const st_ctx* ctx = kv->ctx;
+  CK(cudaMemcpyAsync(dst_dev, (const char*)p + offset, bytes, cudaMemcpyDeviceToDevice, S(stream)));
+  return ST_OK;
+}
+
 extern "C" int st_gemm(st_ctx* ctx, const void* A_dev, const void* W_dev, int32_t M, int32_t N,
                        int32_t K, float* C_dev, void* stream) {
   ST_TRACE("st_gemm");
@@ -762,7 +788,7 @@ extern "C" int st_gemm(st_ctx* ctx, const void* A_dev, const void* W_dev, int32_
   ep.mode = EPI_STORE_F32;
   ep.out = C_dev;
   ep.ld = N;
-  return project(ctx, A_dev, W_dev, M, N, K, ep, nullptr, nullptr, S(stream));
+  return project(ctx, A_dev, W_dev, M, N, K, ep, nullptr, nullptr, S(stream), false);
 }
 
 // ================================================================== operators
@@ -1083,7 +1109,8 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
     {
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
       if (c.dtype == ST_BF16)
-        rmsnorm_rows<bf16>(w.x + (size_t)(P - 1) * c.d, np, c.d, c.eps, (bf16*)mp->xn, nullptr, s, (int64_t)P * c.d);
+        rmsnorm_rows<__half>(w.x + (size_t)(P - 1) * c.d, np, c.d, c.eps, (__half*)mp->xn, nullptr, s,
+                             (int64_t)P * c.d);
       else
         rmsnorm_rows<float>(w.x + (size_t)(P - 1) * c.d, np, c.d, c.eps, (float*)mp->xn, nullptr, s, (int64_t)P * c.d);
       CKLAUNCH();

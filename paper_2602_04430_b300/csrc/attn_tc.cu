@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     const int r = threadIdx.x;                 // query row == TMEM lane
     const float sl2 = a.scale * 1.4426950408889634f;
     const uint32_t lane_base = (uint32_t)((warp * 32) << 16);
-    bf16* og = reinterpret_cast<bf16*>(a.o);
+    __half* og = reinterpret_cast<__half*>(a.o);   // O feeds the half-operand O projection
     bool ok = true;
     uint32_t c = 0, qc = 0;
     // With two O buffers an item's O is read out after the next item's first
@@ -580,10 +580,10 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
 #pragma unroll
           for (int e = 0; e < 32; e += 8)
             dst[4 * h + e / 8] =
-                make_uint4(pack_bf16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
-                           pack_bf16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
-                           pack_bf16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
-                           pack_bf16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
+                make_uint4(pack_f16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
+                           pack_f16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
+                           pack_f16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
+                           pack_f16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
         }
       }
       return true;

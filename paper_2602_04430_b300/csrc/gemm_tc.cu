@@ -164,8 +164,11 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         *reinterpret_cast<uint4*>(st + sw64(lane, q)) =
-            make_uint4(pack2<false>(hv[8 * q], hv[8 * q + 1]), pack2<false>(hv[8 * q + 2], hv[8 * q + 3]),
-                       pack2<false>(hv[8 * q + 4], hv[8 * q + 5]), pack2<false>(hv[8 * q + 6], hv[8 * q + 7]));
+            ep.act_f16
+                ? make_uint4(pack2<true>(hv[8 * q], hv[8 * q + 1]), pack2<true>(hv[8 * q + 2], hv[8 * q + 3]),
+                             pack2<true>(hv[8 * q + 4], hv[8 * q + 5]), pack2<true>(hv[8 * q + 6], hv[8 * q + 7]))
+                : make_uint4(pack2<false>(hv[8 * q], hv[8 * q + 1]), pack2<false>(hv[8 * q + 2], hv[8 * q + 3]),
+                             pack2<false>(hv[8 * q + 4], hv[8 * q + 5]), pack2<false>(hv[8 * q + 6], hv[8 * q + 7]));
       __syncwarp();
       copy_out64(st, reinterpret_cast<char*>(ep.h) + ((int64_t)row0 * ep.ld + n0 / 2 + j) * 2,
                  ep.ld * 2, nrows, lane);
@@ -188,7 +191,7 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
   } else if (EPI == EPI_RESID) {
     // x[row*row_mul + row_add] += acc, 32 columns at a time through the
     // staging buffer (coalesced float32 read-modify-write, the next chunk's x
-    // loads in flight meanwhile); xb = bf16(x)
+    // loads in flight meanwhile); xb = x rounded to the operand type
     const int64_t xs = (int64_t)ep.row_mul * ep.ld * 4;   // byte stride of the warp's x rows
     char* xrow0 = reinterpret_cast<char*>(ep.x) + ((int64_t)row0 * ep.row_mul + ep.row_add) * ep.ld * 4;
     float ss = 0.f;
@@ -213,8 +216,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
         o.y += __uint_as_float(r[4 * j + 1]) * inv;
         o.z += __uint_as_float(r[4 * j + 2]) * inv;
         o.w += __uint_as_float(r[4 * j + 3]) * inv;
-        xw[2 * j] = pack2<false>(o.x, o.y);
-        xw[2 * j + 1] = pack2<false>(o.z, o.w);
+        xw[2 * j] = ep.act_f16 ? pack2<true>(o.x, o.y) : pack2<false>(o.x, o.y);
+        xw[2 * j + 1] = ep.act_f16 ? pack2<true>(o.z, o.w) : pack2<false>(o.z, o.w);
         ss += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
         *reinterpret_cast<float4*>(st + sw128(lane, j)) = o;
       }
@@ -258,7 +261,7 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
 template <int EPI>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              int M, int N, int K, EpiParams ep, int* status) {
+              int M, int N, int K, EpiParams ep, int* status, uint32_t idesc) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -318,7 +321,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -406,7 +408,7 @@ struct PairBars {
 template <int EPI>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               int M, int N, int K, EpiParams ep, int* status) {
+               int M, int N, int K, EpiParams ep, int* status, uint32_t idesc) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -474,7 +476,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {
-      constexpr uint32_t idesc = ptx::idesc_bf16_f32(P_BM, BN);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -563,14 +564,15 @@ int num_sms() {
 }
 
 bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_outer,
-              uint64_t row_stride = 0) {
+              uint64_t row_stride, bool f16) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {(row_stride ? row_stride : inner) * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, box_outer};
   cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+  return fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void*>(ptr), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -591,7 +593,7 @@ bool gemm_tc_supported(int M, int N, int K) {
 // add a second wave).
 template <int EPI>
 cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const EpiParams& ep,
-                        int* status, cudaStream_t s) {
+                        int* status, cudaStream_t s, uint32_t idesc) {
   static int max_clusters = 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -617,31 +619,33 @@ cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, int M, int
   }
   const int tiles = ((M + P_BM - 1) / P_BM) * (N / BN);
   cfg.gridDim = dim3(2 * (tiles < max_clusters ? tiles : max_clusters));
-  return cudaLaunchKernelEx(&cfg, k_gemm_tc2<EPI>, ma, mb, M, N, K, ep, status);
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc2<EPI>, ma, mb, M, N, K, ep, status, idesc);
 }
 
-int gemm_tc(const bf16* A, const bf16* W, int M, int N, int K, const EpiParams& ep, int* status,
-            cudaStream_t s) {
+int gemm_tc(const void* A, const void* W, int M, int N, int K, const EpiParams& ep, int* status,
+            cudaStream_t s, bool f16) {
   if (M <= 0) return ST_OK;
   if (!gemm_tc_supported(M, N, K)) return ST_EUNSUPPORTED;
   if (M > BM && gemm_pair_enabled()) {
     // 2-SM MMA: W and A tiles of 128 rows per CTA
+    const uint32_t idesc = f16 ? ptx::idesc_f16_f32(P_BM, BN) : ptx::idesc_bf16_f32(P_BM, BN);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, P_HALF, (uint64_t)ep.a_ld) ||
-        !make_map(&mb, W, (uint64_t)K, (uint64_t)N, P_HALF))
+    if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, P_HALF, (uint64_t)ep.a_ld, f16) ||
+        !make_map(&mb, W, (uint64_t)K, (uint64_t)N, P_HALF, 0, f16))
       return ST_ECUDA;
     cudaError_t e;
     switch (ep.mode) {
-      case EPI_QKV: e = launch_pair<EPI_QKV>(ma, mb, M, N, K, ep, status, s); break;
-      case EPI_RESID: e = launch_pair<EPI_RESID>(ma, mb, M, N, K, ep, status, s); break;
-      case EPI_SWIGLU: e = launch_pair<EPI_SWIGLU>(ma, mb, M, N, K, ep, status, s); break;
-      default: e = launch_pair<EPI_STORE_F32>(ma, mb, M, N, K, ep, status, s); break;
+      case EPI_QKV: e = launch_pair<EPI_QKV>(ma, mb, M, N, K, ep, status, s, idesc); break;
+      case EPI_RESID: e = launch_pair<EPI_RESID>(ma, mb, M, N, K, ep, status, s, idesc); break;
+      case EPI_SWIGLU: e = launch_pair<EPI_SWIGLU>(ma, mb, M, N, K, ep, status, s, idesc); break;
+      default: e = launch_pair<EPI_STORE_F32>(ma, mb, M, N, K, ep, status, s, idesc); break;
     }
     return e == cudaSuccess ? ST_OK : ST_ECUDA;
   }
+  const uint32_t idesc = f16 ? ptx::idesc_f16_f32(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, BM, (uint64_t)ep.a_ld) ||
-      !make_map(&mb, W, (uint64_t)K, (uint64_t)N, BN))
+  if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, BM, (uint64_t)ep.a_ld, f16) ||
+      !make_map(&mb, W, (uint64_t)K, (uint64_t)N, BN, 0, f16))
     return ST_ECUDA;
   static bool attr = false;
   if (!attr) {
@@ -654,10 +658,10 @@ int gemm_tc(const bf16* A, const bf16* W, int M, int N, int K, const EpiParams& 
   const int tiles = ((M + BM - 1) / BM) * (N / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
   switch (ep.mode) {
-    case EPI_QKV: k_gemm_tc<EPI_QKV><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
-    case EPI_RESID: k_gemm_tc<EPI_RESID><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
-    case EPI_SWIGLU: k_gemm_tc<EPI_SWIGLU><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
-    default: k_gemm_tc<EPI_STORE_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status); break;
+    case EPI_QKV: k_gemm_tc<EPI_QKV><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status, idesc); break;
+    case EPI_RESID: k_gemm_tc<EPI_RESID><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status, idesc); break;
+    case EPI_SWIGLU: k_gemm_tc<EPI_SWIGLU><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status, idesc); break;
+    default: k_gemm_tc<EPI_STORE_F32><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, M, N, K, ep, status, idesc); break;
   }
   return ST_OK;
 }

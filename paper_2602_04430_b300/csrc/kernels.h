@@ -13,6 +13,7 @@ struct EpiParams {
   int M = 0, N = 0;
   int64_t a_ld = 0;               // row stride of A in elements (0: K)
   int qkv_f16 = 0;                // EPI_QKV: store q / k / v as IEEE half instead of the act type
+  int act_f16 = 0;                // EPI_RESID xb and EPI_SWIGLU h as IEEE half (the next GEMM's operand type)
   // Fused RMSNorm (tensor-core path).  EPI_RESID also writes xb[row * N + col] =
   // bf16(new stream value) and ssq_out[row * (N/128) + col/128] = the sum of the
   // squares of its 128-column slice.  EPI_QKV / EPI_SWIGLU multiply every
@@ -131,6 +132,8 @@ void decode_plan(int n, int S, int P, int t, int n_gen, const int32_t* len, cons
                  cudaStream_t s);
 void argmax_rows(const float* logits, int n, int V, int t, int n_gen, int32_t* tokens, float* logits_out,
                  int* status, cudaStream_t s);
+// In-place conversion of n bfloat16 values to IEEE half (round to nearest).
+void bf16_to_f16(void* p, size_t n, cudaStream_t s);
 // Final RMSNorm of each pair's last prompt row, its operator's label logits and decision.
 void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, const int32_t* pP,
                 const int32_t* pop, const int32_t* pj, int d, float eps, const void* w_lm, int dtype,
@@ -147,8 +150,10 @@ bool gemm_tc_supported(int M, int N, int K);
 // Process-wide choice of the tcgen05 GEMM for M > 128: CTA pairs (2-SM MMA,
 // the default) or single CTAs.
 void set_gemm_pairs(bool on);
-int gemm_tc(const bf16* A, const bf16* W, int M, int N, int K, const EpiParams& ep, int* status,
-            cudaStream_t s);
+// f16: A and W are IEEE half (the model path, whose BF16 weights are held
+// exactly as f16); otherwise bfloat16 (st_gemm).
+int gemm_tc(const void* A, const void* W, int M, int N, int K, const EpiParams& ep, int* status,
+            cudaStream_t s, bool f16);
 
 // ---- attention ----
 struct AttnParams {
@@ -202,8 +207,10 @@ int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int*
                     cudaStream_t s);
 
 // ---- host sequencing helpers (api.cu): one projection / RMSNorm / attention step
+// f16_ops: the BF16 model's operands (IEEE half activations and weights, the
+// residual / SwiGLU epilogues writing half); false: caller-given bfloat16 (st_gemm).
 int project(st_ctx* ctx, const void* A, const void* W, int M, int N, int K, EpiParams ep, float* tmp,
-            void* h_out, cudaStream_t s);
+            void* h_out, cudaStream_t s, bool f16_ops = true);
 int rmsnorm(st_ctx* ctx, const float* x, int64_t rows, void* xn, float* inv, cudaStream_t s);
 int attention(st_ctx* ctx, const AttnParams& a, const int32_t* items, int n_items, cudaStream_t s);
 // The projection reads bf16(x) and scales its rows by 1/rms from `ssq`.

@@ -242,6 +242,13 @@ template void embed_rows<bf16>(const int32_t*, int64_t, const bf16*, int, int, f
 
 // ------------------------------------------------------------------ RMSNorm
 __device__ __forceinline__ void store4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void store4(__half* p, float4 v) {
+  __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t*>(&a);
+  u.y = *reinterpret_cast<uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
+}
 __device__ __forceinline__ void store4(bf16* p, float4 v) {
   __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
   uint2 u;
@@ -284,6 +291,8 @@ void rmsnorm_rows(const float* x, int64_t rows, int d, float eps, act_t* xn, flo
 template void rmsnorm_rows<float>(const float*, int64_t, int, float, float*, float*, cudaStream_t,
                                   int64_t);
 template void rmsnorm_rows<bf16>(const float*, int64_t, int, float, bf16*, float*, cudaStream_t,
+                                 int64_t);
+template void rmsnorm_rows<__half>(const float*, int64_t, int, float, __half*, float*, cudaStream_t,
                                  int64_t);
 
 // ------------------------------------------------------------------ EA-lite statistics
@@ -561,10 +570,27 @@ void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, co
                 const int32_t* pop, const int32_t* pj, int d, float eps, const void* w_lm, int dtype,
                 cudaStream_t s) {
   if (np <= 0) return;
-  if (dtype == ST_BF16)
-    k_label_head<bf16><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const bf16*)w_lm);
+  if (dtype == ST_BF16)   // the BF16 model holds its LM head as IEEE half
+    k_label_head<__half><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const __half*)w_lm);
   else
     k_label_head<float><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const float*)w_lm);
+}
+
+// ------------------------------------------------------------------ weight conversion
+__global__ void k_bf16_to_f16(uint32_t* p, size_t n2) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t u = p[i];
+    const float lo = __uint_as_float(u << 16), hi = __uint_as_float(u & 0xFFFF0000u);
+    __half2 h = __floats2half2_rn(lo, hi);
+    p[i] = *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+void bf16_to_f16(void* p, size_t n, cudaStream_t s) {
+  // n is even for every weight matrix (dimensions multiples of 64)
+  const size_t n2 = n / 2;
+  if (n2 == 0) return;
+  k_bf16_to_f16<<<(unsigned)std::min<size_t>((n2 + 255) / 256, 4096), 256, 0, s>>>((uint32_t*)p, n2);
 }
 
 // ------------------------------------------------------------------ map operator (decode)

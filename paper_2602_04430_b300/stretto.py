@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
         "st_set_scoring": (i32, [VP, i32, i32]),
         "st_set_gemm_pairs": (i32, [i32]),
         "st_kv_profile_bytes": (i32, [VP, ctypes.POINTER(ctypes.c_size_t)]),
+        "st_kv_read_at": (i32, [VP, i32, ctypes.c_size_t, VP, ctypes.c_size_t, VP]),
         "st_kv_export": (i32, [VP, VP, VP, ctypes.c_size_t, VP]),
         "st_kv_import": (i32, [VP, VP, VP, ctypes.c_size_t, VP]),
         "st_kv_score_query": (i32, [VP, VP, VP, VP]),
@@ -313,6 +314,15 @@ class KVCache:
         out = torch.empty(shape, dtype=dtype, device="cuda")
         nbytes = out.numel() * out.element_size()
         self.model.check(self.L.st_kv_read(self.h, which, _ptr(out), nbytes, _stream(stream)))
+        return out
+
+    def read_at(self, which: int, dtype, shape, offset_elems: int, stream=None):
+        """Copy a contiguous piece of a view, starting at element ``offset_elems``."""
+        import torch
+        out = torch.empty(shape, dtype=dtype, device="cuda")
+        es = out.element_size()
+        self.model.check(self.L.st_kv_read_at(self.h, which, int(offset_elems) * es, _ptr(out),
+                                              out.numel() * es, _stream(stream)))
         return out
 
 
