@@ -110,6 +110,11 @@ typedef struct {
  *   wd [d][ffn]; then w_lm [vocab][d].  They are copied (the caller may free
  *   them after the stream has passed this call's copies; the call synchronises
  *   `stream` before returning).
+ * ST_BF16 contexts keep the projection and LM-head weights as IEEE half (an
+ *   exact conversion of the given bf16 values) and run the projections on half
+ *   operands (normalised inputs, attention and SwiGLU outputs stored as half,
+ *   f32 accumulation); Q, K, V, attention probabilities and the KV cache are
+ *   bf16, the residual stream float32.
  * Errors: ST_EINVAL on an unsupported shape, ST_ENOMEM, ST_ECUDA. */
 int st_create(const st_model_cfg* cfg, const void* const* weights, void* stream, st_ctx** out);
 void st_destroy(st_ctx* ctx);
