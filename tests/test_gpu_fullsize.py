@@ -1,5 +1,6 @@
 """Parity at the configurations' full sizes, in the benchmark's launch
-configuration, on outputs the float64 oracle can compute one by one.
+configuration, on outputs the float64 oracle can compute one by one (config 4,
+batching, is described at its test).
 
 Config 2 (the benchmark workload itself: 4096 tuples, lognormal lengths
 64..2048, the benchmark's weights, table, operator and r = 0.5, one cache and
@@ -173,3 +174,62 @@ def test_config3_precision_sharded():
         agree = float((labels[(r, stretto.ST_BF16)] == labels[(r, stretto.ST_E4M3)]).mean())
         print(f"config 3, r={r}: E4M3 vs BF16 decision agreement {agree:.4f} over {T} tuples")
         assert agree >= 0.98
+
+
+def test_config4_batching_sharded():
+    """Config 4 (batching: the 16-layer model, 32768 tuples with Zipf(1.1)
+    lengths over 32..8192, three concurrent operators -- filter P16 r 0.1,
+    8-way classify P48 r 0.3, filter P64 r 1.0 -- reading one profile retained
+    at r = 1): the full table (about 1.3 TB of cache) in shards of 2048 tuples.
+    Every shard's batched pass equals the three separate evaluations bit for
+    bit; on the first shard the pass replayed as a CUDA graph equals the eager
+    pass, and the two shortest tuples match the oracle for every operator
+    (BF16 <= 2e-2)."""
+    import torch
+    from paper_2602_04430_b300 import build, stretto, synth
+    build.build()
+    cfg = synth.MODELS["c3_bf16"]
+    table = synth.make_table(synth.TABLES["c4"], cfg.vocab, seed=3400)
+    w = synth.make_weights(cfg, seed=3401)
+    model = stretto.Model(cfg, w, max_pos=8192 + 64 + 8)
+    ops_np = [synth.make_prompt(16, cfg.vocab, seed=3402, label_ids=(1, 0), r=0.1),
+              synth.make_prompt(48, cfg.vocab, seed=3403, label_ids=tuple(range(2, 10)), r=0.3, kind="classify"),
+              synth.make_prompt(64, cfg.vocab, seed=3404, label_ids=(3, 4), r=1.0)]
+    ops = [model.operator(o) for o in ops_np]
+    off, tok, lengths = table["offsets"], table["tokens"], table["lengths"]
+    T = len(lengths)
+    assert T == 32768
+    shard = 2048
+    check = [int(x) for x in np.argsort(lengths[:shard], kind="stable")[:2]]
+    for s0 in range(0, T, shard):
+        s1 = min(T, s0 + shard)
+        soff = off[s0:s1 + 1] - off[s0]
+        kv = model.kv_alloc(soff)
+        kv.build(torch.from_numpy(np.ascontiguousarray(tok[off[s0]:off[s1]])).cuda())
+        kv.retain(1.0)
+        ids = [torch.arange(s1 - s0, dtype=torch.int32, device="cuda") for _ in ops]
+        sep = [op.eval(kv, i) for op, i in zip(ops, ids)]
+        lg_b, lb_b = stretto.eval_multi(model, kv, ops, ids)
+        torch.cuda.synchronize()
+        model.status()
+        for (lg, lb), g, b in zip(sep, lg_b, lb_b):
+            assert torch.equal(lg, g) and torch.equal(lb, b)
+        if s0 == 0:
+            graph = stretto.Graph(model, kv, ops, ids)
+            graph.launch()
+            torch.cuda.synchronize()
+            model.status()
+            for (lg, lb), g, b in zip(sep, graph.logits, graph.labels):
+                assert torch.equal(lg, g) and torch.equal(lb, b)
+            graph.close()
+            R = int(soff[-1])
+            rank = kv.read(stretto.ST_VIEW_RANK, torch.int32, (cfg.layers, cfg.hkv, R)).cpu().numpy()
+            for t in check:
+                a, b = int(soff[t]), int(soff[t + 1])
+                rows = [[rank[l, g, a:b] for g in range(cfg.hkv)] for l in range(cfg.layers)]
+                for (lg, _), o in zip(sep, ops_np):
+                    z = _oracle_logits(cfg, w, tok[off[t]:off[t + 1]], rows, o.r, o.prompt, o.label_ids, False)
+                    err = normwise_rel(lg[t].cpu().numpy(), z)
+                    print(f"config 4, tuple {t} (L={b - a}), P={len(o.prompt)} r={o.r}: normwise error {err:.3e}")
+                    assert err <= 2e-2, (t, o.r, err)
+        kv.close()
