@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--batched-tuples", type=int, default=2048)
     ap.add_argument("--no-map", action="store_true", help="skip the map-operator (greedy decode) arm")
     ap.add_argument("--no-ablation", action="store_true", help="skip the retention-scoring ablation arm")
+    ap.add_argument("--config5", action="store_true",
+                    help="also run the learned-proxy configuration at full size (16-layer model, 65536 "
+                         "training and 65536 held-out tuples; several minutes)")
     ap.add_argument("--map-tuples", type=int, default=1024)
     ap.add_argument("--map-gen", type=int, default=16)
     return ap.parse_args()
@@ -502,6 +505,123 @@ def scoring_ablation_arm(args, model, kv, cfg, T, tok, op, stretto, synth, torch
     return out
 
 
+def proxy_config5_arm(args, stretto, synth, torch):
+    """The learned-proxy configuration at full size: the 16-layer d 2048 decoder,
+    65536 training tuples and 65536 held-out tuples with the precision
+    configuration's lengths (lognormal, median 1024, 128..4096), the proxy MLP
+    2048 -> 512 -> 128 -> 2 trained on the pooled states with labels from the
+    full FP8-KV operator (threshold: the training margins' median), and the
+    confidence threshold swept so that 5-50 % of the held-out tuples fall back
+    to the full FP8 operator.  The caches do not fit the GPU at once (about
+    2.5 TB per table), so every table runs in shards of 2048 tuples; per shard
+    the plain BF16 operator and each cascade (proxy + compaction + FP8 operator
+    on the unsure tuples + merge) are timed with CUDA events, KV resident."""
+    cfg = synth.MODELS["c3_bf16"]
+    r, shard, n = 0.25, 2048, 65536
+    model = stretto.Model(cfg, synth.make_weights_device(cfg, seed=5151), max_pos=4096 + 64)
+    base = synth.make_prompt(32, cfg.vocab, seed=5152, label_ids=(1, 0), r=r)
+    op_m = model.operator(base)
+    stream = torch.cuda.current_stream()
+
+    def shards(seed):
+        tb = synth.make_table(synth.TABLES["c3"], cfg.vocab, seed=seed, n_tuples=n)
+        off, tok = tb["offsets"], tb["tokens"]
+        for s0 in range(0, n, shard):
+            s1 = min(n, s0 + shard)
+            kv = model.kv_alloc(off[s0:s1 + 1] - off[s0])
+            kv.build(torch.from_numpy(np.ascontiguousarray(tok[off[s0]:off[s1]])).cuda())
+            yield s0, s1, kv
+
+    t0 = time.perf_counter()
+    xs, ms = [], []
+    for s0, s1, kv in shards(5200):
+        ids = torch.arange(s1 - s0, dtype=torch.int32, device="cuda")
+        kv.retain(r, stretto.ST_E4M3)
+        lg, _ = op_m.eval(kv, ids)
+        xs.append(kv.read(stretto.ST_VIEW_POOLED, torch.float32, (s1 - s0, cfg.d)))
+        ms.append(lg[:, 0] - lg[:, 1])
+        kv.close()
+    x_tr, m_tr = torch.cat(xs), torch.cat(ms)
+    theta = float(m_tr.median().item())
+    y_tr = (m_tr > theta).to(torch.int32)
+    px = stretto.Proxy(model, synth.make_proxy_weights(cfg.d, 512, 128, seed=5153))
+    batches = synth.minibatches(n, 512, args.proxy_epochs, seed=5154)
+    bt = torch.from_numpy(np.stack(batches)).cuda()
+    for i in range(len(batches)):
+        px.train_step(x_tr, y_tr, bt[i], lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del x_tr
+    opf = model.operator(synth.Operator(prompt=base.prompt, label_ids=base.label_ids, r=r,
+                                        theta_pos=theta, theta_neg=theta))
+    fracs = (0.05, 0.1, 0.2, 0.3, 0.4, 0.5)
+
+    def timed(fn):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1)
+
+    ms_plain, ms_casc = 0.0, {f: 0.0 for f in fracs}
+    plain_all, fp8_all, final_all = [], [], {f: [] for f in fracs}
+    plab_all = []
+    for s0, s1, kv in shards(5300):
+        m = s1 - s0
+        ids = torch.arange(m, dtype=torch.int32, device="cuda")
+        x = kv.read(stretto.ST_VIEW_POOLED, torch.float32, (m, cfg.d))
+        lg = torch.empty((m, 2), dtype=torch.float32, device="cuda")
+        lab_p = torch.empty(m, dtype=torch.int32, device="cuda")
+        kv.retain(r, stretto.ST_BF16)
+        opf.eval(kv, ids, lg, lab_p)
+        ms_plain += timed(lambda: opf.eval(kv, ids, lg, lab_p))
+        plain_all.append(lab_p.cpu().numpy())
+        kv.retain(r, stretto.ST_E4M3)
+        lab_f = torch.empty(m, dtype=torch.int32, device="cuda")
+        opf.eval(kv, ids, lg, lab_f)
+        fp8_all.append(lab_f.cpu().numpy())
+        conf, plab = px.eval(x)
+        plab_all.append(plab.cpu().numpy())
+        pos = torch.empty(m, dtype=torch.int32, device="cuda")
+        tid = torch.empty(m, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        cnt2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+        full = torch.empty(m, dtype=torch.int32, device="cuda")
+        out = torch.empty(m, dtype=torch.int32, device="cuda")
+        ch = conf.cpu().numpy()
+        for f in fracs:
+            tau = float(np.quantile(ch, f))
+
+            def cascade():
+                px.eval(x, conf=conf, label=plab)
+                stretto.cascade_compact(model, conf, tau, out=pos, count=cnt)
+                stretto.cascade_compact(model, conf, tau, ids=ids, out=tid, count=cnt2)
+                k = int(cnt.item())
+                if k:
+                    opf.eval(kv, tid[:k], lg[:k], full[:k])
+                stretto.cascade_merge(model, plab, pos, cnt, full, out=out)
+
+            cascade()
+            ms_casc[f] += timed(cascade)
+            final_all[f].append(out.cpu().numpy())
+        kv.close()
+    plain = np.concatenate(plain_all)
+    sweep = []
+    for f in fracs:
+        fin = np.concatenate(final_all[f])
+        sweep.append({"fallback_target": f, "agreement_with_plain_bf16": float((fin == plain).mean()),
+                      "tuples_per_s": n / (ms_casc[f] / 1000.0),
+                      "gain_vs_plain_bf16": ms_plain / ms_casc[f]})
+    return {"workload": "16L d2048 32q/8kv x64 F5632 random-init; 65536 training + 65536 held-out tuples, "
+                        "lognormal(1024, 0.6) lengths 128..4096, 32-token filter, r = 0.25, shards of 2048",
+            "train_tuples": n, "train_steps": len(batches), "train_and_label_seconds": train_s,
+            "theta": theta, "plain_bf16_tuples_per_s": n / (ms_plain / 1000.0),
+            "fp8_only_agreement": float((np.concatenate(fp8_all) == plain).mean()),
+            "proxy_holdout_accuracy": float((np.concatenate(plab_all) == plain).mean()),
+            "sweep": sweep}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -626,6 +746,9 @@ def main():
     ablation = None
     if not args.no_ablation and rank == 0:
         ablation = scoring_ablation_arm(args, model, kv, cfg, T, tok, op, stretto, synth, torch)
+    config5 = None
+    if args.config5 and rank == 0:
+        config5 = proxy_config5_arm(args, stretto, synth, torch)
     proxy = None
     if not args.no_proxy and rank == 0:
         proxy = proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch)
@@ -664,7 +787,7 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                 "per_family_ms": {k: v["ms"] for k, v in prof.items()},
                 "op_eval": out, "map": mapr, "scoring_ablation": ablation, "proxy_fp8": proxy,
-                "batched_ops": batched}
+                "proxy_config5": config5, "batched_ops": batched}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
