@@ -788,6 +788,18 @@ def main():
                 "per_family_ms": {k: v["ms"] for k, v in prof.items()},
                 "op_eval": out, "map": mapr, "scoring_ablation": ablation, "proxy_fp8": proxy,
                 "proxy_config5": config5, "batched_ops": batched}
+        # the metric's two clauses in one place: the proxy + FP8 cascade against the
+        # plain BF16 operator at the validated >= 99 % agreement, and the operator
+        # attention's fraction of the HBM roofline at the benchmark's r
+        parts = {}
+        if proxy is not None:
+            parts["proxy_fp8_gain_vs_plain_bf16"] = proxy["gain_vs_plain_bf16"]
+            parts["proxy_fp8_label_agreement"] = proxy["at_validation_tau"]["agreement"]
+            parts["proxy_fp8_tuples_per_s"] = proxy["at_validation_tau"]["tuples_per_s"]
+        if str(args.r) in out:
+            parts["attention_hbm_frac"] = out[str(args.r)]["attention_hbm_frac"]
+            parts["attention_hbm_frac_unit"] = f"compulsory bytes / time over the measured HBM peak, r = {args.r}"
+        line["metric_parts"] = parts
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
