@@ -86,6 +86,8 @@ def config_dict(args, cfg, table, op):
                     "Zipf(1.1) ids; 32-token prompt",
         "tuples": int(len(L)), "doc_tokens": int(L.sum()), "mean_len": float(L.mean()),
         "prompt_len": len(op.prompt), "r": args.r, "kv_dtype": args.kv_dtype,
+        "operands": "BF16 weights (held exactly as f16 for the tensor cores), f16 GEMM activations, "
+                    "BF16 Q/K/V, probabilities and KV cache, f32 accumulation, softmax and residual",
         "l2": "inputs larger than L2 (full KV cache %.1f GB per step)" % (
             8 * 4 * 64 * 2 * 2 * float(L.sum()) / 1e9),
     }
