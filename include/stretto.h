@@ -132,7 +132,9 @@ int st_reserve(st_ctx* ctx, int64_t build_rows, int64_t eval_rows);
  * offsets_host[i] .. offsets_host[i+1]-1 (monotone, offsets_host[0] == 0,
  * every length in 1 .. max_pos-1).  Sizes the full cache (dtype of the model)
  * and the retained cache for any r <= 1 (either dtype).
- * Errors: ST_EINVAL (bad offsets), ST_ENOMEM. */
+ * Errors: ST_EINVAL (bad offsets: T < 1, offsets[0] != 0, an empty document
+ * or one longer than max_pos - 1), ST_EUNSUPPORTED (a document longer than
+ * 16384 tokens), ST_ENOMEM. */
 int st_kv_alloc(st_ctx* ctx, const int64_t* offsets_host, int32_t T, st_kv** out);
 void st_kv_free(st_kv* kv);
 

@@ -198,3 +198,16 @@ def test_out_of_range_token_is_reported_not_read(run):
     torch.cuda.synchronize()
     model.status()
     assert torch.isfinite(lg).all()
+
+
+def test_kv_alloc_validates_offsets(run):
+    """Empty documents, documents past max_pos - 1, a nonzero first offset and
+    an empty table are refused on the host, before any device work."""
+    import numpy as np
+    from paper_2602_04430_b300 import stretto
+    model = run["model"]                       # max_pos 512
+    for off in ([0, 3, 3, 7], [0, 600], [1, 5], [0]):
+        with pytest.raises(stretto.StrettoError) as ei:
+            model.kv_alloc(np.asarray(off, dtype=np.int64))
+        assert ei.value.code == stretto.ST_EINVAL, off
+    model.kv_alloc(np.asarray([0, 1, 511], dtype=np.int64)).close()
