@@ -382,9 +382,9 @@ int st_cascade_run(int32_t n_stages, const st_stage* stages, const int32_t* tupl
  *
  * eval_rows: prompt rows per pass through the layers (the evaluation is cut
  * into chunks of at most this many rows; 0 = library default 262144);
- * attn_nb: BF16-KV attention layout, 1 = two CTAs per SM with single S / P /
- * O buffers (default), 2 = one CTA per SM with double buffers (E4M3 KV always
- * uses 2); longest_first: attention work items ordered by retained document
+ * attn_nb: tensor-core attention layout, 1 = two CTAs per SM with single S /
+ * P / O buffers (default; E4M3 KV then runs 64-key tiles), 2 = one CTA per SM
+ * with double buffers; longest_first: attention work items ordered by retained document
  * length, longest first (1, default) or in arrival order (0).  ms: measured
  * time of one evaluation (autotuner output).
  * st_autotune_eval times the batched evaluation of its arguments (which it

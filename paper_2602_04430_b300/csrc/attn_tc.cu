@@ -17,10 +17,11 @@
 //               the end of the item.
 //   loads       one thread decodes each work item (into shared memory for the
 //               other roles) and issues TMA for its Q (3-D box, two buffers)
-//               and its K/V tiles (three stages), in 64-row boxes, so that key
+//               and its K/V tiles (2-5 stages), in 64-row boxes, so that key
 //               rows no query of the item can see are not read.
-//   E4M3 KV     raw code tiles land in two raw stages; two warps widen them
-//               exactly to f16 into the swizzled K/V stage; Q and the prompt's
+//   E4M3 KV     raw code tiles land in raw stages; one warp widens the K codes
+//               and one the V codes exactly to f16 into the swizzled K/V stage,
+//               each as soon as the stage's half is free; Q and the prompt's
 //               K/V arrive in f16, both products run as f16 MMAs, the K block
 //               scale multiplies the f32 scores and the V block scale P.
 //
@@ -36,41 +37,44 @@ namespace st {
 namespace {
 
 constexpr int HD = 64;
-constexpr int TK = 128;          // keys per tile
 constexpr int BOX = 64;          // key rows per TMA box
 constexpr int ROWS = 128;        // query rows per work item
 // Two layouts, by the number NB of S, P and O buffers:
 //   NB = 1: two CTAs per SM, each with one S, P and O buffer in 256 TMEM
-//           columns and two K/V stages, so every SM sub-partition runs two
-//           independent softmax warps (BF16 KV default);
-//   NB = 2: one CTA per SM with double buffers in 512 TMEM columns and 5 K/V
-//           stages (4 with E4M3 KV, whose two raw code stages leave no room for
-//           a second CTA; E4M3 always uses it).
+//           columns, so every SM sub-partition runs two independent softmax
+//           warps (the default; E4M3 KV then runs 64-key tiles, whose register,
+//           shared-memory and TMEM budget fits two CTAs per SM);
+//   NB = 2: one CTA per SM with double buffers in 512 TMEM columns.
+// K/V stages: 2 (NB = 1) or 5 (NB = 2; 4 with E4M3 KV), and with E4M3 KV two
+// raw code stages (with 64-key tiles, 3 K/V or 4 raw stages measured no faster).
 constexpr int ctas_per_sm(int nb) { return nb == 1 ? 2 : 1; }
-constexpr int NKV_MAX = 5;
+constexpr int NKV_MAX = 5, NRAW_MAX = 2;
 constexpr int nkv(bool fp8, int nb) { return nb == 1 ? 2 : (fp8 ? 4 : 5); }
+constexpr int nraw(bool fp8, int nb) { return fp8 ? 2 : 0; }
 // warps 0-3 softmax, 4 item decode + Q and K/V loads, 5 MMA issue,
-// (E4M3 KV) 6-7 widen codes to f16
+// (E4M3 KV) 6 widens the K codes to f16, 7 the V codes
 constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
 constexpr int OFF_Q = 0;                           // 2 x 16 KB
 constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // nkv x 16 KB
-constexpr int off_v(bool fp8, int nb) { return OFF_K + nkv(fp8, nb) * TK * 128; }       // nkv x 16 KB
-constexpr int off_raw(bool fp8, int nb) { return off_v(fp8, nb) + nkv(fp8, nb) * TK * 128; }  // (E4M3) 2 x 16 KB
-constexpr int RAW_BYTES = 2 * TK * HD;             // K + V codes of one tile
-constexpr int off_bar(bool fp8, int nb) { return off_raw(fp8, nb) + (fp8 ? 2 * RAW_BYTES : 0); }
-constexpr int off_work(bool fp8, int nb) { return off_bar(fp8, nb) + 512; }   // 2 decoded work items
-constexpr size_t smem_bytes(bool fp8, int nb) { return (size_t)off_work(fp8, nb) + 256 + 1024; }
-// TMEM columns: S buffers [0, 128 nb), O buffers [128 nb, 192 nb), P buffers [192 nb, 256 nb)
+constexpr int off_v(bool fp8, int nb, int tk) { return OFF_K + nkv(fp8, nb) * tk * 128; }   // nkv x tk x 128 B
+constexpr int off_raw(bool fp8, int nb, int tk) { return off_v(fp8, nb, tk) + nkv(fp8, nb) * tk * 128; }
+constexpr int raw_bytes(int tk) { return 2 * tk * HD; }   // K + V codes of one tile
+constexpr int off_bar(bool fp8, int nb, int tk) { return off_raw(fp8, nb, tk) + nraw(fp8, nb) * raw_bytes(tk); }
+constexpr int off_work(bool fp8, int nb, int tk) { return off_bar(fp8, nb, tk) + 512; }   // 2 decoded work items
+constexpr size_t smem_bytes(bool fp8, int nb, int tk) { return (size_t)off_work(fp8, nb, tk) + 256 + 1024; }
+// TMEM columns: S buffers [0, tk nb), O buffers [tk nb, (tk + 64) nb), P buffers
+// [(tk + 64) nb, (1.5 tk + 64) nb) -- within 256 nb for tk <= 128
 constexpr uint32_t tmem_cols(int nb) { return 256 * nb; }
-constexpr uint32_t col_o(int nb) { return TK * nb; }
-constexpr uint32_t col_p(int nb) { return (TK + HD) * nb; }
+constexpr uint32_t col_o(int nb, int tk) { return tk * nb; }
+constexpr uint32_t col_p(int nb, int tk) { return (tk + HD) * nb; }
 
 struct Bars {
   // K and V halves of a stage fill and free separately: K after the tile's
   // S = Q K^T, V after its P.V
   uint64_t k_full[NKV_MAX], v_full[NKV_MAX], k_empty[NKV_MAX], v_empty[NKV_MAX], s_full[2], s_free[2], p_full[2], pv_done[2], o_free[2];
   uint64_t q_full[2], q_empty[2];
-  uint64_t kvc_full[NKV_MAX], raw_full[2], raw_empty[2];   // E4M3: widened stages, raw code stages
+  // E4M3: K / V halves of a stage widened; raw code stages loaded / free
+  uint64_t kc_full[NKV_MAX], vc_full[NKV_MAX], raw_full[NRAW_MAX], raw_empty[NRAW_MAX];
   uint32_t tmem;
 };
 static_assert(sizeof(Bars) <= 512, "barrier block");
@@ -154,7 +158,7 @@ struct TileInfo {
 };
 
 // One work item: 128 query rows of one kv head of one tuple.
-template <int MODE>
+template <int MODE, int TK>
 struct Work {
   int g, G, rows, row_base, n_tiles, n_doc_tiles;
   int i, n_doc, P;          // eval
@@ -222,7 +226,7 @@ struct Work {
 // MMA, softmax (and E4M3 widening) roles each walk the same sequence,
 // connected by mbarrier rings (decoded item + Q: 2 slots, K/V: 3 stages, S, P
 // and O: 2 TMEM buffers each), so the next item's loads overlap this item's math.
-template <int MODE, bool FP8, int NB>
+template <int MODE, bool FP8, int NB, int TK>
 __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     k_attn_tc(AttnParams a, const int32_t* __restrict__ items, int n_work, int zb_count,
               const __grid_constant__ CUtensorMap tmQ,
@@ -232,13 +236,16 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  Bars* bars = reinterpret_cast<Bars*>(smem + off_bar(FP8, NB));
-  Work<MODE>* slots = reinterpret_cast<Work<MODE>*>(smem + off_work(FP8, NB));
-  static_assert(sizeof(Work<MODE>) <= 128, "work slot");
+  Bars* bars = reinterpret_cast<Bars*>(smem + off_bar(FP8, NB, TK));
+  Work<MODE, TK>* slots = reinterpret_cast<Work<MODE, TK>*>(smem + off_work(FP8, NB, TK));
+  static_assert(sizeof(Work<MODE, TK>) <= 128, "work slot");
   const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
-  static_assert(NB == 2 || !FP8, "E4M3 KV runs with double buffers");
-  constexpr int NKV = nkv(FP8, NB), OFF_V = off_v(FP8, NB), OFF_RAW = off_raw(FP8, NB);
-  constexpr uint32_t TMEM_COLS = tmem_cols(NB), COL_O = col_o(NB), COL_P = col_p(NB);
+  static_assert(TK == 128 || TK == 64, "tile width");
+  static_assert(!FP8 || NB == 2 || TK == 64, "E4M3 KV: double buffers, or single buffers with 64-key tiles");
+  constexpr int NKV = nkv(FP8, NB), OFF_V = off_v(FP8, NB, TK), OFF_RAW = off_raw(FP8, NB, TK);
+  constexpr int RAW_BYTES = raw_bytes(TK), NRAW = FP8 ? nraw(FP8, NB) : 1;   // (1: unused with BF16 KV)
+  constexpr int NCH = TK / 32, NHALF = TK / 64;   // 32-key chunks, 64-key halves of a tile
+  constexpr uint32_t TMEM_COLS = tmem_cols(NB), COL_O = col_o(NB, TK), COL_P = col_p(NB, TK);
   const uint32_t sK0 = ptx::smem_u32(smem + OFF_K), sV0 = ptx::smem_u32(smem + OFF_V);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -248,9 +255,10 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       ptx::mbar_init(&bars->v_full[s], 1);
       ptx::mbar_init(&bars->k_empty[s], 1);
       ptx::mbar_init(&bars->v_empty[s], 1);
-      ptx::mbar_init(&bars->kvc_full[s], 64);
+      ptx::mbar_init(&bars->kc_full[s], 32);
+      ptx::mbar_init(&bars->vc_full[s], 32);
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NRAW; ++s) {
       ptx::mbar_init(&bars->raw_full[s], 1);
       ptx::mbar_init(&bars->raw_empty[s], 64);
     }
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       // of the loads, so that a stage's TMA load, issued once the stage is
       // free, finds its rows in L2
       constexpr int PF = 4;
-      Work<MODE> PW;
+      Work<MODE, TK> PW;
       int pw = blockIdx.x, pti = 0;
       if (pw < n_work) PW.decode(a, items, pw, zb_count);
       auto prefetch_next = [&]() {
@@ -318,12 +326,21 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       for (int i = 0; i < PF; ++i) prefetch_next();
       bool ok = true;
       uint32_t c = 0, dc = 0, qc = 0;   // tile / E4M3 document-tile / item counters of this CTA
-      int last_raw[2] = {-1, -1}, last_q[2] = {-1, -1};
+      int last_raw[NRAW_MAX], last_q[2] = {-1, -1};
+      for (int s = 0; s < NRAW_MAX; ++s) last_raw[s] = -1;
+      // E4M3: widened fills of each stage, and the one whose completion this
+      // warp has not observed yet (-1: none)
+      uint32_t n_cvt[NKV];
+      int pend_cvt[NKV];
+      for (int s = 0; s < NKV; ++s) {
+        n_cvt[s] = 0;
+        pend_cvt[s] = -1;
+      }
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
         // the item into slot qc & 1 once every reader of the item two back is done with it
         const int qb = qc & 1;
         if (!ptx::mbar_wait(&bars->q_empty[qb], ((qc >> 1) & 1) ^ 1)) { ok = false; break; }
-        Work<MODE> W;
+        Work<MODE, TK> W;
         W.decode(a, items, w, zb_count);
         slots[qb] = W;
         ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
@@ -336,20 +353,38 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
           const TileInfo T = W.tile(ti);
           const int nbox = (T.kc + BOX - 1) / BOX;
           prefetch_next();
-          if (FP8 && !T.prompt) {
-            // raw codes into a raw stage; the widening warps fill K/V stage s
-            const int rs = dc & 1;
-            if (!ptx::mbar_wait(&bars->raw_empty[rs], ((dc >> 1) & 1) ^ 1)) { ok = false; break; }
-            ptx::mbar_arrive_expect_tx(&bars->raw_full[rs], nbox * 2 * BOX * HD);
-            uint8_t* dr = smem + OFF_RAW + rs * RAW_BYTES;
-            for (int h = 0; h < nbox; ++h) {
-              const int y = (int)(W.doc_row0 + T.key0 + h * BOX);
-              ptx::tma_load_2d(dr + h * BOX * HD, &tmK, &bars->raw_full[rs], 0, y);
-              ptx::tma_load_2d(dr + TK * HD + h * BOX * HD, &tmV, &bars->raw_full[rs], 0, y);
+          if (FP8) {
+            // With E4M3 KV, stage s is filled in turn by this warp (TMA, prompt
+            // tiles) and by the widening warps (document tiles).  A parity wait
+            // is unambiguous only while the waiter trails the barrier by at most
+            // one phase, so before its next fill of stage s this warp observes
+            // the completion of the stage's last widened fill: that widening
+            // itself waited for the release before it, so the stage's release
+            // barriers are then at most one phase ahead of this warp's view.
+            if (pend_cvt[s] >= 0) {
+              const uint32_t ph = (uint32_t)pend_cvt[s] & 1;
+              if (!ptx::mbar_wait(&bars->kc_full[s], ph) || !ptx::mbar_wait(&bars->vc_full[s], ph)) {
+                ok = false;
+                break;
+              }
+              pend_cvt[s] = -1;
             }
-            last_raw[rs] = (int)((dc >> 1) & 1);
-            ++dc;
-            continue;
+            if (!T.prompt) {
+              // raw codes into a raw stage; the widening warps fill K/V stage s
+              const int rs = dc % NRAW;
+              if (!ptx::mbar_wait(&bars->raw_empty[rs], ((dc / NRAW) & 1) ^ 1)) { ok = false; break; }
+              ptx::mbar_arrive_expect_tx(&bars->raw_full[rs], nbox * 2 * BOX * HD);
+              uint8_t* dr = smem + OFF_RAW + rs * RAW_BYTES;
+              for (int h = 0; h < nbox; ++h) {
+                const int y = (int)(W.doc_row0 + T.key0 + h * BOX);
+                ptx::tma_load_2d(dr + h * BOX * HD, &tmK, &bars->raw_full[rs], 0, y);
+                ptx::tma_load_2d(dr + TK * HD + h * BOX * HD, &tmV, &bars->raw_full[rs], 0, y);
+              }
+              last_raw[rs] = (int)((dc / NRAW) & 1);
+              pend_cvt[s] = (int)n_cvt[s]++;
+              ++dc;
+              continue;
+            }
           }
           uint8_t* dk = smem + OFF_K + s * TK * 128;
           uint8_t* dv = smem + OFF_V + s * TK * 128;
@@ -374,12 +409,12 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         if (last_kv[s] >= 0 && (!ptx::mbar_wait(&bars->k_full[s], (uint32_t)last_kv[s], 100000000LL) ||
                                 !ptx::mbar_wait(&bars->v_full[s], (uint32_t)last_kv[s], 100000000LL)))
           ok = false;
-      for (int s = 0; s < 2; ++s) {
+      for (int s = 0; s < NRAW; ++s)
         if (last_raw[s] >= 0 && !ptx::mbar_wait(&bars->raw_full[s], (uint32_t)last_raw[s], 100000000LL))
           ok = false;
+      for (int s = 0; s < 2; ++s)
         if (last_q[s] >= 0 && !ptx::mbar_wait(&bars->q_full[s], (uint32_t)last_q[s], 100000000LL))
           ok = false;
-      }
       if (!ok) atomicExch(status, ST_ETIMEOUT);
     }
   } else if (warp == 5) {
@@ -407,11 +442,11 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
           const int qb = sq & 1;
           if (!s_have) s_have = ptx::mbar_test(&bars->q_full[qb], (sq >> 1) & 1);
           if (s_have) {
-            const Work<MODE>& W = slots[qb];
+            const Work<MODE, TK>& W = slots[qb];
             const int s = cs % NKV, b = cs % NB;
             const TileInfo T = W.tile(sti);
             const bool widened = FP8 && !T.prompt;
-            uint64_t* fb = widened ? &bars->kvc_full[s] : &bars->k_full[s];
+            uint64_t* fb = widened ? &bars->kc_full[s] : &bars->k_full[s];
             uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
             if (ptx::mbar_test(fb, nuse & 1) && ptx::mbar_test(&bars->s_free[b], ((cs / NB) & 1) ^ 1)) {
               ++nuse;
@@ -440,12 +475,14 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         // ---- P.V of tile cp
         if (cp < cs) {
           const int qb = pq & 1, ob = pq % NB;
-          const Work<MODE>& W = slots[qb];
+          const Work<MODE, TK>& W = slots[qb];
           const int b = cp % NB, s = cp % NKV;
           const TileInfo T = W.tile(pti);
           const bool tma_v = !FP8 || T.prompt;
-          // the stage's latest TMA fill is this tile's when the tile is TMA-filled
-          if ((!tma_v || ptx::mbar_test(&bars->v_full[s], (n_tma[s] - 1) & 1)) &&
+          // the stage's latest fill of the tile's kind (counted when its S was
+          // issued) is this tile's
+          if ((tma_v ? ptx::mbar_test(&bars->v_full[s], (n_tma[s] - 1) & 1)
+                     : ptx::mbar_test(&bars->vc_full[s], (n_cvt[s] - 1) & 1)) &&
               ptx::mbar_test(&bars->p_full[b], (cp / NB) & 1) &&
               (pti != 0 || ptx::mbar_test(&bars->o_free[ob], ((pq / NB) & 1) ^ 1))) {
             ptx::tc_fence_after();
@@ -487,63 +524,67 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     __syncwarp();
   } else if (FP8 && warp >= 6) {
     // ------------------------------------------------------------ widen E4M3 -> f16
-    // 64 threads; thread tc widens rows tc and tc + 64 of the K and V code tiles
-    // into the swizzled MMA stage (the block scales act later, in f32).
-    const int tc = threadIdx.x - 192;
+    // Warp 6 widens the K codes of each document tile, warp 7 the V codes, into
+    // the swizzled MMA stage (the block scales act later, in f32); lane l takes
+    // rows l, l + 32, ...  K is widened once the stage's previous S has read it,
+    // V once the previous P.V has, so the next S does not wait for a P.V.
+    const int half = warp - 6;   // 0: K, 1: V
+    uint64_t* const empty = half == 0 ? bars->k_empty : bars->v_empty;
+    uint64_t* const full = half == 0 ? bars->kc_full : bars->vc_full;
+    uint8_t* const dst0 = smem + (half == 0 ? OFF_K : OFF_V);
+    // a row's four 16-byte code chunks, visited from a lane-dependent start:
+    // rows are 64 bytes apart, so lanes 2j and 2j + 1 with the same start would
+    // share banks with lanes 2j + 2 ... 2j + 7
+    const int rot = (lane >> 1) & 3;
     bool ok = true;
     uint32_t c = 0, dc = 0, qc = 0;
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
       const int qb = qc & 1;
       if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
-      const Work<MODE> W = slots[qb];
+      const Work<MODE, TK> W = slots[qb];
       ptx::mbar_arrive(&bars->q_empty[qb]);
       for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
         const TileInfo T = W.tile(ti);
         if (T.prompt) continue;
-        const int s = c % NKV, rs = dc & 1;
-        if (!ptx::mbar_wait(&bars->raw_full[rs], (dc >> 1) & 1)) { ok = false; break; }
-        if (!ptx::mbar_wait(&bars->k_empty[s], ((c / NKV) & 1) ^ 1) ||
-            !ptx::mbar_wait(&bars->v_empty[s], ((c / NKV) & 1) ^ 1)) { ok = false; break; }
-        const uint8_t* raw = smem + OFF_RAW + rs * RAW_BYTES;
+        const int s = c % NKV, rs = dc % NRAW;
+        if (!ptx::mbar_wait(&bars->raw_full[rs], (dc / NRAW) & 1)) { ok = false; break; }
+        if (!ptx::mbar_wait(&empty[s], ((c / NKV) & 1) ^ 1)) { ok = false; break; }
+        const uint8_t* raw = smem + OFF_RAW + rs * RAW_BYTES + half * TK * HD;
+        uint8_t* dst = dst0 + s * TK * 128;
 #pragma unroll
-        for (int kv = 0; kv < 2; ++kv) {
-          uint8_t* dst = smem + (kv == 0 ? OFF_K : OFF_V) + s * TK * 128;
+        for (int i = 0; i < TK / 32; ++i) {
+          const int row = lane + 32 * i;
+          if (row >= T.count) {
+            // past the tuple's retained slots: exact zeros (their codes were
+            // not loaded, and their block scale may not exist)
 #pragma unroll
-          for (int hrow = 0; hrow < 2; ++hrow) {
-            const int row = tc + hrow * 64;
-            if (row >= T.count) {
-              // past the tuple's retained slots: exact zeros (their codes were
-              // not loaded, and their block scale may not exist)
+            for (int ch = 0; ch < 8; ++ch)
+              *reinterpret_cast<uint4*>(dst + swz(row, ch)) = make_uint4(0, 0, 0, 0);
+            continue;
+          }
+          const uint4* src = reinterpret_cast<const uint4*>(raw + row * HD);
 #pragma unroll
-              for (int ch = 0; ch < 8; ++ch)
-                *reinterpret_cast<uint4*>(dst + swz(row, ch)) = make_uint4(0, 0, 0, 0);
-              continue;
-            }
-            const uint4* src = reinterpret_cast<const uint4*>(raw + kv * TK * HD + row * HD);
+          for (int j = 0; j < 4; ++j) {
+            const int q16 = (j + rot) & 3;
+            const uint4 cw = src[q16];
+            const uint32_t words[4] = {cw.x, cw.y, cw.z, cw.w};
+            uint32_t out[8];
 #pragma unroll
-            for (int q16 = 0; q16 < 4; ++q16) {
-              const uint4 cw = src[q16];
-              const uint32_t words[4] = {cw.x, cw.y, cw.z, cw.w};
-              uint32_t out[8];
+            for (int wd = 0; wd < 4; ++wd) {
 #pragma unroll
-              for (int wd = 0; wd < 4; ++wd) {
-#pragma unroll
-                for (int hw = 0; hw < 2; ++hw) {
-                  const uint16_t pair = (uint16_t)(words[wd] >> (16 * hw));
-                  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(out[2 * wd + hw]) : "h"(pair));
-                }
+              for (int hw = 0; hw < 2; ++hw) {
+                const uint16_t pair = (uint16_t)(words[wd] >> (16 * hw));
+                asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(out[2 * wd + hw]) : "h"(pair));
               }
-              // 16 codes -> 32 bytes of f16 = chunks 2*q16, 2*q16+1 of the row
-              *reinterpret_cast<uint4*>(dst + swz(row, 2 * q16)) =
-                  make_uint4(out[0], out[1], out[2], out[3]);
-              *reinterpret_cast<uint4*>(dst + swz(row, 2 * q16 + 1)) =
-                  make_uint4(out[4], out[5], out[6], out[7]);
             }
+            // 16 codes -> 32 bytes of f16 = chunks 2*q16, 2*q16+1 of the row
+            *reinterpret_cast<uint4*>(dst + swz(row, 2 * q16)) = make_uint4(out[0], out[1], out[2], out[3]);
+            *reinterpret_cast<uint4*>(dst + swz(row, 2 * q16 + 1)) = make_uint4(out[4], out[5], out[6], out[7]);
           }
         }
         fence_proxy_async();
         ptx::mbar_arrive(&bars->raw_empty[rs]);
-        ptx::mbar_arrive(&bars->kvc_full[s]);
+        ptx::mbar_arrive(&full[s]);
         ++dc;
       }
     }
@@ -597,7 +638,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       const int qb = qc & 1;
       if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
       // read in place; the slot is released at the item's end
-      const Work<MODE>& W = slots[qb];
+      const Work<MODE, TK>& W = slots[qb];
       const int pos = (W.row_base + r) / W.G;
 
       // O accumulates in TMEM (buffer qb); the running max m only moves when a
@@ -619,9 +660,9 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         // release the TMEM buffer
         uint32_t v[TK];
         ST_TMEM_LD32(sb, v);
-        if (nch > 1) ST_TMEM_LD32(sb + 32, (v + 32));
-        if (nch > 2) ST_TMEM_LD32(sb + 64, (v + 64));
-        if (nch > 3) ST_TMEM_LD32(sb + 96, (v + 96));
+        if (NCH > 1 && nch > 1) ST_TMEM_LD32(sb + 32, (v + 32));
+        if (NCH > 2 && nch > 2) ST_TMEM_LD32(sb + 64, (v + (NCH > 2 ? 64 : 0)));
+        if (NCH > 3 && nch > 3) ST_TMEM_LD32(sb + 96, (v + (NCH > 3 ? 96 : 0)));
         ptx::tmem_wait_ld();
         ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->s_free[b]);
@@ -630,7 +671,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         int nvis = T.count;
         if (causal) nvis = min(nvis, lim - T.key0 + 1);
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int ch = 0; ch < NCH; ++ch) {
           const int lo = nvis - 32 * ch;    // visible keys of this chunk
           if (ch < nch && lo < 32) {
 #pragma unroll
@@ -639,21 +680,24 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
           }
         }
         // E4M3 document tiles: one K and one V scale per 64-slot half of the tile
-        float ks[2] = {1.f, 1.f}, vs[2] = {1.f, 1.f};
+        float ks[NHALF], vs[NHALF];
+#pragma unroll
+        for (int hf = 0; hf < NHALF; ++hf) ks[hf] = vs[hf] = 1.f;
         if (FP8 && !T.prompt) {
           const float* scp = a.scales + ((W.doc_row0 + T.key0) >> 6) * 2;
           ks[0] = scp[0];
           vs[0] = scp[1];
-          if (T.count > 64) {
-            ks[1] = scp[2];
-            vs[1] = scp[3];
+          if (NHALF > 1 && T.count > 64) {
+            ks[NHALF - 1] = scp[2];
+            vs[NHALF - 1] = scp[3];
           }
         }
         // row maximum of the scaled scores (a positive scale commutes with the max)
         float cm[4];
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch)
-          cm[ch] = ch < nch ? chunk_max(v + 32 * ch) * ks[ch >> 1] : -INFINITY;
+          cm[ch] = (ch < NCH && ch < nch) ? chunk_max(v + 32 * (ch < NCH ? ch : 0)) * ks[(ch < NCH ? ch : 0) >> 1]
+                                          : -INFINITY;
         const float mx = max3(cm[0], cm[1], fmaxf(cm[2], cm[3])) * sl2;
         const bool need = mx > m + 8.f;
         if (__any_sync(0xffffffffu, need)) {
@@ -693,7 +737,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         const uint64_t nb2 = f2pack(-base, -base);
         uint64_t rs2[2] = {0, 0};           // packed partial row sums (+0.0f lanes)
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int ch = 0; ch < NCH; ++ch) {
           if (ch < nch) {
             const float mul = sl2 * ks[ch >> 1];
             const uint64_t m2 = f2pack(mul, mul), vs2 = f2pack(vs[ch >> 1], vs[ch >> 1]);
@@ -835,14 +879,25 @@ bool map2d_u8(CUtensorMap* m, const void* base, uint64_t outer, uint32_t box_out
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MODE, bool FP8, int NB>
+template <int MODE, bool FP8, int NB, int TK>
 void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_attn_tc<MODE, FP8, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_bytes(FP8, NB));
+    cudaFuncSetAttribute(k_attn_tc<MODE, FP8, NB, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_bytes(FP8, NB, TK));
     done = true;
   }
+}
+
+template <int MODE, bool FP8, int NB, int TK>
+void launch_attn(const AttnParams& a, const int32_t* items, int n_work, int zb, const CUtensorMap& mq,
+                 const CUtensorMap& mk, const CUtensorMap& mv, const CUtensorMap& mkp, const CUtensorMap& mvp,
+                 int* status, cudaStream_t s) {
+  set_smem_attr<MODE, FP8, NB, TK>();
+  const int slots = sm_count() * ctas_per_sm(NB);
+  const int grid = n_work < slots ? n_work : slots;
+  k_attn_tc<MODE, FP8, NB, TK><<<grid, nthreads(FP8), smem_bytes(FP8, NB, TK), s>>>(a, items, n_work, zb, mq, mk,
+                                                                                  mv, mkp, mvp, status);
 }
 
 }  // namespace
@@ -869,24 +924,17 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   else ok = ok && map2d(&mk, a.Kr, HD, planes, BOX) && map2d(&mv, a.Vr, HD, planes, BOX);
   if (!ok) return ST_ECUDA;
   const int n_work = a.n_work * a.hkv;
-  // buffer layout: E4M3 always double-buffered; BF16 by a.nb (0: two CTAs per SM)
-  const int nb = fp8 ? 2 : (a.nb == 2 ? 2 : 1);
-  const int slots = sm_count() * ctas_per_sm(nb);
-  const int grid = n_work < slots ? n_work : slots;
   const int zb = 1;   // unused in eval (the work list carries the row block)
-  if (fp8) {
-    set_smem_attr<1, true, 2>();
-    k_attn_tc<1, true, 2><<<grid, nthreads(true), smem_bytes(true, 2), s>>>(a, a.work, n_work, zb, mq, mk,
-                                                                      mv, mkp, mvp, status);
-  } else if (nb == 2) {
-    set_smem_attr<1, false, 2>();
-    k_attn_tc<1, false, 2><<<grid, nthreads(false), smem_bytes(false, 2), s>>>(a, a.work, n_work, zb, mq,
-                                                                              mk, mv, mkp, mvp, status);
-  } else {
-    set_smem_attr<1, false, 1>();
-    k_attn_tc<1, false, 1><<<grid, nthreads(false), smem_bytes(false, 1), s>>>(a, a.work, n_work, zb, mq,
-                                                                         mk, mv, mkp, mvp, status);
-  }
+  // layout by a.nb (0 or 1: two CTAs per SM with single buffers, 2: one CTA with
+  // double buffers); E4M3 single buffers run 64-key tiles
+  if (fp8 && a.nb == 2)
+    launch_attn<1, true, 2, 128>(a, a.work, n_work, zb, mq, mk, mv, mkp, mvp, status, s);
+  else if (fp8)
+    launch_attn<1, true, 1, 64>(a, a.work, n_work, zb, mq, mk, mv, mkp, mvp, status, s);
+  else if (a.nb == 2)
+    launch_attn<1, false, 2, 128>(a, a.work, n_work, zb, mq, mk, mv, mkp, mvp, status, s);
+  else
+    launch_attn<1, false, 1, 128>(a, a.work, n_work, zb, mq, mk, mv, mkp, mvp, status, s);
   return ST_OK;
 }
 
@@ -900,12 +948,7 @@ int attn_tc_prefill(const AttnParams& a, const int32_t* items, int n_items, int*
   if (!map_q(&mq, a.q, a.hq, (uint64_t)a.rows, G) || !map2d(&mk, a.K, HD, planes, BOX) ||
       !map2d(&mv, a.V, HD, planes, BOX))
     return ST_ECUDA;
-  set_smem_attr<0, false, 1>();
-  const int n_work = n_items * a.hkv;
-  const int slots = sm_count() * ctas_per_sm(1);
-  const int grid = n_work < slots ? n_work : slots;
-  k_attn_tc<0, false, 1><<<grid, nthreads(false), smem_bytes(false, 1), s>>>(a, items, n_work, 1, mq, mk,
-                                                                       mv, mk, mv, status);
+  launch_attn<0, false, 1, 128>(a, items, n_items * a.hkv, 1, mq, mk, mv, mk, mv, status, s);
   return ST_OK;
 }
 

@@ -155,11 +155,11 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
   };
   // Coordinate search: the attention layout and work order at the default
   // chunk size, then the chunk size (prompt rows per pass of the layers).
-  const bool bf16_kv = kv->kv_dtype == ST_BF16 && ctx->cfg.dtype == ST_BF16;
+  const bool tc_kv = ctx->cfg.dtype == ST_BF16;   // tensor-core attention (BF16 or E4M3 KV)
   Sched bestc{start.eval_rows > 0 ? start.eval_rows : (1LL << 18), 1, 1};
   float best_ms = 1e30f, ms = 0.f;
   for (int nb : {1, 2}) {
-    if (nb == 2 && !bf16_kv) continue;
+    if (nb == 2 && !tc_kv) continue;
     for (int lf : {1, 0}) {
       const Sched sc{bestc.eval_rows, nb, lf};
       if ((rc = time_sched(sc, &ms)) != ST_OK) break;
