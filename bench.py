@@ -80,14 +80,17 @@ def workload(args, rank=0):
 def config_dict(args, cfg, table, op):
     L = table["lengths"]
     return {
-        "workload": "plain BF16 KV-cache filter operator, full path per step: kv_build (prefill) "
+        "workload": ("plain BF16" if args.kv_dtype == "bf16" else "BF16 model, E4M3 retained")
+                    + " KV-cache filter operator, full path per step: kv_build (prefill) "
                     f"+ kv_retain(r={args.r}) + op_eval; decoder 8L d1024 16q/4kv x64 F2816 V32000 "
                     f"random-init; {len(L)} tuples, lognormal(512, 0.6) lengths clipped 64..2048, "
                     "Zipf(1.1) ids; 32-token prompt",
         "tuples": int(len(L)), "doc_tokens": int(L.sum()), "mean_len": float(L.mean()),
         "prompt_len": len(op.prompt), "r": args.r, "kv_dtype": args.kv_dtype,
         "operands": "BF16 weights (held exactly as f16 for the tensor cores), f16 GEMM activations, "
-                    "BF16 Q/K/V, probabilities and KV cache, f32 accumulation, softmax and residual",
+                    "BF16 Q/K/V, probabilities and KV cache, f32 accumulation, softmax and residual"
+                    + ("" if args.kv_dtype == "bf16" else "; retained K/V as E4M3 codes with f32 scales "
+                       "per 64-slot block, widened exactly to f16 for the attention MMAs"),
         "l2": "inputs larger than L2 (full KV cache %.1f GB per step)" % (
             8 * 4 * 64 * 2 * 2 * float(L.sum()) / 1e9),
     }
