@@ -162,19 +162,6 @@ __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
 __device__ __forceinline__ void tmem_relinquish() {
   asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
-// Per-warpgroup register budget (every thread of the warpgroup executes it):
-// .dec returns registers to the CTA's pool, .inc waits until the pool holds
-// enough, so the budgets of all warpgroups must sum to the launch's registers.
-template <int N>
-__device__ __forceinline__ void setmaxnreg_inc() {
-  static_assert(N % 8 == 0 && N >= 24 && N <= 256, "setmaxnreg count");
-  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
-}
-template <int N>
-__device__ __forceinline__ void setmaxnreg_dec() {
-  static_assert(N % 8 == 0 && N >= 24 && N <= 256, "setmaxnreg count");
-  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
-}
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
                : "memory");
