@@ -739,11 +739,17 @@ def main():
             ab = attention_bytes(cfg, table["lengths"], r, kv_esz, len(pr_r.prompt))
             gbs = ab / (at["ms"] / reps / 1000.0) / 1e9 if at["ms"] > 0 else 0.0
             gg = pr["gemm"]
+            # whole-op_eval roofline: the projections' algorithmic FLOPs at the
+            # sustained tensor peak plus the attention's compulsory bytes at the
+            # HBM peak, per pass over the table
+            roof_s = gg["flops"] / reps / (tf_peak * 1e12) + ab / (hbm_peak * 1e9)
             out[str(r)] = {"tuples_per_s": T / (e_ms / 1000.0), "ms": e_ms,
                            "attention_ms": at["ms"] / reps, "attention_GBps": gbs,
                            "attention_hbm_frac": gbs / hbm_peak,
                            "gemm_ms": gg["ms"] / reps,
-                           "gemm_TFLOPs": gg["flops"] / (gg["ms"] / 1000.0) / 1e12 if gg["ms"] else 0}
+                           "gemm_TFLOPs": gg["flops"] / (gg["ms"] / 1000.0) / 1e12 if gg["ms"] else 0,
+                           "roofline_tuples_per_s": T / roof_s if roof_s > 0 else None,
+                           "frac_of_roofline": (roof_s * 1000.0) / e_ms if e_ms > 0 else None}
         kv.retain(op.r, kvd)
     mapr = None
     if not args.no_map and rank == 0:
@@ -803,6 +809,9 @@ def main():
             parts["proxy_fp8_tuples_per_s"] = proxy["at_validation_tau"]["tuples_per_s"]
         if str(args.r) in out:
             parts["attention_hbm_frac"] = out[str(args.r)]["attention_hbm_frac"]
+            parts["op_eval_frac_of_roofline"] = out[str(args.r)]["frac_of_roofline"]
+            parts["op_eval_roofline_unit"] = ("op_eval time at the roofline (GEMM FLOPs / sustained tensor "
+                                              f"peak + attention bytes / HBM peak) over measured, r = {args.r}")
             parts["attention_hbm_frac_unit"] = f"compulsory bytes / time over the measured HBM peak, r = {args.r}"
         line["metric_parts"] = parts
         print(json.dumps(line))
