@@ -613,6 +613,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         uint32_t o0[32];
         ST_TMEM_LD32(o_addr + 32 * h, o0);
         ptx::tmem_wait_ld();
+        ST_TMEM_TIE32(o0);
         if (h == 1) {
           ptx::tc_fence_before();
           ptx::mbar_arrive(&bars->o_free[ob]);
@@ -664,6 +665,8 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         if (NCH > 2 && nch > 2) ST_TMEM_LD32(sb + 64, (v + (NCH > 2 ? 64 : 0)));
         if (NCH > 3 && nch > 3) ST_TMEM_LD32(sb + 96, (v + (NCH > 3 ? 96 : 0)));
         ptx::tmem_wait_ld();
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) ST_TMEM_TIE32((v + 32 * ch));
         ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->s_free[b]);
         // invisible keys of this row (ragged tail, causal limit) in the loaded
@@ -713,6 +716,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
               uint32_t o0[16];
               ST_TMEM_LD16(o_addr + 16 * part, o0);
               ptx::tmem_wait_ld();
+              ST_TMEM_TIE16(o0);
 #pragma unroll
               for (int e = 0; e < 16; e += 2) {
                 const uint64_t x = mul2((uint64_t)o0[e] | ((uint64_t)o0[e + 1] << 32), a2);

@@ -158,6 +158,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
       ST_TMEM_LD32(taddr + j, g);
       ST_TMEM_LD32(taddr + BN / 2 + j, u);
       ptx::tmem_wait_ld();
+      ST_TMEM_TIE32(g);
+      ST_TMEM_TIE32(u);
       float hv[32];
 #pragma unroll
       for (int e = 0; e < 32; ++e) hv[e] = silu_f(__uint_as_float(g[e]) * inv) * (__uint_as_float(u[e]) * inv);
@@ -182,6 +184,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
       ST_TMEM_LD32(taddr + c, r);
       ST_TMEM_LD32(taddr + c + 32, r2);
       ptx::tmem_wait_ld();
+      ST_TMEM_TIE32(r);
+      ST_TMEM_TIE32(r2);
       float v[64];
 #pragma unroll
       for (int e = 0; e < 64; ++e) v[e] = __uint_as_float(r[e]) * inv;
@@ -207,6 +211,7 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
       }
       if (c + 32 < (half + 1) * (BN / 2)) resid_load(ep, pre, row0, nrows, n0 + c + 32, lane);
       ptx::tmem_wait_ld();
+      ST_TMEM_TIE32(r);
       __syncwarp();
       uint32_t xw[16];   // bf16(x) of the row, packed in pairs
 #pragma unroll
@@ -246,6 +251,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, uint8_t* st, 
       ST_TMEM_LD32(taddr + c, r);
       ST_TMEM_LD32(taddr + c + 32, r2);
       ptx::tmem_wait_ld();
+      ST_TMEM_TIE32(r);
+      ST_TMEM_TIE32(r2);
       if (row < M) {
         float* o = ep.out + (int64_t)row * ep.ld + n0 + c;
 #pragma unroll

@@ -258,6 +258,23 @@ __device__ __forceinline__ void tmem_wait_st() {
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// tcgen05.ld writes its registers asynchronously and tcgen05.wait::ld names
+// none of them, so nothing orders a use of the loaded values after the wait.
+// These empty statements read and rewrite the registers right after the wait:
+// every later use then depends on them, at no instruction cost.
+#define ST_TMEM_TIE16(r)   \
+  asm volatile(""        \
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), \
+        "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), \
+        "+r"(r[13]), "+r"(r[14]), "+r"(r[15]))
+#define ST_TMEM_TIE32(r)   \
+  asm volatile(""        \
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), \
+        "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), \
+        "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), \
+        "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), \
+        "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), \
+        "+r"(r[31]))
 
 // Shared-memory matrix descriptor of a K-major tile stored with the 128-byte
 // swizzle (rows of 64 bf16 = 128 B; 8-row groups 1024 B apart).
