@@ -277,16 +277,21 @@ def proxy_fp8_arm(args, model, kv, cfg, table, stretto, synth, torch):
     kv.build(torch.from_numpy(table["tokens"]).cuda())
     x_ho = kv.read(stretto.ST_VIEW_POOLED, torch.float32, (T, cfg.d))
 
-    def timed(fn, reps=3):
+    def timed(fn, reps=5, rounds=3):
+        # median over rounds of the mean over reps (the cascade reads its
+        # fallback count on the host every pass, so single rounds are noisy)
         fn()
         torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(reps):
-            fn()
-        a1.record(stream)
-        torch.cuda.synchronize()
-        return a0.elapsed_time(a1) / reps
+        per = []
+        for _ in range(rounds):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            per.append(a0.elapsed_time(a1) / reps)
+        return statistics.median(per)
 
     kv.retain(r, stretto.ST_BF16)
     lab_plain = torch.empty(T, dtype=torch.int32, device="cuda")

@@ -534,21 +534,24 @@ extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, vo
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
       build_rowinfo(kv->off, ch.t0, ch.t1, ch.r0, ch.rows, w.rowtup, w.pos, s);
     }
+    // bf16 path: the gather writes layer 0's normalised rows too; afterwards every
+    // residual epilogue leaves half(x) and the row's partial sums of squares, and
+    // the next projection applies 1/rms in its epilogue.
+    const bool fused = c.dtype == ST_BF16;
     {
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      if (c.dtype == ST_BF16) embed_rows<bf16>(tokens_dev + ch.r0, ch.rows, (const bf16*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
-      else embed_rows<float>(tokens_dev + ch.r0, ch.rows, (const float*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
+      if (fused)
+        embed_norm_rows(tokens_dev + ch.r0, ch.rows, (const bf16*)ctx->embed, c.d, c.vocab, c.eps, w.x,
+                        (__half*)w.xn, ctx->dstatus, s);
+      else
+        embed_rows<float>(tokens_dev + ch.r0, ch.rows, (const float*)ctx->embed, c.d, c.vocab, w.x, ctx->dstatus, s);
     }
     CKLAUNCH();
-    // bf16 path: only layer 0 runs a standalone RMSNorm; afterwards every residual
-    // epilogue leaves bf16(x) and the row's partial sums of squares, and the next
-    // projection applies 1/rms in its epilogue.
-    const bool fused = c.dtype == ST_BF16;
     for (int l = 0; l < c.layers; ++l) {
       const LayerW& LW = ctx->layers[l];
       char* Kl = (char*)kv->K + (size_t)l * c.hkv * kv->R * c.hd * e;
       char* Vl = (char*)kv->V + (size_t)l * c.hkv * kv->R * c.hd * e;
-      if (!fused || l == 0) RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
+      if (!fused) RC(rmsnorm(ctx, w.x, ch.rows, w.xn, nullptr, s));
       EpiParams ep;
       if (fused && l > 0) set_norm_in(ep, w.ssq, c);
       ep.mode = EPI_QKV;

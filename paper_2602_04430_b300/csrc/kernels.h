@@ -79,6 +79,9 @@ struct OpSet {
 template <typename act_t>
 void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, int vocab, float* x, int* status,
                 cudaStream_t s);
+// BF16 model: the gather fused with the first layer's RMSNorm (xn in half).
+void embed_norm_rows(const int32_t* tok, int64_t rows, const bf16* E, int d, int vocab, float eps, float* x,
+                     __half* xn, int* status, cudaStream_t s);
 template <typename act_t>
 void rmsnorm_rows(const float* x, int64_t rows, int d, float eps, act_t* xn, float* inv_rms,
                   cudaStream_t s, int64_t x_ld = 0);

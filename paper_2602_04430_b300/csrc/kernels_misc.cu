@@ -295,6 +295,49 @@ template void rmsnorm_rows<bf16>(const float*, int64_t, int, float, bf16*, float
 template void rmsnorm_rows<__half>(const float*, int64_t, int, float, __half*, float*, cudaStream_t,
                                  int64_t);
 
+// Embedding gather fused with the first layer's RMSNorm (BF16 model), one warp
+// per row: x = E[tok] in float32 (the residual stream) and xn = x / rms(x) in
+// half.  Each lane sums its squares in k_rmsnorm's order, so xn equals the
+// gather followed by k_rmsnorm bit for bit; the second pass re-reads the
+// embedding row (an L2 hit) instead of the float32 row just written.
+__device__ __forceinline__ float4 load4_bf16(const bf16* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__global__ void k_embed_norm(const int32_t* __restrict__ tok, int64_t rows, const bf16* __restrict__ E, int d,
+                             int vocab, float eps, float* __restrict__ x, __half* __restrict__ xn,
+                             int* status) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const int t = tok[row];
+  const bool ok = t >= 0 && t < vocab;
+  if (!ok && lane == 0) atomicCAS(status, ST_OK, ST_EINVAL);
+  const bf16* er = E + (int64_t)(ok ? t : 0) * d;
+  float* xr = x + row * d;
+  float ss = 0.f;
+  for (int c = lane * 4; c < d; c += 128) {
+    const float4 v = ok ? load4_bf16(er + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(xr + c) = v;
+    ss += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+  }
+  ss = warp_sum(ss);
+  const float inv = 1.0f / sqrtf(ss / (float)d + eps);
+  __half* o = xn + row * d;
+  for (int c = lane * 4; c < d; c += 128) {
+    const float4 v = ok ? load4_bf16(er + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    store4(o + c, make_float4(v.x * inv, v.y * inv, v.z * inv, v.w * inv));
+  }
+}
+
+void embed_norm_rows(const int32_t* tok, int64_t rows, const bf16* E, int d, int vocab, float eps, float* x,
+                     __half* xn, int* status, cudaStream_t s) {
+  if (rows <= 0) return;
+  k_embed_norm<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(tok, rows, E, d, vocab, eps, x, xn, status);
+}
+
 // ------------------------------------------------------------------ EA-lite statistics
 // Block per (tuple, kv head): mean and population variance over (document
 // position, query head of the group) of every post-RoPE query dimension.
@@ -410,13 +453,20 @@ __global__ void __launch_bounds__(256) k_scores(const act_t* __restrict__ K, con
     float kk[VN], vx[VN];
     Vec<act_t>::load(K + ((int64_t)g * R + r0 + m) * hd + c, kk);
     Vec<act_t>::load(V + ((int64_t)g * R + r0 + m) * hd + c, vx);
-    const float* mup = mu + ((int64_t)lt * hkv + g) * hd + c;
-    const float* s2p = s2 + ((int64_t)lt * hkv + g) * hd + c;
+    // the tuple's statistics as 16-byte vectors (c is a multiple of VN >= 4 floats)
+    const float4* mup = reinterpret_cast<const float4*>(mu + ((int64_t)lt * hkv + g) * hd + c);
+    const float4* s2p = reinterpret_cast<const float4*>(s2 + ((int64_t)lt * hkv + g) * hd + c);
 #pragma unroll
-    for (int e = 0; e < VN; ++e) {
-      d1 += mup[e] * kk[e];
-      d2 += s2p[e] * kk[e] * kk[e];
-      vv += vx[e] * vx[e];
+    for (int e4 = 0; e4 < VN / 4; ++e4) {
+      const float4 m4 = mup[e4], q4 = s2p[e4];
+      const float mm[4] = {m4.x, m4.y, m4.z, m4.w}, ss[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = 4 * e4 + j;
+        d1 += mm[j] * kk[e];
+        d2 += ss[j] * kk[e] * kk[e];
+        vv += vx[e] * vx[e];
+      }
     }
   }
   float lin = d1 * c1 + d2 * c2;
