@@ -33,10 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = "tuples/s: proxy+FP8 vs plain BF16 at >=99% label agreement; % HBM roofline"
 # DRAM bytes per projection-GEMM launch on this workload (the CTA-pair kernel
 # k_gemm_tc2, which runs every launch of more than 128 rows), from the ncu
-# capture of the current kernel (29.40 GB over the four projections of one
+# capture of the current kernel (28.76 GB over the four projections of one
 # layer of the 1024-tuple table, 610,382 rows each, scaled to the 652,000 rows
 # of this workload's average launch).  Set to None whenever the kernel changes.
-GEMM_TRAFFIC_PER_LAUNCH = 7.85e9
+GEMM_TRAFFIC_PER_LAUNCH = 7.68e9
 
 
 def parse():

@@ -453,20 +453,13 @@ __global__ void __launch_bounds__(256) k_scores(const act_t* __restrict__ K, con
     float kk[VN], vx[VN];
     Vec<act_t>::load(K + ((int64_t)g * R + r0 + m) * hd + c, kk);
     Vec<act_t>::load(V + ((int64_t)g * R + r0 + m) * hd + c, vx);
-    // the tuple's statistics as 16-byte vectors (c is a multiple of VN >= 4 floats)
-    const float4* mup = reinterpret_cast<const float4*>(mu + ((int64_t)lt * hkv + g) * hd + c);
-    const float4* s2p = reinterpret_cast<const float4*>(s2 + ((int64_t)lt * hkv + g) * hd + c);
+    const float* mup = mu + ((int64_t)lt * hkv + g) * hd + c;
+    const float* s2p = s2 + ((int64_t)lt * hkv + g) * hd + c;
 #pragma unroll
-    for (int e4 = 0; e4 < VN / 4; ++e4) {
-      const float4 m4 = mup[e4], q4 = s2p[e4];
-      const float mm[4] = {m4.x, m4.y, m4.z, m4.w}, ss[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int e = 4 * e4 + j;
-        d1 += mm[j] * kk[e];
-        d2 += ss[j] * kk[e] * kk[e];
-        vv += vx[e] * vx[e];
-      }
+    for (int e = 0; e < VN; ++e) {
+      d1 += mup[e] * kk[e];
+      d2 += s2p[e] * kk[e] * kk[e];
+      vv += vx[e] * vx[e];
     }
   }
   float lin = d1 * c1 + d2 * c2;
