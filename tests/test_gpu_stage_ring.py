@@ -1,0 +1,68 @@
+"""Determinism of the tensor-core attention's K/V stage ring under heavy
+alternation of fill kinds.  With E4M3 retained caches a stage is filled in turn
+by TMA (the prompt's f16 keys) and by the widening warps (document codes); a
+table of thousands of short documents (1 .. 70 tokens, so almost every work
+item is one or two document tiles followed by one prompt tile) makes the two
+kinds alternate on nearly every fill.  A stage refilled while still being read
+shows up as evaluations that differ from one call to the next, so repeated
+evaluations must agree bit for bit, in both attention layouts; the BF16 cache
+of the same table is checked the same way, and E4M3 decisions must agree with
+BF16 on almost every tuple."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ring():
+    import torch
+    from paper_2602_04430_b300 import build, stretto, synth
+    build.build()
+    cfg = synth.MODELS["c2_bf16"]
+    lengths = [1 + (7 * i) % 70 for i in range(3000)]
+    table = synth.make_table_from_lengths(lengths, cfg.vocab, seed=71, ids="zipf")
+    model = stretto.Model(cfg, synth.make_weights(cfg, seed=72), max_pos=256)
+    kv = model.kv_alloc(table["offsets"])
+    kv.build(torch.from_numpy(table["tokens"]).cuda())
+    torch.cuda.synchronize()
+    model.status()
+    return dict(cfg=cfg, model=model, kv=kv, T=len(lengths), stretto=stretto, synth=synth, torch=torch)
+
+
+def _evals(e, kv_dtype, nb, reps=4):
+    st, torch = e["stretto"], e["torch"]
+    st.set_schedule(e["model"], attn_nb=nb)
+    e["kv"].retain(1.0, kv_dtype)
+    op = e["model"].operator(e["synth"].make_prompt(32, e["cfg"].vocab, seed=73, r=1.0))
+    ids = torch.arange(e["T"], dtype=torch.int32, device="cuda")
+    out = []
+    for _ in range(reps):
+        lg, lb = op.eval(e["kv"], ids)
+        out.append((lg.clone(), lb.clone()))
+    torch.cuda.synchronize()
+    e["model"].status()
+    return out
+
+
+@pytest.mark.parametrize("nb", [1, 2])
+@pytest.mark.parametrize("kv_dtype", ["e4m3", "bf16"])
+def test_repeated_evaluations_are_bit_identical(ring, kv_dtype, nb):
+    st, torch = ring["stretto"], ring["torch"]
+    code = st.ST_E4M3 if kv_dtype == "e4m3" else st.ST_BF16
+    try:
+        runs = _evals(ring, code, nb)
+    finally:
+        st.set_schedule(ring["model"], attn_nb=1)
+    lg0, lb0 = runs[0]
+    assert bool(torch.isfinite(lg0).all())
+    for lg, lb in runs[1:]:
+        assert torch.equal(lg, lg0), "an evaluation differs from the first one"
+        assert torch.equal(lb, lb0)
+
+
+def test_e4m3_decisions_agree_with_bf16(ring):
+    st = ring["stretto"]
+    lb_e4 = _evals(ring, st.ST_E4M3, 1, reps=1)[0][1].cpu().numpy()
+    lb_bf = _evals(ring, st.ST_BF16, 1, reps=1)[0][1].cpu().numpy()
+    assert float(np.mean(lb_e4 == lb_bf)) >= 0.98
