@@ -162,3 +162,37 @@ def test_e4m3_codes_bit_exact(run):
                     c_ref, s_ref, _ = F.quantize_blocks(src[l, g, a:b], "f32")
                     np.testing.assert_array_equal(codes[l, g, a:b], c_ref)
                     np.testing.assert_array_equal(sc[l, g, a // 64:b // 64, which], s_ref)
+
+
+def test_out_of_range_token_is_reported_not_read(run):
+    """The BF16 build's fused gather + first RMSNorm checks token ids itself: an
+    id outside [0, vocab) embeds as zeros (so layer 0's key at that position is
+    exactly zero in every kv head), st_status reports ST_EINVAL once, and the
+    context keeps working."""
+    import torch
+    from paper_2602_04430_b300 import stretto, synth
+    cfg, model = run["cfg"], run["model"]
+    table = synth.make_table_from_lengths([5, 40, 3], cfg.vocab, seed=31, ids="zipf")
+    tok = table["tokens"].copy()
+    bad = [3, len(tok) - 1]
+    tok[bad[0]], tok[bad[1]] = cfg.vocab, -1
+    model.status()
+    kv = model.kv_alloc(table["offsets"])
+    kv.build(torch.from_numpy(tok).cuda())
+    torch.cuda.synchronize()
+    with pytest.raises(stretto.StrettoError) as e:
+        model.status()
+    assert e.value.code == stretto.ST_EINVAL
+    model.status()
+    R = len(tok)
+    K = kv.read(stretto.ST_VIEW_K, torch.bfloat16, (cfg.layers, cfg.hkv, R, cfg.hd)).float()
+    for j in bad:
+        assert bool((K[0, :, j, :] == 0).all())
+    assert bool((K[0, :, 0, :] != 0).any())
+    kv.build(torch.from_numpy(table["tokens"]).cuda())
+    kv.retain(1.0)
+    op = model.operator(synth.make_prompt(16, cfg.vocab, seed=32, r=1.0))
+    lg, _ = op.eval(kv, torch.arange(kv.T, dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    model.status()
+    assert bool(torch.isfinite(lg).all())
