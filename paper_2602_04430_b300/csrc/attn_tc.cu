@@ -654,6 +654,20 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         const TileInfo T = W.tile(ti);
         const int nch = (T.kc + 31) >> 5;           // 32-key chunks any row can see
         const bool causal = (MODE == 0) || T.prompt;
+        // E4M3 document tiles: one K and one V scale per 64-slot half of the
+        // tile, loaded before the wait for S so that their latency overlaps it
+        float ks[NHALF], vs[NHALF];
+#pragma unroll
+        for (int hf = 0; hf < NHALF; ++hf) ks[hf] = vs[hf] = 1.f;
+        if (FP8 && !T.prompt) {
+          const float* scp = a.scales + ((W.doc_row0 + T.key0) >> 6) * 2;
+          ks[0] = scp[0];
+          vs[0] = scp[1];
+          if (NHALF > 1 && T.count > 64) {
+            ks[NHALF - 1] = scp[2];
+            vs[NHALF - 1] = scp[3];
+          }
+        }
         if (!ptx::mbar_wait(&bars->s_full[b], (c / NB) & 1)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t sb = tmem + lane_base + b * TK;
@@ -680,19 +694,6 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
 #pragma unroll
             for (int j = 0; j < 32; ++j)
               if (j >= lo) v[32 * ch + j] = 0xFF800000u;
-          }
-        }
-        // E4M3 document tiles: one K and one V scale per 64-slot half of the tile
-        float ks[NHALF], vs[NHALF];
-#pragma unroll
-        for (int hf = 0; hf < NHALF; ++hf) ks[hf] = vs[hf] = 1.f;
-        if (FP8 && !T.prompt) {
-          const float* scp = a.scales + ((W.doc_row0 + T.key0) >> 6) * 2;
-          ks[0] = scp[0];
-          vs[0] = scp[1];
-          if (NHALF > 1 && T.count > 64) {
-            ks[NHALF - 1] = scp[2];
-            vs[NHALF - 1] = scp[3];
           }
         }
         // row maximum of the scaled scores (a positive scale commutes with the max)
