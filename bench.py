@@ -197,15 +197,15 @@ def run_reference(args):
     return 0
 
 
-def attention_bytes(cfg, lengths, r, kv_esz, P):
+def attention_bytes(cfg, nkeep, kv_esz, P):
     """Compulsory HBM bytes of the operator's attention, all layers: the retained
     K and V once (plus the E4M3 block scales), and per prompt row its queries,
-    its own keys and values, and its output, 16-bit each."""
-    from oracle.operator import n_keep  # host arithmetic only: the retained counts
-    n = np.array([n_keep(int(L), r) for L in lengths], dtype=np.float64)
+    its own keys and values, and its output, 16-bit each.  ``nkeep``: the
+    retained count of every tuple (as the library's ST_VIEW_NKEEP reports it)."""
+    n = np.asarray(nkeep, dtype=np.float64)
     kv = 2.0 * cfg.layers * cfg.hkv * cfg.hd * kv_esz * n.sum()
     scales = 0.0 if kv_esz == 2 else 2.0 * 4 * cfg.layers * cfg.hkv * np.ceil(n / 64).sum()
-    rows = float(len(lengths)) * P
+    rows = float(len(n)) * P
     prompt = cfg.layers * rows * 2.0 * cfg.hd * (2 * cfg.hq + 2 * cfg.hkv)
     return kv + scales + prompt
 
@@ -741,7 +741,8 @@ def main():
             pr = model.prof_read()
             e_ms = a0.elapsed_time(a1) / reps
             at = pr["attention"]
-            ab = attention_bytes(cfg, table["lengths"], r, kv_esz, len(pr_r.prompt))
+            nkeep = kv.read(stretto.ST_VIEW_NKEEP, torch.int32, (T,)).cpu().numpy()
+            ab = attention_bytes(cfg, nkeep, kv_esz, len(pr_r.prompt))
             gbs = ab / (at["ms"] / reps / 1000.0) / 1e9 if at["ms"] > 0 else 0.0
             gg = pr["gemm"]
             # whole-op_eval roofline: the projections' algorithmic FLOPs at the

@@ -15,16 +15,16 @@ def test_attention_bytes_hand_case():
     import bench
     from paper_2602_04430_b300 import synth
     cfg = synth.ModelConfig(layers=2, d=16, hq=4, hkv=2, hd=4, ffn=32, vocab=64)
-    lengths = [3, 10, 64, 65]        # n_keep at r = 0.5: 2, 5, 32, 33 (sum 72; one 64-slot block each)
+    nkeep = [2, 5, 32, 33]           # retained counts (sum 72; one 64-slot block each)
     # per layer and kv head the retained K and V, 2 bytes a value: 2 * 2 * 2 * 4 * 2 * 72
     kv_bf16 = 4608
     # per prompt row (4 tuples x P = 2) and layer: Q and O (hq * hd each) plus the
     # row's own K and V (hkv * hd each), 2 bytes a value: 2 * 8 * 2 * 4 * (8 + 4)
     prompt = 1536
-    assert bench.attention_bytes(cfg, lengths, 0.5, 2, 2) == kv_bf16 + prompt
+    assert bench.attention_bytes(cfg, nkeep, 2, 2) == kv_bf16 + prompt
     # E4M3: one byte a value, plus a float32 K and V scale per 64-slot block
     scales = 2 * 4 * 2 * 2 * 4
-    assert bench.attention_bytes(cfg, lengths, 0.5, 1, 2) == kv_bf16 // 2 + scales + prompt
+    assert bench.attention_bytes(cfg, nkeep, 1, 2) == kv_bf16 // 2 + scales + prompt
 
 
 def test_clock_record_reports_throttle_reasons():
