@@ -35,7 +35,7 @@
  *   - Weights, caches and workspaces are allocated by st_create, st_kv_alloc and
  *     st_reserve; st_kv_build / st_kv_retain / st_op_eval allocate only when the
  *     context's workspace must grow (never after st_reserve with the largest
- *     sizes used).
+ *     sizes used), and never when the caller provides it (st_set_workspace).
  */
 #ifndef STRETTO_H
 #define STRETTO_H
@@ -125,6 +125,32 @@ const char* st_version(void);
  * document tokens and op_eval batches of up to `eval_rows` prompt rows
  * (tuples * P), so that later calls allocate nothing. */
 int st_reserve(st_ctx* ctx, int64_t build_rows, int64_t eval_rows);
+
+/* Caller-owned activation workspace (the boundary keeps no hidden device
+ * allocation on the hot path when the caller provides it).
+ *
+ * st_workspace_size: bytes of device workspace that one chunk of `rows` rows
+ * needs -- which = ST_WS_BUILD: st_kv_build over chunks of up to `rows`
+ * document tokens (a document longer than that is one chunk of its own
+ * length); ST_WS_EVAL: st_op_eval / st_op_eval_multi / st_map_eval over chunks
+ * of up to `rows` prompt rows (tuples x P).  Returns 0 for a bad argument.
+ *
+ * st_set_workspace: from now on the context carves that workspace out of the
+ * caller's device buffer `dev` of `bytes` bytes (256-byte aligned) instead of
+ * allocating its own; the library's own buffer of that kind is freed (which
+ * waits for the device).  The buffer is caller-owned: it must stay valid until
+ * it is replaced, reset with dev = NULL, bytes = 0 (back to library-owned
+ * workspace), or the context is destroyed; the library never frees it.  Calls
+ * of the context must not overlap on the GPU (they share it).  A call whose
+ * chunk needs more than `bytes` fails with ST_ENOMEM before launching
+ * anything; st_reserve fixes the chunk sizes (its own allocation then fails
+ * with ST_ENOMEM too if the caller's buffer is smaller).
+ * Errors: ST_EINVAL (which, alignment, or dev / bytes not both set or both
+ * zero). */
+#define ST_WS_BUILD 0
+#define ST_WS_EVAL 1
+size_t st_workspace_size(const st_ctx* ctx, int which, int64_t rows);
+int st_set_workspace(st_ctx* ctx, int which, void* dev, size_t bytes);
 
 /* ---- KV caches ---- */
 

@@ -48,6 +48,9 @@ int dev_alloc(st_ctx* ctx, void** p, size_t bytes) {
 
 int grow(st_ctx* ctx, DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes) return ST_OK;
+  if (b.external)
+    return fail(ctx, ST_ENOMEM, "the workspace given to st_set_workspace holds " + std::to_string(b.bytes) +
+                                    " bytes, this call needs " + std::to_string(bytes));
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -379,8 +382,8 @@ extern "C" void st_destroy(st_ctx* ctx) {
   cudaFree(ctx->rope);
   cudaFree(ctx->rope_t);
   cudaFree(ctx->dstatus);
-  cudaFree(ctx->ws_build.p);
-  cudaFree(ctx->ws_eval.p);
+  if (!ctx->ws_build.external) cudaFree(ctx->ws_build.p);
+  if (!ctx->ws_eval.external) cudaFree(ctx->ws_eval.p);
   cudaFree(ctx->ws_casc.p);
   cudaFree(ctx->ws_map.p);
   cudaFree(ctx->ws_score.p);
@@ -403,6 +406,27 @@ extern "C" int st_reserve(st_ctx* ctx, int64_t build_rows, int64_t eval_rows) {
     ctx->eval_rows_cap = eval_rows;
     RC(grow(ctx, ctx->ws_eval, eval_bufs(ctx, eval_rows, eval_rows, nullptr, nullptr)));
   }
+  return ST_OK;
+}
+
+extern "C" size_t st_workspace_size(const st_ctx* ctx, int which, int64_t rows) {
+  if (!ctx || rows <= 0) return 0;
+  // a chunk of `rows` rows holds at most `rows` tuples (build) or pairs (eval)
+  if (which == ST_WS_BUILD) return build_ws_bytes(ctx, rows, rows, nullptr, nullptr);
+  if (which == ST_WS_EVAL) return eval_bufs(ctx, rows, rows, nullptr, nullptr);
+  return 0;
+}
+
+extern "C" int st_set_workspace(st_ctx* ctx, int which, void* dev, size_t bytes) {
+  if (!ctx || (which != ST_WS_BUILD && which != ST_WS_EVAL) || (dev == nullptr) != (bytes == 0) ||
+      (reinterpret_cast<uintptr_t>(dev) & 255u))
+    return fail(ctx, ST_EINVAL, "st_set_workspace: bad argument (which, a 256-byte aligned pointer and its size, "
+                                "or NULL and 0)");
+  DevBuf& b = which == ST_WS_BUILD ? ctx->ws_build : ctx->ws_eval;
+  if (!b.external && b.p) cudaFree(b.p);   // the library's own buffer (waits for its users)
+  b.p = dev;
+  b.bytes = bytes;
+  b.external = dev != nullptr;
   return ST_OK;
 }
 

@@ -116,6 +116,7 @@ struct LayerW {
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool external = false;   // caller-owned (st_set_workspace): never grown or freed here
 };
 
 struct ProfRec {

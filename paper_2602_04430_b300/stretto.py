@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libstretto.so")
 ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ENAN, ST_EUNSUPPORTED = range(7)
 ST_SCORE_EA_LITE, ST_SCORE_EA_FULL = 0, 1
 ST_F32, ST_BF16, ST_E4M3 = 0, 1, 2
+ST_WS_BUILD, ST_WS_EVAL = 0, 1
 ST_OP_FILTER, ST_OP_CLASSIFY = 0, 1
 ST_REJECT, ST_ACCEPT, ST_UNSURE = 0, 1, 2
 (ST_VIEW_K, ST_VIEW_V, ST_VIEW_SCORES, ST_VIEW_POOLED, ST_VIEW_RANK, ST_VIEW_KR, ST_VIEW_VR,
@@ -84,6 +85,8 @@ def lib() -> ctypes.CDLL:
         "st_last_error": (ctypes.c_char_p, [VP]),
         "st_version": (ctypes.c_char_p, []),
         "st_reserve": (i32, [VP, i64, i64]),
+        "st_workspace_size": (sz, [VP, i32, i64]),
+        "st_set_workspace": (i32, [VP, i32, VP, sz]),
         "st_kv_alloc": (i32, [VP, ctypes.POINTER(i64), i32, ctypes.POINTER(VP)]),
         "st_kv_free": (None, [VP]),
         "st_kv_build": (i32, [VP, VP, VP, VP]),
@@ -197,6 +200,23 @@ class Model:
 
     def reserve(self, build_rows: int = 0, eval_rows: int = 0):
         self.check(self.L.st_reserve(self.h, int(build_rows), int(eval_rows)))
+
+    def workspace_size(self, which: int, rows: int) -> int:
+        """Bytes of device workspace one chunk of ``rows`` rows needs (ST_WS_BUILD / ST_WS_EVAL)."""
+        return int(self.L.st_workspace_size(self.h, int(which), int(rows)))
+
+    def set_workspace(self, which: int, buf=None):
+        """Carve that workspace out of the caller's device tensor ``buf`` (kept alive
+        here until replaced), or go back to library-owned workspace with None."""
+        if not hasattr(self, "_ws_keep"):
+            self._ws_keep = {}
+        if buf is None:
+            self.check(self.L.st_set_workspace(self.h, int(which), None, 0))
+            self._ws_keep.pop(int(which), None)
+            return
+        nbytes = buf.numel() * buf.element_size()
+        self.check(self.L.st_set_workspace(self.h, int(which), _ptr(buf), nbytes))
+        self._ws_keep[int(which)] = buf
 
     def selftest_wait(self, limit_cycles: int = 1000000, stream=None):
         """Run the bounded-wait failure self-test (its time-out shows in status())."""

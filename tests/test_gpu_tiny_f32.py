@@ -211,3 +211,52 @@ def test_kv_alloc_validates_offsets(run):
             model.kv_alloc(np.asarray(off, dtype=np.int64))
         assert ei.value.code == stretto.ST_EINVAL, off
     model.kv_alloc(np.asarray([0, 1, 511], dtype=np.int64)).close()
+
+
+def test_caller_owned_workspace():
+    """st_workspace_size / st_set_workspace: with caller-owned build and eval
+    workspaces sized for st_reserve's chunks, kv_build + retain + op_eval give
+    the same results bit for bit as with library-owned workspace; a workspace
+    too small for a chunk is refused with ST_ENOMEM before anything runs; NULL
+    returns to library-owned workspace; a misaligned buffer is rejected."""
+    import torch
+    from paper_2602_04430_b300 import build, stretto, synth
+    build.build()
+    cfg = synth.MODELS["tiny_f32"]
+    w = synth.make_weights(cfg, seed=91)
+    table = synth.make_table(synth.TABLES["tiny"], cfg.vocab, seed=92, n_tuples=16)
+    tok = torch.from_numpy(table["tokens"]).cuda()
+    op_np = synth.make_prompt(16, cfg.vocab, seed=93, r=0.5)
+
+    def run_model(caller_ws):
+        m = stretto.Model(cfg, w, max_pos=512)
+        m.reserve(build_rows=1024, eval_rows=128)     # 4 build chunks, 2 eval chunks
+        if caller_ws:
+            bb = m.workspace_size(stretto.ST_WS_BUILD, 1024)
+            eb = m.workspace_size(stretto.ST_WS_EVAL, 128)
+            assert bb > 0 and eb > 0
+            m.set_workspace(stretto.ST_WS_BUILD, torch.empty(bb, dtype=torch.uint8, device="cuda"))
+            m.set_workspace(stretto.ST_WS_EVAL, torch.empty(eb, dtype=torch.uint8, device="cuda"))
+        kv = m.kv_alloc(table["offsets"])
+        kv.build(tok)
+        kv.retain(0.5)
+        op = m.operator(op_np)
+        lg, lb = op.eval(kv, torch.arange(kv.T, dtype=torch.int32, device="cuda"))
+        torch.cuda.synchronize()
+        m.status()
+        return m, kv, lg.clone(), lb.clone()
+
+    _, _, lg0, lb0 = run_model(False)
+    m, kv, lg1, lb1 = run_model(True)
+    assert torch.equal(lg0, lg1) and torch.equal(lb0, lb1)
+    m.set_workspace(stretto.ST_WS_BUILD, torch.empty(4096, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(stretto.StrettoError) as e:
+        kv.build(tok)
+    assert e.value.code == stretto.ST_ENOMEM
+    m.set_workspace(stretto.ST_WS_BUILD, None)
+    kv.build(tok)
+    torch.cuda.synchronize()
+    m.status()
+    with pytest.raises(stretto.StrettoError) as e:
+        m.set_workspace(stretto.ST_WS_EVAL, torch.empty(1024, dtype=torch.uint8, device="cuda")[1:])
+    assert e.value.code == stretto.ST_EINVAL
