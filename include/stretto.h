@@ -262,6 +262,18 @@ int st_kv_profile_bytes(const st_kv* kv, size_t* bytes);
 int st_kv_export(st_ctx* ctx, const st_kv* kv, void* host, size_t bytes, void* stream);
 int st_kv_import(st_ctx* ctx, st_kv* kv, const void* host, size_t bytes, void* stream);
 
+/* The retained slot indices at a fraction r (paper Sec. 5: the retained set
+ * of each (tuple, layer, kv head) is the top n_keep(L, r) of its ranking):
+ * off_dev (int64 [T+1], caller DEVICE memory) receives the offsets, off[0] = 0
+ * and off[t+1] = off[t] + n_keep(L_t, r); idx_dev (int32 [layers][hkv][off[T]],
+ * caller DEVICE memory, or NULL for the offsets only) receives, for every
+ * (layer, kv head), each tuple's retained slot indices (0 .. L_t - 1) in rank
+ * order at idx[l][g][off[t] .. off[t+1]-1].  Any r in (0, 1] (the ranking
+ * covers each whole segment, so smaller r read prefixes: the sets are nested).
+ * Valid after st_kv_retain and until the next st_kv_build.  Enqueued on
+ * `stream`.  Errors: ST_EINVAL (r, no ranking yet, NULL off_dev). */
+int st_kv_indices(st_ctx* ctx, const st_kv* kv, double r, int32_t* idx_dev, int64_t* off_dev, void* stream);
+
 /* Device status of the last retain on `kv`: synchronises `stream`, returns
  * ST_OK or ST_ENAN (and clears it). */
 int st_kv_status(st_ctx* ctx, st_kv* kv, void* stream);

@@ -733,6 +733,28 @@ extern "C" int st_kv_retain(st_ctx* ctx, st_kv* kv, double r, int32_t kv_dtype, 
   return ST_OK;
 }
 
+extern "C" int st_kv_indices(st_ctx* ctx, const st_kv* kv, double r, int32_t* idx_dev, int64_t* off_dev,
+                             void* stream) {
+  ST_TRACE("st_kv_indices");
+  if (!ctx || !kv || kv->ctx != ctx || !off_dev) return fail(ctx, ST_EINVAL, "st_kv_indices: bad argument");
+  if (!(r > 0.0 && r <= 1.0)) return fail(ctx, ST_EINVAL, "st_kv_indices: r must lie in (0, 1]");
+  if (!kv->built || kv->r <= 0.0)
+    return fail(ctx, ST_EINVAL, "st_kv_indices: no ranking (st_kv_retain after st_kv_build)");
+  const st_model_cfg& c = ctx->cfg;
+  std::vector<int64_t> o(kv->T + 1, 0);
+  for (int t = 0; t < kv->T; ++t) o[t + 1] = o[t] + n_keep_host(kv->off_h[t + 1] - kv->off_h[t], r);
+  cudaStream_t s = S(stream);
+  // pageable source: the call returns once it has been staged
+  if (cudaMemcpyAsync(off_dev, o.data(), o.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(ctx, ST_ECUDA, std::string("st_kv_indices: ") + cudaGetErrorString(cudaGetLastError()));
+  if (idx_dev) {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    gather_indices(kv->rank, kv->off, off_dev, kv->T, c.layers * c.hkv, kv->R, o[kv->T], idx_dev, s);
+  }
+  CKLAUNCH();
+  return ST_OK;
+}
+
 extern "C" int st_kv_status(st_ctx* ctx, st_kv* kv, void* stream) {
   if (!ctx || !kv) return fail(ctx, ST_EINVAL, "st_kv_status: bad argument");
   int32_t h = 0;

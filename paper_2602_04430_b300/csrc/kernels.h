@@ -80,6 +80,10 @@ template <typename act_t>
 void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, int vocab, float* x, int* status,
                 cudaStream_t s);
 // BF16 model: the gather fused with the first layer's RMSNorm (xn in half).
+// st_kv_indices: the first n_t entries of every rank-ordered segment, compacted
+// at out_off (int64 [T+1]) into idx [layers * hkv][out_off[T]].
+void gather_indices(const int32_t* rank, const int64_t* doc_off, const int64_t* out_off, int T, int LH,
+                    int64_t R, int64_t Rn, int32_t* idx, cudaStream_t s);
 void embed_norm_rows(const int32_t* tok, int64_t rows, const bf16* E, int d, int vocab, float eps, float* x,
                      __half* xn, int* status, cudaStream_t s);
 template <typename act_t>

@@ -173,4 +173,24 @@ int retain(const RetainParams& p, cudaStream_t s) {
   return ST_OK;
 }
 
+// The retained slot indices of every (layer, kv head, tuple) at a fraction r,
+// compacted: the first n_t entries of the tuple's rank-ordered segment (the
+// ranking covers the whole segment, so every r reads a prefix of it).
+__global__ void k_gather_indices(const int32_t* __restrict__ rank, const int64_t* __restrict__ doc_off,
+                                 const int64_t* __restrict__ out_off, int64_t R, int64_t Rn,
+                                 int32_t* __restrict__ idx) {
+  const int t = blockIdx.x, lg = blockIdx.y;
+  const int64_t o = out_off[t];
+  const int n = (int)(out_off[t + 1] - o);
+  const int32_t* src = rank + (int64_t)lg * R + doc_off[t];
+  int32_t* dst = idx + (int64_t)lg * Rn + o;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
+}
+
+void gather_indices(const int32_t* rank, const int64_t* doc_off, const int64_t* out_off, int T, int LH,
+                    int64_t R, int64_t Rn, int32_t* idx, cudaStream_t s) {
+  if (T <= 0 || LH <= 0 || Rn <= 0) return;
+  k_gather_indices<<<dim3((unsigned)T, (unsigned)LH), 128, 0, s>>>(rank, doc_off, out_off, R, Rn, idx);
+}
+
 }  // namespace st

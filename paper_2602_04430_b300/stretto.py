@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "st_kv_free": (None, [VP]),
         "st_kv_build": (i32, [VP, VP, VP, VP]),
         "st_kv_retain": (i32, [VP, VP, dbl, i32, VP]),
+        "st_kv_indices": (i32, [VP, VP, dbl, VP, VP, VP]),
         "st_kv_status": (i32, [VP, VP, VP]),
         "st_status": (i32, [VP, VP]),
         "st_kv_view": (i32, [VP, i32, ctypes.POINTER(VP), ctypes.POINTER(sz)]),
@@ -296,6 +297,20 @@ class KVCache:
 
     def status(self, stream=None):
         self.model.check(self.L.st_kv_status(self.model.h, self.h, _stream(stream)))
+
+    def indices(self, r: float, stream=None):
+        """The retained slot indices at fraction r (st_kv_indices): returns
+        (idx int32 [layers, hkv, total], off int64 [T+1]) on the device; tuple t's
+        indices, in rank order, are idx[l, g, off[t]:off[t+1]]."""
+        import torch
+        cfg = self.model.cfg
+        off = torch.empty(self.T + 1, dtype=torch.int64, device="cuda")
+        self.model.check(self.L.st_kv_indices(self.model.h, self.h, float(r), None, _ptr(off), _stream(stream)))
+        total = int(off[-1].item())
+        idx = torch.empty((cfg.layers, cfg.hkv, max(total, 1)), dtype=torch.int32, device="cuda")
+        self.model.check(self.L.st_kv_indices(self.model.h, self.h, float(r), _ptr(idx), _ptr(off),
+                                              _stream(stream)))
+        return idx[:, :, :total], off
 
     def export_profile(self, stream=None) -> np.ndarray:
         """The current retained profile as a host byte array (``st_kv_export``)."""

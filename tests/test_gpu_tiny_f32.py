@@ -260,3 +260,44 @@ def test_caller_owned_workspace():
     with pytest.raises(stretto.StrettoError) as e:
         m.set_workspace(stretto.ST_WS_EVAL, torch.empty(1024, dtype=torch.uint8, device="cuda")[1:])
     assert e.value.code == stretto.ST_EINVAL
+
+
+def test_kv_indices_are_the_retained_sets(run):
+    """st_kv_indices: at r = 0.5, 0.25 and 1 the offsets are the prefix sums of
+    n_keep(L, r) and every (layer, kv head, tuple) lists its top n_keep slots by
+    (score desc, index asc) on the kernel's own scores, in that order; smaller r
+    gives prefixes (nested sets); before any retain the call is refused."""
+    import torch
+    from oracle import operator as O
+    from paper_2602_04430_b300 import stretto, synth
+    cfg, model = run["cfg"], run["model"]
+    table = synth.make_table_from_lengths([1, 2, 37, 64, 65, 200], cfg.vocab, seed=95)
+    kv = model.kv_alloc(table["offsets"])
+    kv.build(torch.from_numpy(table["tokens"]).cuda())
+    with pytest.raises(stretto.StrettoError) as e:
+        kv.indices(0.5)
+    assert e.value.code == stretto.ST_EINVAL
+    model.status()
+    kv.retain(0.5)
+    off_h = table["offsets"]
+    R = int(off_h[-1])
+    S = kv.read(stretto.ST_VIEW_SCORES, torch.float32, (cfg.layers, cfg.hkv, R)).cpu().numpy()
+    prev = None
+    for r in (1.0, 0.5, 0.25):
+        idx, off = kv.indices(r)
+        idx, off = idx.cpu().numpy(), off.cpu().numpy()
+        n = [O.n_keep(int(off_h[t + 1] - off_h[t]), r) for t in range(len(off_h) - 1)]
+        assert list(off) == [0] + list(np.cumsum(n))
+        for l in range(cfg.layers):
+            for g in range(cfg.hkv):
+                for t in range(len(n)):
+                    seg = S[l, g, off_h[t]:off_h[t + 1]]
+                    want = np.lexsort((np.arange(len(seg)), -seg))[:n[t]]
+                    got = idx[l, g, off[t]:off[t + 1]]
+                    assert np.array_equal(got, want)
+                    if prev is not None:
+                        p_idx, p_off = prev
+                        assert np.array_equal(got, p_idx[l, g, p_off[t]:p_off[t] + n[t]])
+        prev = (idx, off)
+    torch.cuda.synchronize()
+    model.status()
