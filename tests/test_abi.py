@@ -49,3 +49,14 @@ def test_version_and_error_without_gpu(libst):
 def test_library_is_sm103a_only():
     from paper_2602_04430_b300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_binding_covers_every_declared_function(libst):
+    """The Python binding declares a ctypes signature for every entry point of
+    the header, under the same name, and for nothing else."""
+    from paper_2602_04430_b300 import stretto
+    src = open(stretto.__file__).read()
+    bound = set(re.findall(r'"(st_[a-z0-9_]+)":\s*\(', src))
+    assert bound == set(declared_functions())
+    for name in bound:
+        assert getattr(libst, name).argtypes is not None
