@@ -301,3 +301,36 @@ def test_kv_indices_are_the_retained_sets(run):
         prev = (idx, off)
     torch.cuda.synchronize()
     model.status()
+
+
+def test_operator_arguments_are_validated(run):
+    """st_op_create refuses, with ST_EINVAL and without touching the device,
+    prompt or label ids outside [0, vocab), an empty or over-long prompt, r
+    outside (0, 1], and label counts other than 2 (filter) or 2..8
+    (classify); the context keeps working afterwards."""
+    import dataclasses
+    import torch
+    from paper_2602_04430_b300 import stretto, synth
+    cfg, model, kv = run["cfg"], run["model"], run["kv"]
+    good = synth.make_prompt(16, cfg.vocab, seed=97, label_ids=(1, 0), r=1.0)
+    bad = [
+        dataclasses.replace(good, prompt=good.prompt[:-1] + (cfg.vocab,)),
+        dataclasses.replace(good, prompt=(-1,) + good.prompt[1:]),
+        dataclasses.replace(good, label_ids=(1, cfg.vocab)),
+        dataclasses.replace(good, prompt=()),
+        dataclasses.replace(good, prompt=tuple(range(257))),
+        dataclasses.replace(good, r=0.0),
+        dataclasses.replace(good, r=1.5),
+        dataclasses.replace(good, label_ids=(1, 0, 2)),
+        dataclasses.replace(good, kind="classify", label_ids=tuple(range(9)), bias=None),
+        dataclasses.replace(good, kind="classify", label_ids=(3,), bias=None),
+    ]
+    for op in bad:
+        with pytest.raises(stretto.StrettoError) as e:
+            model.operator(op)
+        assert e.value.code == stretto.ST_EINVAL
+    kv.retain(1.0)
+    lg, _ = model.operator(good).eval(kv, torch.arange(kv.T, dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    model.status()
+    assert bool(torch.isfinite(lg).all())
