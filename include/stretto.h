@@ -526,6 +526,15 @@ int st_cascade_merge(st_ctx* ctx, const int32_t* proxy_label_dev, int32_t n,
                      const int32_t* full_label_dev, int32_t* out_dev, void* stream);
 /* Copy one of the ST_PROXY_* buffers (float32, ST_PROXY_PARAMS layout) to DEVICE memory. */
 int st_proxy_read(const st_proxy* p, int32_t which, void* dst_dev, size_t bytes, void* stream);
+/* Checkpoint / resume of training: st_proxy_steps returns the Adam steps taken
+ * (-1 for NULL); st_proxy_restore sets the parameters and both Adam moments
+ * from caller DEVICE buffers (float32, ST_PROXY_PARAMS layout, n_params each,
+ * as st_proxy_read writes them) and the step count, so that the next
+ * st_proxy_train_step continues exactly where the saved proxy stopped.
+ * Enqueued on `stream`.  Errors: ST_EINVAL (NULL buffer, steps < 0). */
+int64_t st_proxy_steps(const st_proxy* p);
+int st_proxy_restore(st_proxy* p, const float* params_dev, const float* m_dev, const float* v_dev,
+                     int64_t steps, void* stream);
 
 /* ---- kernel self-test entry ---- */
 

@@ -425,6 +425,22 @@ extern "C" int st_cascade_merge(st_ctx* ctx, const int32_t* proxy_label_dev, int
   return ST_OK;
 }
 
+extern "C" int64_t st_proxy_steps(const st_proxy* p) { return p ? p->t : -1; }
+
+extern "C" int st_proxy_restore(st_proxy* p, const float* params_dev, const float* m_dev, const float* v_dev,
+                                int64_t steps, void* stream) {
+  if (!p || !params_dev || !m_dev || !v_dev || steps < 0)
+    return pfail(p ? p->ctx : nullptr, ST_EINVAL, "st_proxy_restore: bad argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)p->n_params * sizeof(float);
+  if (cudaMemcpyAsync(p->params, params_dev, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p->m, m_dev, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p->v, v_dev, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return pfail(p->ctx, ST_ECUDA, "st_proxy_restore: copy failed");
+  p->t = steps;
+  return ST_OK;
+}
+
 extern "C" int st_proxy_read(const st_proxy* p, int32_t which, void* dst_dev, size_t bytes,
                              void* stream) {
   if (!p || !dst_dev) return ST_EINVAL;

@@ -132,6 +132,8 @@ def lib() -> ctypes.CDLL:
         "st_proxy_eval": (i32, [VP, VP, VP, VP, i32, VP, VP, VP]),
         "st_cascade_compact": (i32, [VP, VP, VP, i32, ctypes.c_float, VP, VP, VP]),
         "st_cascade_merge": (i32, [VP, VP, i32, VP, VP, VP, VP, VP]),
+        "st_proxy_steps": (i64, [VP]),
+        "st_proxy_restore": (i32, [VP, VP, VP, VP, i64, VP]),
         "st_proxy_read": (i32, [VP, i32, VP, sz, VP]),
         "st_prof_enable": (i32, [VP, i32]),
         "st_prof_read": (i32, [VP, ctypes.POINTER(dbl)]),
@@ -476,6 +478,27 @@ class Proxy:
                                               _ptr(rows) if rows is not None else None, n,
                                               _ptr(conf), _ptr(label), _stream(stream)))
         return conf, label
+
+    def steps(self) -> int:
+        """Adam steps taken (st_proxy_steps)."""
+        return int(self.L.st_proxy_steps(self.h))
+
+    def state(self):
+        """The training state for a checkpoint: flat device copies of the
+        parameters and Adam moments, and the step count."""
+        import torch
+        n = sum(self.sizes)
+        out = {}
+        for name, which in (("params", ST_PROXY_PARAMS), ("m", ST_PROXY_ADAM_M), ("v", ST_PROXY_ADAM_V)):
+            out[name] = torch.empty(n, dtype=torch.float32, device="cuda")
+            self.model.check(self.L.st_proxy_read(self.h, which, _ptr(out[name]), n * 4, _stream()))
+        out["steps"] = self.steps()
+        return out
+
+    def restore(self, state, stream=None):
+        """Resume from ``state()`` of a proxy of the same shape (st_proxy_restore)."""
+        self.model.check(self.L.st_proxy_restore(self.h, _ptr(state["params"]), _ptr(state["m"]),
+                                                  _ptr(state["v"]), int(state["steps"]), _stream(stream)))
 
     def read(self, which: int) -> Dict[str, np.ndarray]:
         import torch

@@ -99,3 +99,31 @@ def test_cascade_routing_bit_exact(setup, tau):
     torch.cuda.synchronize()
     ref, unsure = PX.cascade(plab, conf, np.float32(tau), full)
     np.testing.assert_array_equal(merged.cpu().numpy(), ref)
+
+
+def test_training_resumes_from_a_checkpoint(setup):
+    """st_proxy_steps / st_proxy_restore: a fresh proxy restored from another's
+    state (parameters, Adam moments, step count) after 5 steps continues
+    exactly: the next 3 steps give both the same parameters bit for bit."""
+    torch, stretto, synth = setup["torch"], setup["stretto"], setup["synth"]
+    x, y = setup["x"], setup["y"]
+    batches = synth.minibatches(len(x), 256, 1, seed=11)[:8]
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    a = stretto.Proxy(setup["model"], setup["params"])
+    for b in batches[:5]:
+        a.train_step(xd, yd, torch.from_numpy(b).cuda(), lr=1e-3)
+    state = a.state()
+    assert state["steps"] == 5
+    c = stretto.Proxy(setup["model"], setup["params"])
+    assert c.steps() == 0
+    c.restore(state)
+    assert c.steps() == 5
+    for b in batches[5:]:
+        bd = torch.from_numpy(b).cuda()
+        a.train_step(xd, yd, bd, lr=1e-3)
+        c.train_step(xd, yd, bd, lr=1e-3)
+    torch.cuda.synchronize()
+    pa, pc = a.read(stretto.ST_PROXY_PARAMS), c.read(stretto.ST_PROXY_PARAMS)
+    for k in pa:
+        assert np.array_equal(pa[k], pc[k]), k
+    assert a.steps() == c.steps() == 8
