@@ -1,0 +1,208 @@
+"""The oracle over many tuples in parallel host processes (test infrastructure only).
+
+Tuples are independent (each has its own document, cache and decision), so the
+float64 oracle parallelises over them without changing any arithmetic: every
+number still comes from ``oracle.operator``.  Worker processes are started with
+the ``spawn`` method (safe after the parent has initialised CUDA) and run one
+BLAS thread each; they map the model's weights from ``.npy`` files the parent
+writes once, so a large model is held in host memory once, not per worker.
+
+Only ``tests/`` and the CPU legs of ``bench.py`` use this module.
+"""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+import shutil
+import tempfile
+import time
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_W = None
+_CFG = None
+
+
+def n_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _save_weights(w: dict, root: str):
+    np.save(os.path.join(root, "embed.npy"), np.asarray(w["embed"], dtype=np.float32))
+    np.save(os.path.join(root, "w_lm.npy"), np.asarray(w["w_lm"], dtype=np.float32))
+    for l, lw in enumerate(w["layers"]):
+        for k, a in lw.items():
+            np.save(os.path.join(root, f"l{l}_{k}.npy"), np.asarray(a, dtype=np.float32))
+    return len(w["layers"])
+
+
+def _init(cfg, root: str, layers: int):
+    global _W, _CFG
+    try:
+        from threadpoolctl import threadpool_limits
+        threadpool_limits(1)
+    except Exception:
+        pass
+    ld = lambda name: np.load(os.path.join(root, name + ".npy"), mmap_mode="r")
+    keys = ("wq", "wk", "wv", "wo", "wg", "wu", "wd")
+    _W = {"embed": ld("embed"), "w_lm": ld("w_lm"),
+          "layers": [{k: ld(f"l{l}_{k}") for k in keys} for l in range(layers)]}
+    _CFG = cfg
+
+
+def _run_one(task):
+    """One tuple: its float64 cache, then every requested operator evaluation.
+
+    task = (key, tokens, ops, want_scores) with ops a list of dicts
+    {prompt, label_ids, r, kv_fp8, idx (optional [l][g] index lists)}.
+    Returns (key, result dict)."""
+    from . import operator as O
+    key, tokens, ops, want_scores = task
+    t0 = time.perf_counter()
+    c = O.kv_build(_CFG, _W, tokens)
+    t1 = time.perf_counter()
+    out = {"L": c.L, "logits": [], "idx": [], "build_s": t1 - t0}
+    for o in ops:
+        Kr, Vr, idx = O.retained_kv(c, o["r"], idx=o.get("idx"), kv_fp8=o.get("kv_fp8", False))
+        out["logits"].append(O.op_eval(_CFG, _W, c.L, Kr, Vr, o["prompt"], o["label_ids"]))
+        out["idx"].append([[np.asarray(i, dtype=np.int32) for i in row] for row in idx])
+    out["eval_s"] = time.perf_counter() - t1
+    if want_scores:
+        out["scores"] = np.array([[np.asarray(s) for s in row] for row in c.scores])
+        out["pooled"] = c.pooled
+    return key, out
+
+
+class OraclePool:
+    """A pool of oracle worker processes for one model."""
+
+    def __init__(self, cfg, weights: dict, workers: Optional[int] = None):
+        self.workers = max(1, int(workers or n_cores()))
+        self.root = tempfile.mkdtemp(prefix="oracle_w_")
+        layers = _save_weights(weights, self.root)
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.workers, initializer=_init, initargs=(cfg, self.root, layers))
+
+    def run(self, docs: Dict[object, np.ndarray], ops: Sequence[dict], want_scores: bool = False,
+            idx: Optional[Dict[object, List]] = None):
+        """Evaluate ``ops`` on every document of ``docs`` ({key: tokens}); longest
+        documents first.  ``idx[key][op]``, if given, overrides the retained index
+        sets of that tuple.  Returns {key: result}."""
+        order = sorted(docs, key=lambda k: -len(docs[k]))
+        tasks = []
+        for k in order:
+            o_k = [dict(o) for o in ops]
+            if idx is not None:
+                for j, o in enumerate(o_k):
+                    if idx[k][j] is not None:
+                        o["idx"] = idx[k][j]
+            tasks.append((k, np.asarray(docs[k], dtype=np.int64), o_k, want_scores))
+        return dict(self.pool.imap_unordered(_run_one, tasks, chunksize=1))
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+        shutil.rmtree(self.root, ignore_errors=True)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _worker_main(conn, cfg, root: str, layers: int):
+    """A persistent oracle worker: holds one tuple's cache between commands, so
+    that repeated evaluations time the operator with the cache resident (as the
+    GPU path times it)."""
+    from . import operator as O
+    from . import proxy as PX
+    _init(cfg, root, layers)
+    cache, proxy_params = None, None
+    while True:
+        msg = conn.recv()
+        kind = msg[0]
+        if kind == "stop":
+            break
+        if kind == "build":
+            t0 = time.perf_counter()
+            cache = O.kv_build(_CFG, _W, np.asarray(msg[1], dtype=np.int64))
+            conn.send(("built", time.perf_counter() - t0, cache.L))
+        elif kind == "proxy":
+            proxy_params = msg[1]
+            conn.send(("ok",))
+        elif kind == "eval":
+            o = msg[1]
+            t0 = time.perf_counter()
+            if proxy_params is not None:
+                PX.forward(proxy_params, cache.pooled[None, :])
+            Kr, Vr, _ = O.retained_kv(cache, o["r"], kv_fp8=o.get("kv_fp8", False))
+            z = O.op_eval(_CFG, _W, cache.L, Kr, Vr, o["prompt"], o["label_ids"])
+            conn.send(("done", time.perf_counter() - t0, np.asarray(z)))
+
+
+class OracleWorkers:
+    """One persistent oracle process per core, each holding one tuple's cache.
+
+    ``build(docs)`` sends one document to each worker (asynchronously; the
+    caches are built while the caller does other work), ``wait_built()``
+    collects the build times, and ``step(op)`` makes every worker evaluate the
+    operator on its cache once and returns the wall time of that step."""
+
+    def __init__(self, cfg, weights: dict, workers: Optional[int] = None):
+        self.n = max(1, int(workers or n_cores()))
+        self.root = tempfile.mkdtemp(prefix="oracle_w_")
+        layers = _save_weights(weights, self.root)
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for _ in range(self.n):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_worker_main, args=(b, cfg, self.root, layers), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        self.built = False
+
+    def build(self, docs: Sequence[np.ndarray]):
+        assert len(docs) == self.n
+        for c, d in zip(self.conns, docs):
+            c.send(("build", np.asarray(d, dtype=np.int64)))
+
+    def wait_built(self):
+        out = [c.recv() for c in self.conns]
+        self.built = True
+        return [o[1] for o in out], [o[2] for o in out]
+
+    def set_proxy(self, params: dict):
+        for c in self.conns:
+            c.send(("proxy", params))
+        for c in self.conns:
+            c.recv()
+
+    def step(self, op: dict):
+        """Every worker evaluates ``op`` once; returns (wall seconds, per-worker logits)."""
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(("eval", op))
+        res = [c.recv() for c in self.conns]
+        return time.perf_counter() - t0, [r[2] for r in res]
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.terminate()
+        self.conns, self.procs = [], []
+        shutil.rmtree(self.root, ignore_errors=True)

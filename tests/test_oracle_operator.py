@@ -265,3 +265,56 @@ def test_map_eval_cached_equals_from_scratch():
         assert all(0 <= t < cfg.vocab for t in toks)
         # every token is the argmax of its step's logits
         assert all(int(np.argmax(z)) == t for z, t in zip(logs, toks))
+
+
+def test_oracle_pool_matches_serial_oracle():
+    """The parallel runner adds no arithmetic: its logits, retained sets and
+    scores equal serial oracle calls (up to BLAS summation order)."""
+    from oracle import pool as OP
+    cfg = synth.ModelConfig(layers=2, d=32, hq=4, hkv=2, hd=8, ffn=48, vocab=64, dtype="f32", name="p")
+    w = synth.make_weights(cfg, seed=41, std=0.2)
+    table = synth.make_table_from_lengths([5, 17, 33], cfg.vocab, seed=42)
+    op = synth.make_prompt(4, cfg.vocab, seed=43, r=0.5)
+    docs = {t: table["tokens"][table["offsets"][t]:table["offsets"][t + 1]] for t in range(3)}
+    ops = [{"prompt": op.prompt, "label_ids": op.label_ids, "r": 0.5},
+           {"prompt": op.prompt, "label_ids": op.label_ids, "r": 1.0, "kv_fp8": True}]
+    with OP.OraclePool(cfg, w, workers=2) as pool:
+        res = pool.run(docs, ops, want_scores=True)
+    for t, doc in docs.items():
+        c = O.kv_build(cfg, w, doc)
+        for j, o in enumerate(ops):
+            Kr, Vr, idx = O.retained_kv(c, o["r"], kv_fp8=o.get("kv_fp8", False))
+            z = O.op_eval(cfg, w, c.L, Kr, Vr, op.prompt, op.label_ids)
+            np.testing.assert_allclose(res[t]["logits"][j], z, rtol=1e-12, atol=1e-12)
+            for l in range(cfg.layers):
+                for g in range(cfg.hkv):
+                    np.testing.assert_array_equal(res[t]["idx"][j][l][g], idx[l][g])
+                    np.testing.assert_allclose(res[t]["scores"][l][g], c.scores[l][g], rtol=1e-12)
+
+
+def test_oracle_workers_hold_a_cache_and_match_serial_oracle():
+    """Persistent workers (the benchmark's CPU legs): each builds one tuple's
+    cache, then every step evaluates the operator on it; the logits equal a
+    serial oracle run."""
+    from oracle import pool as OP
+    cfg = synth.ModelConfig(layers=2, d=32, hq=4, hkv=2, hd=8, ffn=48, vocab=64, dtype="f32", name="p")
+    w = synth.make_weights(cfg, seed=44, std=0.2)
+    table = synth.make_table_from_lengths([9, 23], cfg.vocab, seed=45)
+    op = synth.make_prompt(4, cfg.vocab, seed=46, r=0.5)
+    o = {"prompt": op.prompt, "label_ids": op.label_ids, "r": 0.5}
+    docs = [table["tokens"][table["offsets"][t]:table["offsets"][t + 1]] for t in range(2)]
+    wk = OP.OracleWorkers(cfg, w, workers=2)
+    try:
+        wk.build(docs)
+        secs, lens = wk.wait_built()
+        assert lens == [9, 23]
+        for _ in range(2):
+            dt, zs = wk.step(o)
+            assert dt > 0
+            for doc, z in zip(docs, zs):
+                c = O.kv_build(cfg, w, doc)
+                Kr, Vr, _ = O.retained_kv(c, 0.5)
+                np.testing.assert_allclose(z, O.op_eval(cfg, w, c.L, Kr, Vr, op.prompt, op.label_ids),
+                                           rtol=1e-12, atol=1e-12)
+    finally:
+        wk.close()
