@@ -10,7 +10,10 @@ uses an embedding filter as its cheap first stage; this proxy plays that role.
 
 Network: ``Linear(d_in, h1) - GELU - Linear(h1, h2) - GELU - Linear(h2, 2)``,
 GELU in its erf form, softmax cross-entropy averaged over the batch, Adam with
-bias correction.  Parameters are ``W [out][in]`` and ``b [out]``.
+bias correction.  Parameters are ``W [out][in]`` and ``b [out]``.  Two
+precisions: exact contractions, and BF16 contractions with exact accumulation
+(the learned-proxy configuration's "BF16, FP32 accum": every matrix product
+reads its operands rounded to bfloat16; ``bf=True``).
 """
 from __future__ import annotations
 
@@ -32,14 +35,37 @@ def gelu_grad(x):
     return 0.5 * (1.0 + erf(x / _SQRT2)) + x * _INV_SQRT_2PI * np.exp(-0.5 * x * x)
 
 
-def forward(params: Dict[str, np.ndarray], x: np.ndarray):
-    """Returns (logits [B, 2], cache of pre-activations for backward)."""
+def bf16(x):
+    """Round to the nearest bfloat16 value (ties to even), returned in float64.
+
+    bfloat16 keeps the sign, the 8 exponent bits and the top 7 mantissa bits of
+    an IEEE single: the value is first rounded to single precision, then its
+    low 16 bits are rounded away (half-way cases to the even upper half)."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = ((u + 0x7FFF + lsb) >> 16) << 16
+    out = u.astype(np.uint32).view(np.float32).astype(F64)
+    return np.where(np.isfinite(f), out, f.astype(F64))
+
+
+def _op(a, bf):
+    """A contraction operand: as given, or rounded to bfloat16 (BF16 contractions)."""
+    return bf16(a) if bf else np.asarray(a, dtype=F64)
+
+
+def forward(params: Dict[str, np.ndarray], x: np.ndarray, bf: bool = False):
+    """Returns (logits [B, 2], cache of pre-activations for backward).
+
+    ``bf``: every contraction reads its two operands rounded to bfloat16 (the
+    weights, the input and the GELU outputs); bias, GELU and accumulation stay
+    exact."""
     x = np.asarray(x, dtype=F64)
-    a1 = x @ params["w1"].T.astype(F64) + params["b1"].astype(F64)
+    a1 = _op(x, bf) @ _op(params["w1"], bf).T + params["b1"].astype(F64)
     h1 = gelu(a1)
-    a2 = h1 @ params["w2"].T.astype(F64) + params["b2"].astype(F64)
+    a2 = _op(h1, bf) @ _op(params["w2"], bf).T + params["b2"].astype(F64)
     h2 = gelu(a2)
-    z = h2 @ params["w3"].T.astype(F64) + params["b3"].astype(F64)
+    z = _op(h2, bf) @ _op(params["w3"], bf).T + params["b3"].astype(F64)
     return z, (x, a1, h1, a2, h2)
 
 
@@ -49,10 +75,14 @@ def softmax(z):
     return e / e.sum(axis=1, keepdims=True)
 
 
-def loss_and_grads(params, x, y):
-    """Mean softmax cross-entropy against integer labels y in {0, 1}, and its gradients."""
+def loss_and_grads(params, x, y, bf: bool = False):
+    """Mean softmax cross-entropy against integer labels y in {0, 1}, and its gradients.
+
+    ``bf``: BF16 contractions, forward and backward -- each product's two
+    operands (activation, weight or gradient) rounded to bfloat16; the bias
+    gradients (column sums) and the GELU derivative stay exact."""
     y = np.asarray(y, dtype=np.int64)
-    z, (x, a1, h1, a2, h2) = forward(params, x)
+    z, (x, a1, h1, a2, h2) = forward(params, x, bf)
     B = z.shape[0]
     p = softmax(z)
     loss = -np.mean(np.log(p[np.arange(B), y]))
@@ -60,15 +90,15 @@ def loss_and_grads(params, x, y):
     dz[np.arange(B), y] -= 1.0
     dz /= B
     g = {}
-    g["w3"] = dz.T @ h2
+    g["w3"] = _op(dz, bf).T @ _op(h2, bf)
     g["b3"] = dz.sum(axis=0)
-    dh2 = dz @ params["w3"].astype(F64)
+    dh2 = _op(dz, bf) @ _op(params["w3"], bf)
     da2 = dh2 * gelu_grad(a2)
-    g["w2"] = da2.T @ h1
+    g["w2"] = _op(da2, bf).T @ _op(h1, bf)
     g["b2"] = da2.sum(axis=0)
-    dh1 = da2 @ params["w2"].astype(F64)
+    dh1 = _op(da2, bf) @ _op(params["w2"], bf)
     da1 = dh1 * gelu_grad(a1)
-    g["w1"] = da1.T @ x
+    g["w1"] = _op(da1, bf).T @ _op(x, bf)
     g["b1"] = da1.sum(axis=0)
     return loss, g
 
@@ -94,21 +124,21 @@ class Adam:
         return params
 
 
-def train(params, x, y, batches: List[np.ndarray], lr=1e-3):
+def train(params, x, y, batches: List[np.ndarray], lr=1e-3, bf: bool = False):
     """Adam over the given mini-batches (index arrays into x, y); returns params, losses."""
     params = {k: np.asarray(v, dtype=F64).copy() for k, v in params.items()}
     opt = Adam(params, lr=lr)
     losses = []
     for bi in batches:
-        loss, g = loss_and_grads(params, x[bi], y[bi])
+        loss, g = loss_and_grads(params, x[bi], y[bi], bf)
         params = opt.step(params, g)
         losses.append(loss)
     return params, np.array(losses)
 
 
-def confidence_and_label(params, x):
+def confidence_and_label(params, x, bf: bool = False):
     """Confidence = max softmax probability; proxy label = its argmax (ties -> 0)."""
-    z, _ = forward(params, x)
+    z, _ = forward(params, x, bf)
     p = softmax(z)
     return p.max(axis=1), np.argmax(p, axis=1).astype(np.int32)
 

@@ -9,12 +9,15 @@
 //          are compacted, in order, into a list for the full operator; the
 //          final labels take the proxy's where it is confident.
 //
-// Everything is float32 with float32 accumulation: the network is ~2 MFLOP
-// per tuple, so the CUDA-core tiled GEMM below is nowhere near the path's
-// critical time, and float32 keeps the gradients comparable to the FP64
-// oracle at a 1e-4 level.
+// Precision (st_proxy_set_precision): float32 contractions on the CUDA cores
+// (default), or BF16 contractions on the tensor cores (mma.sync m16n8k16,
+// operands rounded to bfloat16, float32 accumulation -- the learned-proxy
+// configuration's precision).  Parameters, Adam moments, biases, GELU and the
+// loss are float32 either way.  The network is ~2 MFLOP per tuple, far from
+// the path's critical time in both.
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "kernels.h"
@@ -85,11 +88,97 @@ __global__ void __launch_bounds__(256) k_mm(const float* __restrict__ A, int64_t
   }
 }
 
+// The same contraction on the BF16 tensor-core path (the learned-proxy
+// configuration's precision): each operand element is rounded from float32 to
+// bfloat16 (nearest, ties to even) as it is staged in shared memory, and
+// mma.sync m16n8k16 accumulates in float32; the epilogue is k_mm's.
+// 64 x 64 tiles over K steps of 32, 4 warps of 32 x 32 (2 x 4 MMA tiles).
+constexpr int BM = 64, BK = 32, BKP = BK + 8;   // padded rows: conflict-free fragment loads
 template <int EPI>
-void mm(const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbn, int64_t sbk, int M,
+__global__ void __launch_bounds__(128) k_mm_bf16(const float* __restrict__ A, int64_t sam, int64_t sak,
+                                                 const float* __restrict__ B, int64_t sbn, int64_t sbk,
+                                                 int M, int N, int K, const float* __restrict__ bias,
+                                                 float* __restrict__ pre, float* __restrict__ C) {
+  __shared__ __align__(16) __nv_bfloat16 As[BM][BKP], Bs[BM][BKP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BM;
+  float acc[2][4][4] = {};
+  // stage one operand tile, walking the unit-stride index fastest (coalesced)
+  auto stage = [&](const float* X, int64_t s_row, int64_t s_k, int rows, int r0, int k0,
+                   __nv_bfloat16 (*S)[BKP]) {
+    const bool k_fast = s_k == 1;
+    for (int e = threadIdx.x; e < BM * BK; e += 128) {
+      const int i = k_fast ? e / BK : e % BM;
+      const int k = k_fast ? e % BK : e / BM;
+      const int gr = r0 + i, gk = k0 + k;
+      const float v = (gr < rows && gk < K) ? X[(int64_t)gr * s_row + (int64_t)gk * s_k] : 0.f;
+      S[i][k] = __float2bfloat16_rn(v);
+    }
+  };
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    stage(A, sam, sak, M, m0, k0, As);
+    stage(B, sbn, sbk, N, n0, k0, Bs);
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + g;
+        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t]);
+        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t]);
+        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t + 8]);
+        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + 8 * j + g;
+        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t]);
+        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = m0 + wm + 16 * i + g + (e >> 1) * 8;
+        const int n = n0 + wn + 8 * j + 2 * t + (e & 1);
+        if (m >= M || n >= N) continue;
+        float v = acc[i][j][e];
+        const int64_t o = (int64_t)m * N + n;
+        if (EPI == MM_BIAS || EPI == MM_BIAS_GELU) v += bias[n];
+        if (EPI == MM_BIAS_GELU) {
+          pre[o] = v;
+          v = gelu_f(v);
+        }
+        if (EPI == MM_DGELU) v *= gelu_grad_f(pre[o]);
+        C[o] = v;
+      }
+}
+
+template <int EPI>
+void mm(bool bf, const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbn, int64_t sbk, int M,
         int N, int K, const float* bias, float* pre, float* C, cudaStream_t s) {
   dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_mm<EPI><<<grid, 256, 0, s>>>(A, sam, sak, B, sbn, sbk, M, N, K, bias, pre, C);
+  if (bf)
+    k_mm_bf16<EPI><<<grid, 128, 0, s>>>(A, sam, sak, B, sbn, sbk, M, N, K, bias, pre, C);
+  else
+    k_mm<EPI><<<grid, 256, 0, s>>>(A, sam, sak, B, sbn, sbk, M, N, K, bias, pre, C);
 }
 
 __global__ void k_gather(const float* __restrict__ x, const int32_t* __restrict__ rows, int n,
@@ -213,6 +302,7 @@ struct st_proxy {
   float* v = nullptr;
   int64_t off[7] = {};       // offsets of the six tensors (+ end)
   int64_t t = 0;             // Adam steps taken
+  bool bf16 = false;         // contractions on the BF16 tensor-core path (st_proxy_set_precision)
   // activations of the largest batch seen
   float* ws = nullptr;
   int64_t ws_rows = 0;
@@ -220,7 +310,7 @@ struct st_proxy {
 
 namespace {
 
-int pfail(st_ctx* ctx, int code, const char* msg) {
+int pfail(st_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
   return code;
 }
@@ -265,15 +355,15 @@ void forward(st_proxy* p, const float* x, const int32_t* rows_idx, int n, Act& A
   }
   {
     Launch L(p->ctx, s, ST_PROF_OTHER, 2.0 * n * d * h1, 0);
-    mm<MM_BIAS_GELU>(A.xb, d, 1, P + p->off[0], d, 1, n, h1, d, P + p->off[1], A.a1, A.h1, s);
+    mm<MM_BIAS_GELU>(p->bf16, A.xb, d, 1, P + p->off[0], d, 1, n, h1, d, P + p->off[1], A.a1, A.h1, s);
   }
   {
     Launch L(p->ctx, s, ST_PROF_OTHER, 2.0 * n * h1 * h2, 0);
-    mm<MM_BIAS_GELU>(A.h1, h1, 1, P + p->off[2], h1, 1, n, h2, h1, P + p->off[3], A.a2, A.h2, s);
+    mm<MM_BIAS_GELU>(p->bf16, A.h1, h1, 1, P + p->off[2], h1, 1, n, h2, h1, P + p->off[3], A.a2, A.h2, s);
   }
   {
     Launch L(p->ctx, s, ST_PROF_OTHER, 4.0 * n * h2, 0);
-    mm<MM_BIAS>(A.h2, h2, 1, P + p->off[4], h2, 1, n, 2, h2, P + p->off[5], nullptr, A.z, s);
+    mm<MM_BIAS>(p->bf16, A.h2, h2, 1, P + p->off[4], h2, 1, n, 2, h2, P + p->off[5], nullptr, A.z, s);
   }
 }
 
@@ -345,15 +435,15 @@ extern "C" int st_proxy_train_step(st_ctx* ctx, st_proxy* p, const float* x_dev,
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
     // dW3 = dz^T h2, db3 = colsum(dz); d2 = (dz W3) * gelu'(a2)
-    mm<MM_STORE>(A.dz, 1, 2, A.h2, 1, h2, 2, h2, B, nullptr, nullptr, G + p->off[4], s);
+    mm<MM_STORE>(p->bf16, A.dz, 1, 2, A.h2, 1, h2, 2, h2, B, nullptr, nullptr, G + p->off[4], s);
     k_colsum<<<1, 32, 0, s>>>(A.dz, B, 2, G + p->off[5]);
-    mm<MM_DGELU>(A.dz, 2, 1, P + p->off[4], 1, h2, B, h2, 2, nullptr, A.a2, A.d2, s);
+    mm<MM_DGELU>(p->bf16, A.dz, 2, 1, P + p->off[4], 1, h2, B, h2, 2, nullptr, A.a2, A.d2, s);
     // dW2 = d2^T h1, db2; d1 = (d2 W2) * gelu'(a1)
-    mm<MM_STORE>(A.d2, 1, h2, A.h1, 1, h1, h2, h1, B, nullptr, nullptr, G + p->off[2], s);
+    mm<MM_STORE>(p->bf16, A.d2, 1, h2, A.h1, 1, h1, h2, h1, B, nullptr, nullptr, G + p->off[2], s);
     k_colsum<<<(h2 + 127) / 128, 128, 0, s>>>(A.d2, B, h2, G + p->off[3]);
-    mm<MM_DGELU>(A.d2, h2, 1, P + p->off[2], 1, h1, B, h1, h2, nullptr, A.a1, A.d1, s);
+    mm<MM_DGELU>(p->bf16, A.d2, h2, 1, P + p->off[2], 1, h1, B, h1, h2, nullptr, A.a1, A.d1, s);
     // dW1 = d1^T x, db1
-    mm<MM_STORE>(A.d1, 1, h1, A.xb, 1, d, h1, d, B, nullptr, nullptr, G + p->off[0], s);
+    mm<MM_STORE>(p->bf16, A.d1, 1, h1, A.xb, 1, d, h1, d, B, nullptr, nullptr, G + p->off[0], s);
     k_colsum<<<(h1 + 127) / 128, 128, 0, s>>>(A.d1, B, h1, G + p->off[1]);
   }
   p->t += 1;
@@ -427,12 +517,24 @@ extern "C" int st_cascade_merge(st_ctx* ctx, const int32_t* proxy_label_dev, int
 
 extern "C" int64_t st_proxy_steps(const st_proxy* p) { return p ? p->t : -1; }
 
+extern "C" int st_proxy_set_precision(st_proxy* p, int32_t dtype) {
+  if (!p || (dtype != ST_F32 && dtype != ST_BF16))
+    return pfail(p ? p->ctx : nullptr, ST_EINVAL, "st_proxy_set_precision: ST_F32 or ST_BF16");
+  p->bf16 = dtype == ST_BF16;
+  return ST_OK;
+}
+
 extern "C" int st_proxy_restore(st_proxy* p, const float* params_dev, const float* m_dev, const float* v_dev,
-                                int64_t steps, void* stream) {
+                                size_t bytes, int64_t steps, void* stream) {
   if (!p || !params_dev || !m_dev || !v_dev || steps < 0)
     return pfail(p ? p->ctx : nullptr, ST_EINVAL, "st_proxy_restore: bad argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t n = (size_t)p->n_params * sizeof(float);
+  // a state saved from a proxy of another shape (or a truncated buffer) is refused
+  // before anything is read
+  if (bytes != n)
+    return pfail(p->ctx, ST_EINVAL, "st_proxy_restore: " + std::to_string(bytes) + " bytes per buffer, this proxy needs " +
+                                        std::to_string(n));
   if (cudaMemcpyAsync(p->params, params_dev, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(p->m, m_dev, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(p->v, v_dev, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

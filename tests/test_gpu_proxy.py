@@ -127,3 +127,81 @@ def test_training_resumes_from_a_checkpoint(setup):
     for k in pa:
         assert np.array_equal(pa[k], pc[k]), k
     assert a.steps() == c.steps() == 8
+
+
+def test_restore_refuses_a_state_of_another_shape(setup):
+    """A checkpoint of a proxy with another hidden width (or a truncated buffer)
+    is refused before anything is read: by the binding's checks, and by the
+    library's own size check when the C entry is called directly."""
+    import ctypes
+    torch, stretto, synth = setup["torch"], setup["stretto"], setup["synth"]
+    a = stretto.Proxy(setup["model"], setup["params"])
+    d = a.d
+    other = stretto.Proxy(setup["model"], synth.make_proxy_weights(d, 64, 32, seed=5))
+    with pytest.raises(ValueError):
+        a.restore(other.state())
+    st = a.state()
+    short = dict(st, params=st["params"][:-1].contiguous())
+    with pytest.raises(ValueError):
+        a.restore(short)
+    # the C entry itself: a byte count that is not n_params * 4
+    n = st["params"].numel() * 4
+    rc = a.L.st_proxy_restore(a.h, stretto._ptr(st["params"]), stretto._ptr(st["m"]), stretto._ptr(st["v"]),
+                              ctypes.c_size_t(n - 4), 3, stretto._stream())
+    assert rc == stretto.ST_EINVAL
+    assert a.steps() == 0
+    a.restore(st)
+    torch.cuda.synchronize()
+
+
+def test_bf16_contractions_match_the_oracle(setup):
+    """st_proxy_set_precision(ST_BF16): the tensor-core BF16 contractions
+    against the oracle's BF16 reading (each product's operands rounded to
+    bfloat16, exact accumulation): loss and gradients of one step, then
+    parameters after 12 Adam steps and the confidences they give.  A rounded
+    operand is a decision taken in float32 on both sides, but its input comes
+    from a float32 (GPU) or float64 (oracle) accumulation, so a few roundings
+    land on neighbouring bfloat16 values: the bound is a few units of
+    bfloat16's 2^-8, well under the distance to the float32 network."""
+    from oracle import proxy as PX
+    torch, stretto, synth = setup["torch"], setup["stretto"], setup["synth"]
+    x, y = setup["x"], setup["y"]
+    p64 = {k: v.astype(np.float64) for k, v in setup["params"].items()}
+    px = stretto.Proxy(setup["model"], setup["params"])
+    px.set_precision(stretto.ST_BF16)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    batch = np.arange(3, 3 + 384, dtype=np.int32)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    px.train_step(xd, yd, torch.from_numpy(batch).cuda(), lr=0.0, loss=loss)
+    torch.cuda.synchronize()
+    g = px.read(stretto.ST_PROXY_GRADS)
+    ref_loss, ref = PX.loss_and_grads(p64, x[batch], y[batch], bf=True)
+    _, ref32 = PX.loss_and_grads(p64, x[batch], y[batch])
+    assert abs(loss.item() - ref_loss) <= 1e-4 * abs(ref_loss)
+    for k in ref:
+        err = normwise_rel(g[k], ref[k])
+        assert err <= 4e-3, (k, err)
+        if k.startswith("w"):
+            assert err < 0.5 * normwise_rel(ref32[k], ref[k]) or err <= 1e-4, k
+    # Adam steps, then confidences.  Adam divides each gradient by its own
+    # running magnitude, so where a gradient is near zero the few bfloat16
+    # roundings that land differently can flip its sign and move that weight by
+    # up to ~lr per step: the bound is per element, 2 lr per step.
+    px2 = stretto.Proxy(setup["model"], setup["params"])
+    px2.set_precision(stretto.ST_BF16)
+    lr = 1e-3
+    batches = synth.minibatches(len(x), 256, 2, seed=19)[:12]
+    for b in batches:
+        px2.train_step(xd, yd, torch.from_numpy(b).cuda(), lr=lr)
+    torch.cuda.synchronize()
+    ours = px2.read(stretto.ST_PROXY_PARAMS)
+    ref_p, _ = PX.train(p64, x, y, batches, lr=lr, bf=True)
+    for k in ref_p:
+        assert np.abs(ours[k] - ref_p[k]).max() <= 2 * lr * len(batches), k
+        assert normwise_rel(ours[k], ref_p[k]) <= 5e-2, k
+    conf, lab = px2.eval(xd[:512])
+    c_ref, l_ref = PX.confidence_and_label(ref_p, x[:512], bf=True)
+    assert np.abs(conf.cpu().numpy() - c_ref).max() <= 2e-2
+    assert (lab.cpu().numpy() == l_ref).mean() >= 0.98
+    with pytest.raises(stretto.StrettoError):
+        px2.set_precision(stretto.ST_E4M3)

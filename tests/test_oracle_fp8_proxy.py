@@ -1,4 +1,5 @@
 """Pins of the oracle's FP8 E4M3 codec, block quantiser, proxy MLP, Adam and cascade (CPU only)."""
+import math
 import os
 
 import numpy as np
@@ -175,3 +176,56 @@ def test_hard_cascade_and_cost():
     assert (a, r, u, c) == (0.0, 1.0, 0.0, 10.0)
     lab, uns = PX.cascade(np.array([1, 0, 1]), np.array([0.9, 0.5, 0.7]), 0.6, np.array([0, 1, 0]))
     assert lab.tolist() == [1, 1, 1] and uns.tolist() == [False, True, False]
+
+
+def test_bf16_rounding_matches_torch_cast():
+    r = np.random.Generator(np.random.PCG64(11))
+    x = np.concatenate([r.standard_normal(20000) * 10.0 ** r.integers(-30, 30, 20000),
+                        np.array([0.0, -0.0, 1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 3.0e38, -1e-40])])
+    x = x.astype(np.float32)
+    # exact half-way cases: the 16 discarded bits are 0x8000, both parities of the kept bit
+    u = (r.integers(0, 2 ** 15, 2000, dtype=np.uint32) << 17) | np.uint32(0x3F800000) | np.uint32(0x8000)
+    u2 = u | np.uint32(0x10000)
+    ties = np.concatenate([u.view(np.float32), u2.view(np.float32)])
+    for v in (x, ties):
+        ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+        np.testing.assert_array_equal(PX.bf16(v), ref)
+
+
+def test_bf16_contractions_match_torch_with_rounded_operands():
+    """The BF16 forward / backward against a torch float64 run that casts each
+    product's operands through torch.bfloat16, and against the exact network
+    within bfloat16's resolution; a dropped rounding point changes the result."""
+    p = _proxy_params(6, din=40, h1=24, h2=16)
+    r = np.random.Generator(np.random.PCG64(7))
+    x = r.standard_normal((12, 40))
+    y = r.integers(0, 2, 12)
+    rb = lambda a: a.to(torch.bfloat16).to(torch.float64)
+    t = {k: torch.tensor(v, dtype=torch.float64) for k, v in p.items()}
+    xt = torch.from_numpy(x)
+    a1 = rb(xt) @ rb(t["w1"]).T + t["b1"]
+    h1 = torch.nn.functional.gelu(a1)
+    a2 = rb(h1) @ rb(t["w2"]).T + t["b2"]
+    h2 = torch.nn.functional.gelu(a2)
+    z = rb(h2) @ rb(t["w3"]).T + t["b3"]
+    zo, _ = PX.forward(p, x, bf=True)
+    np.testing.assert_allclose(zo, z.numpy(), rtol=1e-13, atol=1e-14)
+    # backward: the same chain rule, operands of every product through bfloat16
+    pr = torch.softmax(z, 1)
+    dz = pr.clone()
+    dz[torch.arange(12), torch.from_numpy(y)] -= 1.0
+    dz /= 12
+    ref = {"w3": rb(dz).T @ rb(h2), "b3": dz.sum(0)}
+    gelu_d = lambda a: 0.5 * (1 + torch.erf(a / math.sqrt(2))) + a * torch.exp(-0.5 * a * a) / math.sqrt(2 * math.pi)
+    da2 = (rb(dz) @ rb(t["w3"])) * gelu_d(a2)
+    ref.update({"w2": rb(da2).T @ rb(h1), "b2": da2.sum(0)})
+    da1 = (rb(da2) @ rb(t["w2"])) * gelu_d(a1)
+    ref.update({"w1": rb(da1).T @ rb(xt), "b1": da1.sum(0)})
+    _, g = PX.loss_and_grads(p, x, y, bf=True)
+    for k in ref:
+        np.testing.assert_allclose(g[k], ref[k].numpy(), rtol=1e-12, atol=1e-15)
+    # within bfloat16 resolution of the exact network, and not equal to it
+    _, g64 = PX.loss_and_grads(p, x, y)
+    for k in ("w1", "w2", "w3"):
+        rel = np.abs(g[k] - g64[k]).max() / np.abs(g64[k]).max()
+        assert 1e-5 < rel < 3e-2, (k, rel)
