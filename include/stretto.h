@@ -149,8 +149,15 @@ int st_reserve(st_ctx* ctx, int64_t build_rows, int64_t eval_rows);
  * zero). */
 #define ST_WS_BUILD 0
 #define ST_WS_EVAL 1
+#define ST_WS_ANY 2
 size_t st_workspace_size(const st_ctx* ctx, int which, int64_t rows);
 int st_set_workspace(st_ctx* ctx, int which, void* dev, size_t bytes);
+/* st_workspace_held: device bytes of workspace the context currently owns
+ * (allocated by the library, not caller-provided) -- ST_WS_BUILD, ST_WS_EVAL,
+ * or ST_WS_ANY for all of its workspaces (build, evaluation, cascade routing,
+ * map decode, query scoring).  0 for a NULL context or an unknown kind.  A
+ * diagnostic: it shows whether a call grew the library's own memory. */
+size_t st_workspace_held(const st_ctx* ctx, int which);
 
 /* ---- KV caches ---- */
 
@@ -162,6 +169,22 @@ int st_set_workspace(st_ctx* ctx, int which, void* dev, size_t bytes);
  * or one longer than max_pos - 1), ST_EUNSUPPORTED (a document longer than
  * 16384 tokens), ST_ENOMEM. */
 int st_kv_alloc(st_ctx* ctx, const int64_t* offsets_host, int32_t T, st_kv** out);
+
+/* A second retained profile of an existing cache `src` (Sec. 5 keeps several
+ * compressed caches -- profiles -- per item, e.g. at two compression ratios or
+ * precisions).  The returned handle shares src's document offsets, full cache
+ * (K, V, scores) and pooled states -- they are not copied, and src must be
+ * built through src and must outlive the profile -- and owns a retained cache
+ * of its own, sized for any r <= r_max in either retained dtype
+ * (sum over tuples of pad64(n_keep(L, r_max)) slots per layer and kv head).
+ * st_kv_retain on it reads src's full cache (src must have been built) and
+ * leaves src's own retained profile untouched, so one table can hold, say, a
+ * BF16 and an E4M3 profile at once and st_op_eval can read either.
+ * st_kv_build, st_kv_import and st_kv_score_query refuse a profile; st_kv_free
+ * releases only what it owns.  Errors: ST_EINVAL (src is NULL, of another
+ * context or itself a profile; r_max outside (0, 1]; later, st_kv_retain with
+ * r > r_max), ST_ENOMEM. */
+int st_kv_profile_alloc(st_ctx* ctx, st_kv* src, double r_max, st_kv** out);
 void st_kv_free(st_kv* kv);
 
 /* Offline KV-cache creation (Sec. 5).  tokens_dev: DEVICE int32 [offsets[T]]
@@ -416,6 +439,29 @@ int st_cascade_run(int32_t n_stages, const st_stage* stages, const int32_t* tupl
                    int32_t* labels_dev, int32_t* stage_dev, int32_t* counts_host, float* ms_host,
                    void* stream);
 
+/* The learned-proxy cascade in one call: the proxy (below) as the cheap first
+ * stage of the Sec. 4.1 cascade, in front of the operator stages of
+ * st_cascade_run.
+ *   1. The proxy evaluates the pooled states of the n tuples: row
+ *      tuple_ids_dev[i] of x_dev (DEVICE float32 [T][d_in], e.g.
+ *      ST_VIEW_POOLED).  Where its confidence is >= tau it decides the tuple.
+ *   2. The other tuples, compacted in order, run through
+ *      st_cascade_run(n_stages, stages) -- for instance an operator over an
+ *      E4M3 profile with an unsure band (theta+ > theta-), then the same
+ *      operator over the BF16 profile on what the first leaves unsure.
+ *   3. labels_dev[i] (DEVICE int32 [n]): the proxy's label (0 reject,
+ *      1 accept) where it decided, else the deciding stage's decision;
+ *      stage_dev[i] (DEVICE int32 [n]): 0 for the proxy, k + 1 for stage k.
+ * counts_host (optional, [n_stages + 1]): n, then the tuples sent to each
+ * operator stage.  Routing buffers are the context's (grown on demand).
+ * Synchronises `stream` after the proxy and after each operator stage, to size
+ * the next stage's launches.  Errors: ST_EINVAL, ST_ENOMEM, and those of the
+ * stages (the message names the stage). */
+typedef struct st_proxy st_proxy;
+int st_proxy_cascade(st_ctx* ctx, st_proxy* p, const float* x_dev, float tau, int32_t n_stages,
+                     const st_stage* stages, const int32_t* tuple_ids_dev, int32_t n,
+                     int32_t* labels_dev, int32_t* stage_dev, int32_t* counts_host, void* stream);
+
 /* ---- schedule of operator evaluation, and its autotuner ----
  *
  * eval_rows: prompt rows per pass through the layers (the evaluation is cut
@@ -494,7 +540,6 @@ int st_run_host(st_ctx* ctx, st_kv* kv, const st_operator* op, int32_t kv_dtype,
  * st_kv_build), trained with softmax cross-entropy and Adam (beta 0.9 / 0.999,
  * eps 1e-8, bias-corrected) against the full operator's labels (0 reject,
  * 1 accept).  float32 parameters, activations and accumulation. */
-typedef struct st_proxy st_proxy;
 #define ST_PROXY_PARAMS 0   /* w1 [h1][d_in], b1 [h1], w2 [h2][h1], b2 [h2], w3 [2][h2], b3 [2] */
 #define ST_PROXY_GRADS 1    /* the same layout: gradients of the last train step */
 #define ST_PROXY_ADAM_M 2
@@ -531,10 +576,20 @@ int st_proxy_read(const st_proxy* p, int32_t which, void* dst_dev, size_t bytes,
  * from caller DEVICE buffers (float32, ST_PROXY_PARAMS layout, n_params each,
  * as st_proxy_read writes them) and the step count, so that the next
  * st_proxy_train_step continues exactly where the saved proxy stopped.
- * Enqueued on `stream`.  Errors: ST_EINVAL (NULL buffer, steps < 0). */
+ * `bytes` is the size of EACH of the three buffers and must equal
+ * n_params * 4 of this proxy; nothing is read otherwise (a state saved from a
+ * proxy of another shape, or a truncated buffer).  Enqueued on `stream`.
+ * Errors: ST_EINVAL (NULL buffer, wrong size, steps < 0). */
 int64_t st_proxy_steps(const st_proxy* p);
+/* Precision of the proxy's contractions: ST_F32 (default; float32 on the CUDA
+ * cores) or ST_BF16 (the tensor cores' mma.sync m16n8k16: each operand of
+ * every forward and backward product rounded to bfloat16, nearest-even, as it
+ * is staged; float32 accumulation).  Parameters, Adam moments, biases, GELU,
+ * loss and bias gradients stay float32.  Takes effect from the next call.
+ * Errors: ST_EINVAL (NULL proxy, another dtype). */
+int st_proxy_set_precision(st_proxy* p, int32_t dtype);
 int st_proxy_restore(st_proxy* p, const float* params_dev, const float* m_dev, const float* v_dev,
-                     int64_t steps, void* stream);
+                     size_t bytes, int64_t steps, void* stream);
 
 /* ---- kernel self-test entry ---- */
 

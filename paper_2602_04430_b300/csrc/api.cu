@@ -149,10 +149,12 @@ static cudaEvent_t take_event(st_ctx* ctx) {
   cudaEventCreate(&e);
   return e;
 }
+thread_local bool tls_no_prof = false;
+
 Launch::Launch(st_ctx* c, cudaStream_t st, int fam, double fl, double by)
-    : ctx(c), s(st), family(fam), flops(fl), bytes(by) {
+    : ctx(c), s(st), family(fam), flops(fl), bytes(by), timed(c->prof.on && !tls_no_prof) {
   ctx->launches++;
-  if (ctx->prof.on) {
+  if (timed) {
     rec.family = fam;
     rec.flops = fl;
     rec.bytes = by;
@@ -162,7 +164,7 @@ Launch::Launch(st_ctx* c, cudaStream_t st, int fam, double fl, double by)
   }
 }
 Launch::~Launch() {
-  if (ctx->prof.on) {
+  if (timed) {
     cudaEventRecord(rec.b, s);
     ctx->prof.pending.push_back(rec);
   }
@@ -387,6 +389,7 @@ extern "C" void st_destroy(st_ctx* ctx) {
   cudaFree(ctx->ws_casc.p);
   cudaFree(ctx->ws_map.p);
   cudaFree(ctx->ws_score.p);
+  cudaFree(ctx->ws_pcasc.p);
   cudaFree(ctx->rope_avg);
   for (auto& r : ctx->prof.pending) {
     cudaEventDestroy(r.a);
@@ -414,6 +417,17 @@ extern "C" size_t st_workspace_size(const st_ctx* ctx, int which, int64_t rows) 
   // a chunk of `rows` rows holds at most `rows` tuples (build) or pairs (eval)
   if (which == ST_WS_BUILD) return build_ws_bytes(ctx, rows, rows, nullptr, nullptr);
   if (which == ST_WS_EVAL) return eval_bufs(ctx, rows, rows, nullptr, nullptr);
+  return 0;
+}
+
+extern "C" size_t st_workspace_held(const st_ctx* ctx, int which) {
+  if (!ctx) return 0;
+  auto own = [](const DevBuf& b) { return b.external ? (size_t)0 : b.bytes; };
+  if (which == ST_WS_BUILD) return own(ctx->ws_build);
+  if (which == ST_WS_EVAL) return own(ctx->ws_eval);
+  if (which == ST_WS_ANY)
+    return own(ctx->ws_build) + own(ctx->ws_eval) + own(ctx->ws_casc) + own(ctx->ws_map) + own(ctx->ws_score) +
+           own(ctx->ws_pcasc);
   return 0;
 }
 
@@ -522,6 +536,12 @@ extern "C" int st_kv_alloc(st_ctx* ctx, const int64_t* offsets_host, int32_t T, 
 extern "C" void st_kv_free(st_kv* kv) {
   if (!kv) return;
   cudaDeviceSynchronize();
+  if (kv->src) {   // a profile: the full cache and offsets belong to its source
+    void* own[] = {kv->rank, kv->Kr, kv->Vr, kv->scales, kv->offp, kv->nkeep, kv->status};
+    for (void* p : own) cudaFree(p);
+    delete kv;
+    return;
+  }
   void* ptrs[] = {kv->off, kv->K, kv->V, kv->scores, kv->pooled, kv->rank, kv->Kr, kv->Vr,
                   kv->scales, kv->offp, kv->nkeep, kv->status, kv->items, kv->tok, kv->iota,
                   kv->out_logits, kv->out_labels};
@@ -529,9 +549,65 @@ extern "C" void st_kv_free(st_kv* kv) {
   delete kv;
 }
 
+extern "C" int st_kv_profile_alloc(st_ctx* ctx, st_kv* src, double r_max, st_kv** out) {
+  if (!ctx || !src || !out || src->ctx != ctx || src->src)
+    return fail(ctx, ST_EINVAL, "st_kv_profile_alloc: bad argument (a cache of this context, not itself a profile)");
+  if (!(r_max > 0.0 && r_max <= 1.0)) return fail(ctx, ST_EINVAL, "st_kv_profile_alloc: r_max must lie in (0, 1]");
+  *out = nullptr;
+  const st_model_cfg& c = ctx->cfg;
+  int64_t rp = 0;
+  for (int t = 0; t < src->T; ++t) rp += (n_keep_host(src->off_h[t + 1] - src->off_h[t], r_max) + 63) & ~63LL;
+  st_kv* kv = new st_kv();
+  kv->ctx = ctx;
+  kv->src = src;
+  kv->r_max = r_max;
+  kv->T = src->T;
+  kv->R = src->R;
+  kv->Rp_cap = rp;
+  kv->max_len = src->max_len;
+  kv->off_h = src->off_h;
+  kv->off = src->off;
+  kv->K = src->K;
+  kv->V = src->V;
+  kv->scores = src->scores;
+  kv->pooled = src->pooled;
+  kv->items = src->items;
+  kv->n_items = src->n_items;
+  kv->item_start = src->item_start;
+  const size_t e = ctx->esz, LH = (size_t)c.layers * c.hkv;
+  int rc = ST_OK;
+  auto A = [&](void** p, size_t bytes) {
+    if (rc == ST_OK) rc = dev_alloc(ctx, p, bytes);
+  };
+  A((void**)&kv->rank, LH * kv->R * sizeof(int32_t));
+  A(&kv->Kr, LH * rp * c.hd * e);
+  A(&kv->Vr, LH * rp * c.hd * e);
+  A((void**)&kv->scales, LH * (rp / 64) * 2 * sizeof(float));
+  A((void**)&kv->offp, (kv->T + 1) * sizeof(int64_t));
+  A((void**)&kv->nkeep, kv->T * sizeof(int32_t));
+  A((void**)&kv->status, sizeof(int32_t));
+  if (rc != ST_OK) {
+    st_kv_free(kv);
+    return rc;
+  }
+  // zeroed like a cache's own retained buffers (tiles past a segment read finite values)
+  cudaMemset(kv->Kr, 0, LH * rp * c.hd * e);
+  cudaMemset(kv->Vr, 0, LH * rp * c.hd * e);
+  cudaMemset(kv->scales, 0, LH * (rp / 64) * 2 * sizeof(float));
+  cudaMemset(kv->status, 0, sizeof(int32_t));
+  cudaError_t err = cudaDeviceSynchronize();
+  if (err != cudaSuccess) {
+    st_kv_free(kv);
+    return fail(ctx, ST_ECUDA, std::string("st_kv_profile_alloc: ") + cudaGetErrorString(err));
+  }
+  *out = kv;
+  return ST_OK;
+}
+
 extern "C" int st_kv_build(st_ctx* ctx, st_kv* kv, const int32_t* tokens_dev, void* stream) {
   ST_TRACE("st_kv_build");
   if (!ctx || !kv || !tokens_dev || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_build: bad argument");
+  if (kv->src) return fail(ctx, ST_EINVAL, "st_kv_build: a profile (st_kv_profile_alloc) is built through its source");
   const st_model_cfg& c = ctx->cfg;
   cudaStream_t s = S(stream);
   const bool ea_full = ctx->score_mode == ST_SCORE_EA_FULL;
@@ -683,7 +759,9 @@ extern "C" int st_kv_retain(st_ctx* ctx, st_kv* kv, double r, int32_t kv_dtype, 
   const st_model_cfg& c = ctx->cfg;
   if (!(kv_dtype == c.dtype || (kv_dtype == ST_E4M3 && c.dtype == ST_BF16)))
     return fail(ctx, ST_EINVAL, "st_kv_retain: kv_dtype must be the model dtype or ST_E4M3 (bf16 models)");
-  if (!kv->built) return fail(ctx, ST_EINVAL, "st_kv_retain: cache not built");
+  if (!(kv->src ? kv->src->built : kv->built)) return fail(ctx, ST_EINVAL, "st_kv_retain: cache not built");
+  if (r > kv->r_max)
+    return fail(ctx, ST_EINVAL, "st_kv_retain: r exceeds the r_max this profile was allocated for");
   cudaStream_t s = S(stream);
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
@@ -738,7 +816,7 @@ extern "C" int st_kv_indices(st_ctx* ctx, const st_kv* kv, double r, int32_t* id
   ST_TRACE("st_kv_indices");
   if (!ctx || !kv || kv->ctx != ctx || !off_dev) return fail(ctx, ST_EINVAL, "st_kv_indices: bad argument");
   if (!(r > 0.0 && r <= 1.0)) return fail(ctx, ST_EINVAL, "st_kv_indices: r must lie in (0, 1]");
-  if (!kv->built || kv->r <= 0.0)
+  if (!(kv->src ? kv->src->built : kv->built) || kv->r <= 0.0)
     return fail(ctx, ST_EINVAL, "st_kv_indices: no ranking (st_kv_retain after st_kv_build)");
   const st_model_cfg& c = ctx->cfg;
   std::vector<int64_t> o(kv->T + 1, 0);
@@ -1466,6 +1544,7 @@ extern "C" int st_set_scoring(st_ctx* ctx, int32_t mode, int32_t horizon) {
 extern "C" int st_kv_score_query(st_ctx* ctx, st_kv* kv, const st_operator* op, void* stream) {
   ST_TRACE("st_kv_score_query");
   if (!ctx || !kv || !op || kv->ctx != ctx) return fail(ctx, ST_EINVAL, "st_kv_score_query: bad argument");
+  if (kv->src) return fail(ctx, ST_EINVAL, "st_kv_score_query: scores belong to the source cache, not to a profile");
   const st_model_cfg& c = ctx->cfg;
   if (!kv->built || kv->r != 1.0 || kv->kv_dtype != c.dtype)
     return fail(ctx, ST_EINVAL, "st_kv_score_query: the cache needs a retained profile at r = 1 in the model dtype");

@@ -76,6 +76,18 @@ __global__ void __launch_bounds__(1024) k_stage_route(const int32_t* __restrict_
   if (tid == 0) *next_n = carry;
 }
 
+// stage of the merged proxy cascade: 0 everywhere (the proxy decided), then,
+// in a second launch, k + 1 at the positions operator stage k decided
+__global__ void k_stage_zero(int n, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = 0;
+}
+__global__ void k_scatter_stage(const int32_t* __restrict__ pos, const int32_t* __restrict__ count,
+                                const int32_t* __restrict__ op_stage, int32_t* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < *count) out[pos[j]] = op_stage[j] + 1;
+}
+
 }  // namespace
 
 extern "C" int st_cascade_run(int32_t n_stages, const st_stage* stages, const int32_t* tuple_ids_dev,
@@ -157,4 +169,78 @@ extern "C" int st_cascade_run(int32_t n_stages, const st_stage* stages, const in
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return rc;
+}
+
+extern "C" int st_proxy_cascade(st_ctx* ctx, st_proxy* p, const float* x_dev, float tau, int32_t n_stages,
+                                const st_stage* stages, const int32_t* tuple_ids_dev, int32_t n,
+                                int32_t* labels_dev, int32_t* stage_dev, int32_t* counts_host, void* stream) {
+  ST_TRACE("st_proxy_cascade");
+  if (!ctx || !p || !x_dev || n < 0 || n_stages < 1 || !stages ||
+      (n > 0 && (!tuple_ids_dev || !labels_dev || !stage_dev)))
+    return cfail(ctx, ST_EINVAL, "st_proxy_cascade: bad argument");
+  if (counts_host)
+    for (int k = 0; k <= n_stages; ++k) counts_host[k] = 0;
+  if (n == 0) return ST_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  {
+    // an error left pending by an earlier call is reported as such, not as this call's
+    const cudaError_t pend = cudaGetLastError();
+    if (pend != cudaSuccess)
+      return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: pending error from an earlier call: ") +
+                                      cudaGetErrorString(pend));
+  }
+  // routing buffers: confidence, proxy label, unsure ids / positions, the
+  // operator stages' labels and stages, the unsure count
+  const size_t need = (size_t)n * 4 * 6 + 4 * 256;
+  if (ctx->ws_pcasc.bytes < need) {
+    if (ctx->ws_pcasc.p) cudaFree(ctx->ws_pcasc.p);
+    ctx->ws_pcasc.p = nullptr;
+    ctx->ws_pcasc.bytes = 0;
+    if (cudaMalloc(&ctx->ws_pcasc.p, need) != cudaSuccess) {
+      cudaGetLastError();
+      return cfail(ctx, ST_ENOMEM, "st_proxy_cascade: routing buffers");
+    }
+    ctx->ws_pcasc.bytes = need;
+  }
+  auto carve = [](char*& q, size_t bytes) {
+    char* r = q;
+    q += (bytes + 255) & ~(size_t)255;
+    return r;
+  };
+  char* q = (char*)ctx->ws_pcasc.p;
+  float* conf = (float*)carve(q, (size_t)n * 4);
+  int32_t* plab = (int32_t*)carve(q, (size_t)n * 4);
+  int32_t* u_ids = (int32_t*)carve(q, (size_t)n * 4);
+  int32_t* u_pos = (int32_t*)carve(q, (size_t)n * 4);
+  int32_t* u_lab = (int32_t*)carve(q, (size_t)n * 4);
+  int32_t* u_stg = (int32_t*)carve(q, (size_t)n * 4);
+  int32_t* cnt = (int32_t*)carve(q, 8);
+  int rc = st_proxy_eval(ctx, p, x_dev, tuple_ids_dev, n, conf, plab, stream);
+  if (rc != ST_OK) return rc;
+  if ((rc = st_cascade_compact(ctx, conf, tuple_ids_dev, n, tau, u_ids, cnt, stream)) != ST_OK) return rc;
+  if ((rc = st_cascade_compact(ctx, conf, nullptr, n, tau, u_pos, cnt + 1, stream)) != ST_OK) return rc;
+  int32_t k = 0;
+  cudaError_t e = cudaMemcpyAsync(&k, cnt, 4, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: count copy: ") + cudaGetErrorString(e));
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: proxy stage: ") + cudaGetErrorString(e));
+  if (counts_host) counts_host[0] = n;
+  if (k > 0 && (rc = st_cascade_run(n_stages, stages, u_ids, k, u_lab, u_stg, counts_host ? counts_host + 1 : nullptr,
+                                    nullptr, stream)) != ST_OK) {
+    if (stages[0].ctx != ctx) ctx->err = stages[0].ctx->err;
+    return rc;
+  }
+  // the proxy's labels everywhere, then the operator stages' at the unsure positions
+  if ((rc = st_cascade_merge(ctx, plab, n, u_pos, cnt, u_lab, labels_dev, stream)) != ST_OK) return rc;
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    k_stage_zero<<<(n + 255) / 256, 256, 0, s>>>(n, stage_dev);
+  }
+  {
+    Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
+    k_scatter_stage<<<(n + 255) / 256, 256, 0, s>>>(u_pos, cnt, u_stg, stage_dev);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: merge: ") + cudaGetErrorString(e));
+  return ST_OK;
 }

@@ -157,6 +157,7 @@ struct st_ctx {
   int score_horizon = 0;
   float2* rope_avg = nullptr;
   st::DevBuf ws_score;            // st_kv_score_query: tuple ids, logits, labels
+  st::DevBuf ws_pcasc;            // st_proxy_cascade: confidences and routing
   int32_t* dstatus = nullptr;     // device status word of bounded waits (ST_ETIMEOUT)
   std::string err;
   st::Prof prof;
@@ -193,6 +194,11 @@ struct st_kv {
   int32_t* iota = nullptr;        // device 0..T-1 of st_run_host
   float* out_logits = nullptr;    // device outputs of st_run_host
   int32_t* out_labels = nullptr;
+  // a second retained profile of another cache (st_kv_profile_alloc): shares
+  // src's offsets, full cache, scores, pooled states and prefill items, owns
+  // its rank, retained cache, scales, offsets, counts and status word
+  st_kv* src = nullptr;
+  double r_max = 1.0;             // largest r the retained capacity holds
 };
 
 struct st_operator {

@@ -50,10 +50,16 @@ struct Launch {
   cudaStream_t s;
   int family;
   double flops, bytes;
+  bool timed;          // profiling events recorded for this launch
   ProfRec rec;
   Launch(st_ctx* c, cudaStream_t st, int fam, double fl, double by);
   ~Launch();
 };
+// Set by an entry that must create no CUDA resources (st_op_eval_noalloc) for
+// the duration of its call, on its own host thread only: Launch records no
+// profiling events while it is set.  Thread-local, so another thread's calls
+// on the same context keep their profiling.
+extern thread_local bool tls_no_prof;
 
 // ---- batched operator evaluation: the operators of one call as the kernels see
 // them (passed by value in kernel parameters, so a captured graph replays them)

@@ -91,11 +91,13 @@ extern "C" int st_op_eval_noalloc(st_ctx* ctx, const st_kv* kv, const st_operato
   EvalBufs w;
   eval_bufs(ctx, M, n, (char*)base, &w);
   // the same layer sequence as st_op_eval (one chunk), with profiling events
-  // switched off so that this entry creates no CUDA resources (its launches
-  // are still counted)
-  const bool prof = ctx->prof.on;
-  ctx->prof.on = false;
-  const int rc = eval_chunk(ctx, kv, os, 0, n, 0, M, w, reinterpret_cast<cudaStream_t>(stream));
-  ctx->prof.on = prof;
-  return rc;
+  // suppressed on this host thread so that this entry creates no CUDA
+  // resources (its launches are still counted); the context's own profiling
+  // switch is left untouched
+  struct NoProf {
+    bool old = tls_no_prof;
+    NoProf() { tls_no_prof = true; }
+    ~NoProf() { tls_no_prof = old; }
+  } guard;
+  return eval_chunk(ctx, kv, os, 0, n, 0, M, w, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -129,6 +129,7 @@ extern "C" int st_kv_import(st_ctx* ctx, st_kv* kv, const void* host, size_t byt
   ST_TRACE("st_kv_import");
   if (!ctx || !kv || kv->ctx != ctx || !host || bytes < sizeof(ProfileHeader))
     return pfail(ctx, ST_EINVAL, "st_kv_import: bad argument");
+  if (kv->src) return pfail(ctx, ST_EINVAL, "st_kv_import: import into a cache of its own, not a profile alias");
   const st_model_cfg& c = ctx->cfg;
   ProfileHeader h;
   std::memcpy(&h, host, sizeof(h));

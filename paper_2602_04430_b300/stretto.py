@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libstretto.so")
 ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ENAN, ST_EUNSUPPORTED = range(7)
 ST_SCORE_EA_LITE, ST_SCORE_EA_FULL = 0, 1
 ST_F32, ST_BF16, ST_E4M3 = 0, 1, 2
-ST_WS_BUILD, ST_WS_EVAL = 0, 1
+ST_WS_BUILD, ST_WS_EVAL, ST_WS_ANY = 0, 1, 2
 ST_OP_FILTER, ST_OP_CLASSIFY = 0, 1
 ST_REJECT, ST_ACCEPT, ST_UNSURE = 0, 1, 2
 (ST_VIEW_K, ST_VIEW_V, ST_VIEW_SCORES, ST_VIEW_POOLED, ST_VIEW_RANK, ST_VIEW_KR, ST_VIEW_VR,
@@ -87,8 +87,10 @@ def lib() -> ctypes.CDLL:
         "st_reserve": (i32, [VP, i64, i64]),
         "st_workspace_size": (sz, [VP, i32, i64]),
         "st_set_workspace": (i32, [VP, i32, VP, sz]),
+        "st_workspace_held": (sz, [VP, i32]),
         "st_kv_alloc": (i32, [VP, ctypes.POINTER(i64), i32, ctypes.POINTER(VP)]),
         "st_kv_free": (None, [VP]),
+        "st_kv_profile_alloc": (i32, [VP, VP, dbl, ctypes.POINTER(VP)]),
         "st_kv_build": (i32, [VP, VP, VP, VP]),
         "st_kv_retain": (i32, [VP, VP, dbl, i32, VP]),
         "st_kv_indices": (i32, [VP, VP, dbl, VP, VP, VP]),
@@ -125,6 +127,8 @@ def lib() -> ctypes.CDLL:
         "st_cascade_run": (i32, [i32, ctypes.POINTER(StageDesc), VP, i32, VP, VP, ctypes.POINTER(i32),
                                  ctypes.POINTER(ctypes.c_float), VP]),
         "st_run_host": (i32, [VP, VP, VP, i32, VP, VP, VP, VP]),
+        "st_proxy_cascade": (i32, [VP, VP, VP, ctypes.c_float, i32, ctypes.POINTER(StageDesc), VP, i32, VP, VP,
+                                   ctypes.POINTER(i32), VP]),
         "st_gemm": (i32, [VP, VP, VP, i32, i32, i32, VP, VP]),
         "st_proxy_create": (i32, [VP, i32, i32, i32, ctypes.POINTER(VP), ctypes.POINTER(VP)]),
         "st_proxy_free": (None, [VP]),
@@ -133,7 +137,8 @@ def lib() -> ctypes.CDLL:
         "st_cascade_compact": (i32, [VP, VP, VP, i32, ctypes.c_float, VP, VP, VP]),
         "st_cascade_merge": (i32, [VP, VP, i32, VP, VP, VP, VP, VP]),
         "st_proxy_steps": (i64, [VP]),
-        "st_proxy_restore": (i32, [VP, VP, VP, VP, i64, VP]),
+        "st_proxy_set_precision": (i32, [VP, i32]),
+        "st_proxy_restore": (i32, [VP, VP, VP, VP, sz, i64, VP]),
         "st_proxy_read": (i32, [VP, i32, VP, sz, VP]),
         "st_prof_enable": (i32, [VP, i32]),
         "st_prof_read": (i32, [VP, ctypes.POINTER(dbl)]),
@@ -208,6 +213,10 @@ class Model:
         """Bytes of device workspace one chunk of ``rows`` rows needs (ST_WS_BUILD / ST_WS_EVAL)."""
         return int(self.L.st_workspace_size(self.h, int(which), int(rows)))
 
+    def workspace_held(self, which: int = ST_WS_ANY) -> int:
+        """Device bytes of workspace the library currently owns for this context."""
+        return int(self.L.st_workspace_held(self.h, int(which)))
+
     def set_workspace(self, which: int, buf=None):
         """Carve that workspace out of the caller's device tensor ``buf`` (kept alive
         here until replaced), or go back to library-owned workspace with None."""
@@ -266,16 +275,27 @@ class Model:
 class KVCache:
     """The caches of one table (an ``st_kv``)."""
 
-    def __init__(self, model: Model, offsets: np.ndarray):
+    def __init__(self, model: Model, offsets: np.ndarray, _handle=None, _source=None):
         self.model = model
         self.L = model.L
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         self.offsets = off
         self.T = len(off) - 1
+        self._source = _source       # a profile keeps its source cache alive
+        if _handle is not None:
+            self.h = _handle
+            return
         h = VP()
         model.check(self.L.st_kv_alloc(model.h, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                        self.T, ctypes.byref(h)))
         self.h = h
+
+    def profile(self, r_max: float = 1.0) -> "KVCache":
+        """A second retained profile of this cache (``st_kv_profile_alloc``): shares
+        the full cache, holds its own retained cache for any r <= r_max."""
+        h = VP()
+        self.model.check(self.L.st_kv_profile_alloc(self.model.h, self.h, float(r_max), ctypes.byref(h)))
+        return KVCache(self.model, self.offsets, _handle=h, _source=self)
 
     def close(self):
         if getattr(self, "h", None):
@@ -479,6 +499,10 @@ class Proxy:
                                               _ptr(conf), _ptr(label), _stream(stream)))
         return conf, label
 
+    def set_precision(self, dtype: int):
+        """ST_F32 (float32 contractions) or ST_BF16 (tensor-core BF16 contractions)."""
+        self.model.check(self.L.st_proxy_set_precision(self.h, int(dtype)))
+
     def steps(self) -> int:
         """Adam steps taken (st_proxy_steps)."""
         return int(self.L.st_proxy_steps(self.h))
@@ -496,9 +520,21 @@ class Proxy:
         return out
 
     def restore(self, state, stream=None):
-        """Resume from ``state()`` of a proxy of the same shape (st_proxy_restore)."""
+        """Resume from ``state()`` of a proxy of the same shape (st_proxy_restore).
+        Each of params / m / v must be a contiguous float32 CUDA tensor of
+        n_params elements; the library refuses any other size."""
+        import torch
+        n = sum(self.sizes)
+        for k in ("params", "m", "v"):
+            t = state[k]
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError(f"proxy state '{k}' must be a contiguous float32 CUDA tensor")
+            if t.numel() != n:
+                raise ValueError(f"proxy state '{k}' holds {t.numel()} values, this proxy has {n}")
+        nbytes = state["params"].numel() * 4
         self.model.check(self.L.st_proxy_restore(self.h, _ptr(state["params"]), _ptr(state["m"]),
-                                                  _ptr(state["v"]), int(state["steps"]), _stream(stream)))
+                                                  _ptr(state["v"]), nbytes, int(state["steps"]),
+                                                  _stream(stream)))
 
     def read(self, which: int) -> Dict[str, np.ndarray]:
         import torch
@@ -615,6 +651,25 @@ def cascade_run(stages, tuple_ids, labels=None, stage=None, stream=None):
     m0.check(m0.L.st_cascade_run(k, arr, _ptr(tuple_ids), n, _ptr(labels), _ptr(stage), counts, ms,
                                  _stream(stream)))
     return labels, stage, list(counts), list(ms)
+
+
+def proxy_cascade(proxy: "Proxy", x, tau: float, stages, tuple_ids, labels=None, stage=None, stream=None):
+    """The learned-proxy cascade in one call (``st_proxy_cascade``): the proxy on
+    rows ``tuple_ids`` of the pooled states ``x``, confident tuples (conf >= tau)
+    decided by it, the rest through the operator ``stages`` = [(model, kv,
+    operator)].  Returns (labels, deciding stage: 0 proxy / k+1 operator stage k,
+    tuples the proxy saw then tuples sent to each stage)."""
+    import torch
+    n = int(tuple_ids.numel())
+    k = len(stages)
+    labels = torch.empty(max(n, 1), dtype=torch.int32, device="cuda") if labels is None else labels
+    stage = torch.empty(max(n, 1), dtype=torch.int32, device="cuda") if stage is None else stage
+    arr = (StageDesc * k)(*[StageDesc(m.h, kv.h, op.h) for m, kv, op in stages])
+    counts = (ctypes.c_int32 * (k + 1))()
+    m = proxy.model
+    m.check(m.L.st_proxy_cascade(m.h, proxy.h, _ptr(x), float(tau), k, arr, _ptr(tuple_ids), n, _ptr(labels),
+                                 _ptr(stage), counts, _stream(stream)))
+    return labels, stage, list(counts)
 
 
 def set_gemm_pairs(on: bool):

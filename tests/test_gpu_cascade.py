@@ -104,3 +104,57 @@ def test_cascade_rejects_classify(tmp_path):
     op = m.operator(synth.make_prompt(8, cfg.vocab, seed=71, label_ids=(1, 2, 3), kind="classify"))
     with pytest.raises(stretto.StrettoError):
         stretto.cascade_run([(m, kv, op)], torch.arange(kv.T, dtype=torch.int32, device="cuda"))
+
+
+def test_proxy_cascade_with_e4m3_band_then_bf16():
+    """st_proxy_cascade: the proxy (trained a few steps on the FP8 operator's
+    labels) as stage 0, then an operator over an E4M3 profile with an unsure
+    band, then the same operator over the BF16 profile of the same cache (two
+    profiles resident at once).  Labels, deciding stages and counts must equal
+    the cascade definition applied to the proxy's decisions (UNSURE below tau)
+    and to each stage's decisions over all tuples, on a shuffled subset of the
+    table's tuples."""
+    import torch
+    from oracle.operator import UNSURE, cascade_stages
+    from paper_2602_04430_b300 import build, stretto, synth
+    build.build()
+    cfg = synth.MODELS["c2_bf16"]
+    table = synth.make_table(synth.TABLES["c2"], cfg.vocab, seed=72, n_tuples=600)
+    model = stretto.Model(cfg, synth.make_weights(cfg, seed=73), max_pos=2112)
+    kv = model.kv_alloc(table["offsets"])
+    kv.build(torch.from_numpy(table["tokens"]).cuda())
+    kv.retain(0.5, stretto.ST_BF16)
+    prof = kv.profile(0.5)
+    prof.retain(0.5, stretto.ST_E4M3)
+    T = kv.T
+    all_ids = torch.arange(T, dtype=torch.int32, device="cuda")
+    base = synth.make_prompt(32, cfg.vocab, seed=74, r=0.5)
+    lg, _ = model.operator(base).eval(prof, all_ids)
+    m = (lg[:, 0] - lg[:, 1]).cpu().numpy()
+    theta = float(np.median(m))
+    band = synth.Operator(prompt=base.prompt, label_ids=base.label_ids, r=0.5,
+                          theta_pos=float(np.quantile(m, 0.6)), theta_neg=float(np.quantile(m, 0.4)))
+    plain = synth.Operator(prompt=base.prompt, label_ids=base.label_ids, r=0.5, theta_pos=theta, theta_neg=theta)
+    op8, op16 = model.operator(band), model.operator(plain)
+    x = kv.read(stretto.ST_VIEW_POOLED, torch.float32, (T, cfg.d))
+    px = stretto.Proxy(model, synth.make_proxy_weights(cfg.d, 512, 128, seed=75))
+    y = torch.from_numpy((m > theta).astype(np.int32)).cuda()
+    for b in synth.minibatches(T, 128, 2, seed=76):
+        px.train_step(x, y, torch.from_numpy(b).cuda(), lr=1e-3)
+    rng = np.random.Generator(np.random.PCG64(77))
+    sub = rng.permutation(T)[:450].astype(np.int32)
+    ids = torch.from_numpy(sub).cuda()
+    conf, plab = px.eval(x, rows=ids)
+    tau = float(np.quantile(conf.cpu().numpy(), 0.5))
+    d_proxy = np.where(conf.cpu().numpy() < np.float32(tau), UNSURE, plab.cpu().numpy()).tolist()
+    d8 = op8.eval(prof, ids)[1].cpu().tolist()
+    d16 = op16.eval(kv, ids)[1].cpu().tolist()
+    labels, stage, counts = stretto.proxy_cascade(px, x, tau, [(model, prof, op8), (model, kv, op16)], ids)
+    torch.cuda.synchronize()
+    model.status()
+    ref_l, ref_s, ref_c = cascade_stages([d_proxy, d8, d16])
+    assert labels.cpu().tolist() == ref_l
+    assert stage.cpu().tolist() == ref_s
+    assert counts == ref_c
+    assert counts[0] > counts[1] > counts[2] > 0, counts
+    print("proxy cascade: tuples per stage", counts)

@@ -87,3 +87,38 @@ def test_profile_blobs_are_validated():
     refused(blob, m2.kv_alloc(table["offsets"]))
     # the intact blob still loads
     fresh.import_profile(blob)
+
+
+def test_second_profile_of_one_cache():
+    """st_kv_profile_alloc: a BF16 profile in the cache itself and an E4M3
+    profile in a second handle over the same full cache, resident at once, each
+    evaluate bit for bit like the cache re-retained in that dtype; the profile
+    refuses r above its r_max, a build, an import and query scoring."""
+    cfg, table, model, kv, st, synth, torch = _setup("c2_bf16", "c2", 48, 411, 2200)
+    ops = [model.operator(synth.make_prompt(16, cfg.vocab, seed=412, r=r)) for r in (0.5, 0.25)]
+    kv.retain(0.5, st.ST_E4M3)
+    want_e4m3 = _evals(model, kv, ops, torch)
+    kv.retain(0.5, st.ST_BF16)
+    want_bf16 = _evals(model, kv, ops, torch)
+    prof = kv.profile(0.5)
+    prof.retain(0.5, st.ST_E4M3)
+    for _ in range(2):      # interleaved: neither retained cache disturbs the other
+        got_e4m3 = _evals(model, prof, ops, torch)
+        got_bf16 = _evals(model, kv, ops, torch)
+        for (a, b), (c, d) in zip(got_e4m3 + got_bf16, want_e4m3 + want_bf16):
+            assert torch.equal(a, c) and torch.equal(b, d)
+    with pytest.raises(st.StrettoError):
+        prof.retain(0.75, st.ST_E4M3)
+    with pytest.raises(st.StrettoError):
+        prof.build(torch.from_numpy(table["tokens"]).cuda())
+    with pytest.raises(st.StrettoError):
+        prof.import_profile(kv.export_profile())
+    blob = prof.export_profile()
+    fresh = model.kv_alloc(table["offsets"])
+    fresh.import_profile(blob)
+    for (a, b), (c, d) in zip(_evals(model, fresh, ops, torch), want_e4m3):
+        assert torch.equal(a, c) and torch.equal(b, d)
+    prof.close()
+    fresh.close()
+    kv.close()
+    model.close()
