@@ -4,13 +4,15 @@ Tuples are independent (each has its own document, cache and decision), so the
 float64 oracle parallelises over them without changing any arithmetic: every
 number still comes from ``oracle.operator``.  Worker processes are started with
 the ``spawn`` method (safe after the parent has initialised CUDA) and run one
-BLAS thread each; they map the model's weights from ``.npy`` files the parent
+BLAS thread each (set through the environment they start with); they map the model's weights from ``.npy`` files the parent
 writes once, so a large model is held in host memory once, not per worker.
 
 Only ``tests/`` and the CPU legs of ``bench.py`` use this module.
 """
 from __future__ import annotations
 
+import atexit
+import contextlib
 import multiprocessing as mp
 import os
 import shutil
@@ -30,6 +32,31 @@ def n_cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+@contextlib.contextmanager
+def _one_blas_thread():
+    """Spawned children read these when their BLAS library loads (threadpoolctl,
+    which would set it later, may not be installed)."""
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        yield
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _weights_dir() -> str:
+    """A fresh directory for the weight files, removed at interpreter exit even
+    if the pool is not closed (a large model's files are gigabytes)."""
+    root = tempfile.mkdtemp(prefix="oracle_w_")
+    atexit.register(shutil.rmtree, root, True)
+    return root
 
 
 def _save_weights(w: dict, root: str):
@@ -83,10 +110,11 @@ class OraclePool:
 
     def __init__(self, cfg, weights: dict, workers: Optional[int] = None):
         self.workers = max(1, int(workers or n_cores()))
-        self.root = tempfile.mkdtemp(prefix="oracle_w_")
+        self.root = _weights_dir()
         layers = _save_weights(weights, self.root)
         ctx = mp.get_context("spawn")
-        self.pool = ctx.Pool(self.workers, initializer=_init, initargs=(cfg, self.root, layers))
+        with _one_blas_thread():
+            self.pool = ctx.Pool(self.workers, initializer=_init, initargs=(cfg, self.root, layers))
 
     def run(self, docs: Dict[object, np.ndarray], ops: Sequence[dict], want_scores: bool = False,
             idx: Optional[Dict[object, List]] = None):
@@ -158,16 +186,17 @@ class OracleWorkers:
 
     def __init__(self, cfg, weights: dict, workers: Optional[int] = None):
         self.n = max(1, int(workers or n_cores()))
-        self.root = tempfile.mkdtemp(prefix="oracle_w_")
+        self.root = _weights_dir()
         layers = _save_weights(weights, self.root)
         ctx = mp.get_context("spawn")
         self.conns, self.procs = [], []
-        for _ in range(self.n):
-            a, b = ctx.Pipe()
-            p = ctx.Process(target=_worker_main, args=(b, cfg, self.root, layers), daemon=True)
-            p.start()
-            self.conns.append(a)
-            self.procs.append(p)
+        with _one_blas_thread():
+            for _ in range(self.n):
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_worker_main, args=(b, cfg, self.root, layers), daemon=True)
+                p.start()
+                self.conns.append(a)
+                self.procs.append(p)
         self.built = False
 
     def build(self, docs: Sequence[np.ndarray]):
