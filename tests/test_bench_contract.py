@@ -12,8 +12,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_the_contract_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0", "--cpu-seconds", "2"],
-                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+                        "--steps", "1", "--warmup", "0", "--cpu-workers", "2",
+                        "--heldout-tuples", "256"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
@@ -24,7 +25,10 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["unit"] == "tuples/s" and "workload" in d["config"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == d["value"] and cb["sample"]
+    # the steps it claims are the steps it ran
+    assert d["steps"] == 1 and len(cb["step_seconds"]) == 1
+    assert abs(d["ms_per_step"] - 1000.0 * cb["step_seconds"][0]) < 1e-6
     e = d["e2e"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0 and e["value"] == d["value"]
     import bench
@@ -35,7 +39,7 @@ def test_reference_arm_other_ranks_exit_quietly():
     # under torchrun only rank 0 runs and prints the reference line
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--gpus", "2", "--steps", "1", "--warmup", "0", "--cpu-seconds", "2"],
+                        "--gpus", "2", "--steps", "1", "--warmup", "0", "--cpu-workers", "2"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
