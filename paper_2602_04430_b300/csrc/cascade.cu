@@ -191,7 +191,8 @@ extern "C" int st_proxy_cascade(st_ctx* ctx, st_proxy* p, const float* x_dev, fl
   }
   // routing buffers: confidence, proxy label, unsure ids / positions, the
   // operator stages' labels and stages, the unsure count
-  const size_t need = (size_t)n * 4 * 6 + 4 * 256;
+  auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t need = 6 * r256((size_t)n * 4) + r256(8);   // exactly what the carving below takes
   if (ctx->ws_pcasc.bytes < need) {
     if (ctx->ws_pcasc.p) cudaFree(ctx->ws_pcasc.p);
     ctx->ws_pcasc.p = nullptr;
@@ -221,9 +222,11 @@ extern "C" int st_proxy_cascade(st_ctx* ctx, st_proxy* p, const float* x_dev, fl
   if ((rc = st_cascade_compact(ctx, conf, nullptr, n, tau, u_pos, cnt + 1, stream)) != ST_OK) return rc;
   int32_t k = 0;
   cudaError_t e = cudaMemcpyAsync(&k, cnt, 4, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: count copy: ") + cudaGetErrorString(e));
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: proxy stage: ") + cudaGetErrorString(e));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // leave no error pending for the next call
+    return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: proxy stage: ") + cudaGetErrorString(e));
+  }
   if (counts_host) counts_host[0] = n;
   if (k > 0 && (rc = st_cascade_run(n_stages, stages, u_ids, k, u_lab, u_stg, counts_host ? counts_host + 1 : nullptr,
                                     nullptr, stream)) != ST_OK) {
