@@ -55,6 +55,7 @@ extern "C" {
 #define ST_ETIMEOUT 4      /* a bounded device wait gave up */
 #define ST_ENAN 5          /* a NaN retention score, or NaN map-operator logits */
 #define ST_EUNSUPPORTED 6  /* shape not supported by the compiled kernels */
+#define ST_ERANGE 7        /* (device status) a tuple id outside [0, T) */
 
 /* ---- element types ---- */
 #define ST_F32 0           /* IEEE float32 */
@@ -341,7 +342,9 @@ int st_op_create(st_ctx* ctx, const st_op* op, st_operator** out);
 void st_op_free(st_operator* op);
 
 /* Online execution of one operator (Sec. 5) on the tuples tuple_ids_dev[0..n-1]
- * (DEVICE int32, each < T, not checked on the device) of `kv`, whose retained
+ * (DEVICE int32, each in [0, T); an id outside it is evaluated as tuple 0 and
+ * recorded in the device status word, which st_status reports as ST_ERANGE)
+ * of `kv`, whose retained
  * profile must have r >= op->r (a smaller r reads the rank-order prefix
  * n_keep(L, op->r), which is exactly the smaller profile's set).
  * Outputs: logits_dev DEVICE float32 [n][n_labels] (label-token logits at the

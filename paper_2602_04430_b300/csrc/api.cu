@@ -854,6 +854,7 @@ extern "C" int st_status(st_ctx* ctx, void* stream) {
     return fail(ctx, h, h == ST_ETIMEOUT ? "device status: a bounded wait timed out"
                         : h == ST_ENAN   ? "device status: non-finite logits in a map operator step"
                         : h == ST_EINVAL ? "device status: a token id outside the vocabulary"
+                        : h == ST_ERANGE ? "device status: a tuple id outside [0, T)"
                                          : "device status: error");
   return ST_OK;
 }
@@ -1009,6 +1010,7 @@ int make_opset(st_ctx* ctx, const st_kv* kv, int n_ops, const st_operator* const
   const st_model_cfg& c = ctx->cfg;
   *os = OpSet();
   os->n_ops = n_ops;
+  os->T = kv->T;
   int64_t rows = 0;
   int64_t pairs = 0;
   for (int k = 0; k < n_ops; ++k) {
@@ -1072,11 +1074,11 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_pairs(os, p0, np, row_base, kv->off, w.tup, w.len, w.nk, w.prow, w.pP, w.pop, w.pj, s);
+    eval_pairs(os, p0, np, row_base, kv->off, w.tup, w.len, w.nk, w.prow, w.pP, w.pop, w.pj, ctx->dstatus, s);
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_rows(os, p0, row_base, M, kv->off, w.pos, w.tok, w.rowpair, s);
+    eval_rows(os, p0, row_base, M, kv->off, w.pos, w.tok, w.rowpair, ctx->dstatus, s);
   }
   if (c.dtype == ST_BF16) {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);

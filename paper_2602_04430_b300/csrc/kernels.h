@@ -78,6 +78,7 @@ struct OpDev {
 };
 struct OpSet {
   int n_ops = 0;
+  int T = 0;                            // tuples of the cache: valid ids are [0, T)
   OpDev op[ST_MAX_OPS];
 };
 
@@ -101,11 +102,13 @@ void build_rowinfo(const int64_t* off, int t0, int t1, int64_t r0, int64_t rows,
 // per pair (eval_pairs) its tuple, document length, retained count, prompt row
 // (relative to row_base), prompt length, operator and index within the
 // operator; per row (eval_rows) its RoPE position, prompt token and pair.
+// A tuple id outside [0, os.T) is replaced by 0 and ST_ERANGE is recorded in
+// *status (first error wins).
 void eval_pairs(const OpSet& os, int p0, int np, int64_t row_base, const int64_t* off, int32_t* tup,
                 int32_t* len, int32_t* nk, int32_t* prow, int32_t* pP, int32_t* pop, int32_t* pj,
-                cudaStream_t s);
+                int* status, cudaStream_t s);
 void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const int64_t* off,
-               int32_t* pos, int32_t* tok, int32_t* rowpair, cudaStream_t s);
+               int32_t* pos, int32_t* tok, int32_t* rowpair, int* status, cudaStream_t s);
 // Attention work list: (pair, 128-row block) entries, longest retained
 // documents first; G = query heads per kv head.
 // nq: query positions per pair (0: its prompt length).

@@ -64,18 +64,29 @@ __device__ __forceinline__ int op_of_row(const OpSet& os, int64_t gr) {
   return k;
 }
 
+// The tuple id at position j of operator o, checked against [0, T): an id
+// outside it is recorded in *status and evaluated as tuple 0, so that no read
+// leaves the cache.
+__device__ __forceinline__ int checked_tuple(const OpSet& os, const OpDev& o, int j, int* status) {
+  const int t = o.tuple_ids[j];
+  if ((unsigned)t < (unsigned)os.T) return t;
+  atomicCAS(status, ST_OK, ST_ERANGE);
+  return 0;
+}
+
 // Thread per pair of [p0, p0 + np): tuple, length, retained count n_keep(L, r)
 // of its operator, prompt row (relative to row_base), prompt length, operator,
 // index within the operator.
 __global__ void k_eval_pairs(OpSet os, int p0, int np, int64_t row_base,
                              const int64_t* __restrict__ off, int32_t* tup, int32_t* len,
-                             int32_t* nk, int32_t* prow, int32_t* pP, int32_t* pop, int32_t* pj) {
+                             int32_t* nk, int32_t* prow, int32_t* pP, int32_t* pop, int32_t* pj,
+                             int* status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   const int gp = p0 + i, k = op_of_pair(os, gp);
   const OpDev& o = os.op[k];
   const int j = gp - o.pair0;
-  const int t = o.tuple_ids[j];
+  const int t = checked_tuple(os, o, j, status);
   const int L = (int)(off[t + 1] - off[t]);
   tup[i] = t;
   len[i] = L;
@@ -90,14 +101,14 @@ __global__ void k_eval_pairs(OpSet os, int p0, int np, int64_t row_base,
 // the prompt token, and the row's pair (relative to p0).
 __global__ void k_eval_rows(OpSet os, int p0, int64_t row_base, int64_t rows,
                             const int64_t* __restrict__ off, int32_t* pos, int32_t* tok,
-                            int32_t* rowpair) {
+                            int32_t* rowpair, int* status) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= rows) return;
   const int64_t gr = row_base + m;
   const int k = op_of_row(os, gr);
   const OpDev& o = os.op[k];
   const int j = (int)((gr - o.row0) / o.P), p = (int)((gr - o.row0) % o.P);
-  const int t = o.tuple_ids[j];
+  const int t = checked_tuple(os, o, j, status);
   pos[m] = (int32_t)(off[t + 1] - off[t]) + p;
   tok[m] = o.prompt[p];
   rowpair[m] = o.pair0 + j - p0;
@@ -105,16 +116,16 @@ __global__ void k_eval_rows(OpSet os, int p0, int64_t row_base, int64_t rows,
 
 void eval_pairs(const OpSet& os, int p0, int np, int64_t row_base, const int64_t* off, int32_t* tup,
                 int32_t* len, int32_t* nk, int32_t* prow, int32_t* pP, int32_t* pop, int32_t* pj,
-                cudaStream_t s) {
+                int* status, cudaStream_t s) {
   if (np <= 0) return;
   k_eval_pairs<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(os, p0, np, row_base, off, tup, len, nk,
-                                                           prow, pP, pop, pj);
+                                                           prow, pP, pop, pj, status);
 }
 void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const int64_t* off,
-               int32_t* pos, int32_t* tok, int32_t* rowpair, cudaStream_t s) {
+               int32_t* pos, int32_t* tok, int32_t* rowpair, int* status, cudaStream_t s) {
   if (rows <= 0) return;
   k_eval_rows<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(os, p0, row_base, rows, off, pos, tok,
-                                                             rowpair);
+                                                             rowpair, status);
 }
 
 // Attention work list: every pair contributes ceil(P G / 128) entries (pair,

@@ -200,6 +200,31 @@ def test_out_of_range_token_is_reported_not_read(run):
     assert torch.isfinite(lg).all()
 
 
+def test_out_of_range_tuple_id_is_reported_not_read(run):
+    """A tuple id outside [0, T) is caught by the planning kernels' bounds
+    check: it is evaluated as tuple 0 (no read leaves the cache), st_status
+    reports ST_ERANGE once, and the other ids' results are unchanged."""
+    import torch
+    from paper_2602_04430_b300 import stretto, synth
+    cfg, kv, model = run["cfg"], run["kv"], run["model"]
+    kv.retain(1.0)
+    opr = model.operator(synth.make_prompt(16, cfg.vocab, seed=9, label_ids=(1, 0), r=1.0))
+    model.status()
+    good = torch.tensor([5, 0, 9], dtype=torch.int32, device="cuda")
+    ref, _ = opr.eval(kv, good)
+    torch.cuda.synchronize()
+    model.status()
+    for bad in (kv.T, -1, 1 << 30):
+        ids = torch.tensor([5, bad, 9], dtype=torch.int32, device="cuda")
+        lg, _ = opr.eval(kv, ids)
+        torch.cuda.synchronize()
+        with pytest.raises(stretto.StrettoError) as e:
+            model.status()
+        assert e.value.code == stretto.ST_ERANGE
+        model.status()                               # reported once, then clear
+        np.testing.assert_array_equal(lg.cpu().numpy(), ref.cpu().numpy())
+
+
 def test_kv_alloc_validates_offsets(run):
     """Empty documents, documents past max_pos - 1, a nonzero first offset and
     an empty table are refused on the host, before any device work."""
