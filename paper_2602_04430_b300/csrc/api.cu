@@ -995,7 +995,7 @@ size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t pairs, char* base, Eva
   b.pP = (int32_t*)take(pairs * 4);
   b.pop = (int32_t*)take(pairs * 4);
   b.pj = (int32_t*)take(pairs * 4);
-  b.order = (int32_t*)take(pairs * max_blocks * 2 * 4);
+  b.order = (int32_t*)take(pairs * max_blocks * WORK_INTS * 4);
   if (w) *w = b;
   return off + 256;
 }
@@ -1082,7 +1082,7 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
   }
   if (c.dtype == ST_BF16) {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_worklist(w.nk, w.pP, np, G, 0, ctx->longest_first != 0, w.order, s);
+    eval_worklist(w.nk, w.pP, w.tup, w.prow, kv->offp, np, G, 0, ctx->longest_first != 0, w.order, s);
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
@@ -1481,7 +1481,7 @@ extern "C" int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
     m->K = take((size_t)c.layers * layer_elems * ctx->esz);
     m->V = take((size_t)c.layers * layer_elems * ctx->esz);
     m->pq0 = (int32_t*)take((size_t)per * 4);
-    m->work = (int32_t*)take((size_t)per * 8);
+    m->work = (int32_t*)take((size_t)per * WORK_INTS * 4);
     m->logits = (float*)take((size_t)per * c.vocab * 4);
     m->xn = take((size_t)per * c.d * ctx->esz);
     return off + 256;
@@ -1499,7 +1499,7 @@ extern "C" int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
     RC(eval_chunk(ctx, kv, os, i0, i0 + nc, (int64_t)i0 * P, (int64_t)nc * P, w, s, &mp));
     if (c.dtype == ST_BF16) {
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      eval_worklist(w.nk, w.pP, nc, G, 1, ctx->longest_first != 0, mp.work, s);
+      eval_worklist(w.nk, w.pP, w.tup, w.prow, kv->offp, nc, G, 1, ctx->longest_first != 0, mp.work, s);
     }
     for (int t = 1; t < n_gen; ++t) RC(decode_step(ctx, kv, P, nc, t, w, mp, s));
   }

@@ -170,22 +170,30 @@ struct Work {
   __device__ void decode(const AttnParams& a, const int32_t* items, int w, int zb_count) {
     G = a.hq / a.hkv;
     if (MODE == 1) {
-      // work list entry (pair, 128-row block), longest documents first; kv head fastest
+      // work list record (pair, 128-row block, P, retained slots, prompt row,
+      // -, offp of the tuple), longest documents first; kv head fastest
       const int e = w / a.hkv;
       g = w % a.hkv;
-      i = items[2 * e];
-      const int zb = items[2 * e + 1];
-      P = a.pP[i];                                 // prompt keys of the pair
+      const int4* rec = reinterpret_cast<const int4*>(items + (int64_t)WORK_INTS * e);
+      const int4 r0 = rec[0], r1 = rec[1];
+      i = r0.x;
+      const int zb = r0.y;
+      P = r0.z;                                    // prompt keys of the pair
+      prompt_row0 = r1.x;
+      qbase = prompt_row0;
+      if (a.pq0) {
+        // decode steps: the prompt grows and moves every step (read live)
+        P = a.pP[i];
+        prompt_row0 = a.prow[i];
+        qbase = a.pq0[i];
+      }
       const int nq = a.nq > 0 ? a.nq : P;          // its queries: the last nq positions
       qoff = P - nq;
       row_base = zb * ROWS;
       rows = min(ROWS, nq * G - row_base);
       lim_max = qoff + (row_base + rows - 1) / G;
-      const int tt = a.tup[i];
-      n_doc = a.nk[i];
-      doc_row0 = (int64_t)g * a.Rp_cap + a.offp[tt];
-      prompt_row0 = a.prow[i];
-      qbase = a.pq0 ? a.pq0[i] : prompt_row0;
+      n_doc = r0.w;
+      doc_row0 = (int64_t)g * a.Rp_cap + (int64_t)(((uint64_t)(uint32_t)r1.w << 32) | (uint32_t)r1.z);
       qrow0 = qbase + row_base / G;
       n_doc_tiles = (n_doc + TK - 1) / TK;
       n_tiles = n_doc_tiles + (min(P, lim_max + 1) + TK - 1) / TK;

@@ -112,8 +112,14 @@ void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const in
 // Attention work list: (pair, 128-row block) entries, longest retained
 // documents first; G = query heads per kv head.
 // nq: query positions per pair (0: its prompt length).
-void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int nq, bool longest_first,
-                   int32_t* list, cudaStream_t s);
+// Each entry is a fully decoded item record of WORK_INTS int32 (32 bytes, one
+// pair of 16-byte loads in the attention kernel): pair, row block, prompt
+// length, retained slots, first prompt row, (unused), and the tuple's padded
+// retained offset offp[tup] as an int64 in two words.
+constexpr int WORK_INTS = 8;
+void eval_worklist(const int32_t* nk, const int32_t* pP, const int32_t* tup, const int32_t* prow,
+                   const int64_t* offp, int np, int G, int nq, bool longest_first, int32_t* list,
+                   cudaStream_t s);
 template <typename act_t>
 void qstats(const act_t* q, const int64_t* off, int t0, int t1, int64_t r0, int hq, int hkv,
             int hd, float* mu, float* s2, cudaStream_t s);

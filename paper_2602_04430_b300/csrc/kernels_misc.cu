@@ -129,12 +129,15 @@ void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const in
 }
 
 // Attention work list: every pair contributes ceil(P G / 128) entries (pair,
-// 128-row block), grouped longest retained document first (a counting sort on
+// 128-row block, as decoded records), grouped longest retained document first (a counting sort on
 // the 128-key tile count, capped at 1023), so that a persistent grid walking
 // the list ends with its shortest items (sorted = 0: one bucket, arrival
 // order).  One block of 1024 threads; the order within a bucket is arbitrary.
 __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restrict__ nk,
-                                                        const int32_t* __restrict__ pP, int n, int G,
+                                                        const int32_t* __restrict__ pP,
+                                                        const int32_t* __restrict__ tup,
+                                                        const int32_t* __restrict__ prow,
+                                                        const int64_t* __restrict__ offp, int n, int G,
                                                         int nq, int sorted, int32_t* list) {
   __shared__ int cnt[1024];
   __shared__ int wsum[32];
@@ -170,17 +173,20 @@ __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restric
   for (int i = tid; i < n; i += 1024) {
     const int nb = blocks(i);
     const int at = atomicAdd(&cnt[bucket(i)], nb);
+    const int64_t o = offp[tup[i]];
     for (int z = 0; z < nb; ++z) {
-      list[2 * (at + z)] = i;
-      list[2 * (at + z) + 1] = z;
+      int4* e = reinterpret_cast<int4*>(list + (int64_t)WORK_INTS * (at + z));
+      e[0] = make_int4(i, z, pP[i], nk[i]);
+      e[1] = make_int4(prow[i], 0, (int)(uint32_t)o, (int)(o >> 32));
     }
   }
 }
 
-void eval_worklist(const int32_t* nk, const int32_t* pP, int np, int G, int nq, bool longest_first,
-                   int32_t* list, cudaStream_t s) {
+void eval_worklist(const int32_t* nk, const int32_t* pP, const int32_t* tup, const int32_t* prow,
+                   const int64_t* offp, int np, int G, int nq, bool longest_first, int32_t* list,
+                   cudaStream_t s) {
   if (np <= 0) return;
-  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, np, G, nq, longest_first ? 1 : 0, list);
+  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, tup, prow, offp, np, G, nq, longest_first ? 1 : 0, list);
 }
 
 // Retained counts and padded (64-slot) offsets of every tuple, one block.
