@@ -5,11 +5,9 @@
 //   S = Q K^T   tcgen05.mma M128 K16 x4, N = the tile's visible key columns
 //               rounded up to 32; Q and K K-major (128-byte swizzle) in shared
 //               memory, f32 accumulator in TMEM (two 128-column buffers).
-//   softmax     8 warps, two threads per query row: the row is their TMEM
-//               lane, each takes one half of the tile's columns, and the two
-//               exchange their row maxima through shared memory (an mbarrier
-//               per warp pair) so that both use the same running max; P is
-//               written back to TMEM (tcgen05.st) as packed 16-bit pairs.
+//   softmax     4 warps, one thread per query row: the row is that thread's TMEM
+//               lane, so max / exp2 / sum need no shuffles; P is written back
+//               to TMEM (tcgen05.st) as packed 16-bit pairs.
 //   O += P V    tcgen05.mma M128 N64 K16, A = P read from TMEM, B = V read
 //               MN-major from its [key][dim] shared-memory tile; O accumulates
 //               in TMEM (one 64-column buffer per item, two in flight). A row's
@@ -53,10 +51,9 @@ constexpr int ctas_per_sm(int nb) { return nb == 1 ? 2 : 1; }
 constexpr int NKV_MAX = 5, NRAW_MAX = 2;
 constexpr int nkv(bool fp8, int nb) { return nb == 1 ? 2 : (fp8 ? 4 : 5); }
 constexpr int nraw(bool fp8, int nb) { return fp8 ? 2 : 0; }
-// warps 0-7 softmax (two threads per query row), 8 item decode + Q and K/V
-// loads, 9 MMA issue, (E4M3 KV) 10 widens the K codes to f16, 11 the V codes
-constexpr int WARP_LOAD = 8, WARP_MMA = 9, WARP_WIDEN = 10;
-constexpr int nthreads(bool fp8) { return fp8 ? 384 : 320; }
+// warps 0-3 softmax, 4 item decode + Q and K/V loads, 5 MMA issue,
+// (E4M3 KV) 6 widens the K codes to f16, 7 the V codes
+constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
 constexpr int OFF_Q = 0;                           // 2 x 16 KB
 constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // nkv x 16 KB
 constexpr int off_v(bool fp8, int nb, int tk) { return OFF_K + nkv(fp8, nb) * tk * 128; }   // nkv x tk x 128 B
@@ -64,9 +61,7 @@ constexpr int off_raw(bool fp8, int nb, int tk) { return off_v(fp8, nb, tk) + nk
 constexpr int raw_bytes(int tk) { return 2 * tk * HD; }   // K + V codes of one tile
 constexpr int off_bar(bool fp8, int nb, int tk) { return off_raw(fp8, nb, tk) + nraw(fp8, nb) * raw_bytes(tk); }
 constexpr int off_work(bool fp8, int nb, int tk) { return off_bar(fp8, nb, tk) + 512; }   // 2 decoded work items
-// the softmax threads' exchange of row maxima and sums: [2 parities][2 halves][128 rows] floats
-constexpr int off_xch(bool fp8, int nb, int tk) { return off_work(fp8, nb, tk) + 256; }
-constexpr size_t smem_bytes(bool fp8, int nb, int tk) { return (size_t)off_xch(fp8, nb, tk) + 2048 + 1024; }
+constexpr size_t smem_bytes(bool fp8, int nb, int tk) { return (size_t)off_work(fp8, nb, tk) + 256 + 1024; }
 // TMEM columns: S buffers [0, tk nb), O buffers [tk nb, (tk + 64) nb), P buffers
 // [(tk + 64) nb, (1.5 tk + 64) nb) -- within 256 nb for tk <= 128
 constexpr uint32_t tmem_cols(int nb) { return 256 * nb; }
@@ -80,8 +75,6 @@ struct Bars {
   uint64_t q_full[2], q_empty[2];
   // E4M3: K / V halves of a stage widened; raw code stages loaded / free
   uint64_t kc_full[NKV_MAX], vc_full[NKV_MAX], raw_full[NRAW_MAX], raw_empty[NRAW_MAX];
-  // the two softmax warps of each row quarter: one exchange per phase (64 arrivals)
-  uint64_t xch[4];
   uint32_t tmem;
 };
 static_assert(sizeof(Bars) <= 512, "barrier block");
@@ -279,18 +272,17 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     }
     for (int s = 0; s < 2; ++s) {
       ptx::mbar_init(&bars->s_full[s], 1);
-      ptx::mbar_init(&bars->s_free[s], 256);
-      ptx::mbar_init(&bars->p_full[s], 256);
+      ptx::mbar_init(&bars->s_free[s], 128);
+      ptx::mbar_init(&bars->p_full[s], 128);
       ptx::mbar_init(&bars->pv_done[s], 1);
-      ptx::mbar_init(&bars->o_free[s], 256);
+      ptx::mbar_init(&bars->o_free[s], 128);
       ptx::mbar_init(&bars->q_full[s], 1);
       // the MMA's commit once the item's Q is consumed + every other reader of the slot
-      ptx::mbar_init(&bars->q_empty[s], 1 + 256 + (FP8 ? 64 : 0));
+      ptx::mbar_init(&bars->q_empty[s], 1 + 128 + (FP8 ? 64 : 0));
     }
-    for (int s = 0; s < 4; ++s) ptx::mbar_init(&bars->xch[s], 64);
     ptx::fence_mbar_init();
   }
-  if (warp == WARP_MMA) {
+  if (warp == 5) {
     ptx::tmem_alloc(&bars->tmem, TMEM_COLS);
     ptx::tmem_relinquish();
   }
@@ -299,7 +291,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
   ptx::tc_fence_after();
   const uint32_t tmem = bars->tmem;
 
-  if (warp == WARP_LOAD) {
+  if (warp == 4) {
     // ------------------------------------------------------------ decode + TMA
     if (lane == 0) {
       ptx::tma_prefetch_desc(&tmQ);
@@ -433,7 +425,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
           ok = false;
       if (!ok) atomicExch(status, ST_ETIMEOUT);
     }
-  } else if (warp == WARP_MMA) {
+  } else if (warp == 5) {
     // ------------------------------------------------------------ MMA issue
     // Two cursors walk the CTA's (item, tile) sequence: the S cursor issues
     // S = Q K^T of tile cs, the P.V cursor issues P.V of tile cp (cp <= cs).
@@ -538,13 +530,13 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
             atomicExch(status, ST_ETIMEOUT);
     }
     __syncwarp();
-  } else if (FP8 && warp >= WARP_WIDEN) {
+  } else if (FP8 && warp >= 6) {
     // ------------------------------------------------------------ widen E4M3 -> f16
     // Warp 6 widens the K codes of each document tile, warp 7 the V codes, into
     // the swizzled MMA stage (the block scales act later, in f32); lane l takes
     // rows l, l + 32, ...  K is widened once the stage's previous S has read it,
     // V once the previous P.V has, so the next S does not wait for a P.V.
-    const int half = warp - WARP_WIDEN;   // 0: K, 1: V
+    const int half = warp - 6;   // 0: K, 1: V
     uint64_t* const empty = half == 0 ? bars->k_empty : bars->v_empty;
     uint64_t* const full = half == 0 ? bars->kc_full : bars->vc_full;
     uint8_t* const dst0 = smem + (half == 0 ? OFF_K : OFF_V);
@@ -605,60 +597,44 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       }
     }
     if (!ok) atomicExch(status, ST_ETIMEOUT);
-  } else {
+  } else if (warp < 4) {
     // ------------------------------------------------------------ softmax warps
-    // Two threads per query row: warp w holds rows 32 (w & 3) .. + 31 (its TMEM
-    // lanes) and column half hf = w >> 2 of every tile (keys hf TK/2 ..
-    // hf TK/2 + TK/2 - 1).  The two threads of a row exchange their maxima
-    // through shared memory (an mbarrier per warp pair), so both take the same
-    // running max; each keeps the partial row sum of its half, added at the
-    // item's end, and writes its half of P and of the output row.
-    constexpr int HK = TK / 2, HCH = NCH / 2;       // keys, 32-key chunks per half
-    static_assert(HCH >= 1, "half tiles of at least 32 keys");
-    const int q4 = warp & 3, hf = warp >> 2;
-    const int r = q4 * 32 + lane;              // query row == TMEM lane
+    const int r = threadIdx.x;                 // query row == TMEM lane
     const float sl2 = a.scale * 1.4426950408889634f;
-    const uint32_t lane_base = (uint32_t)((q4 * 32) << 16);
-    float* const xbuf = reinterpret_cast<float*>(smem + off_xch(FP8, NB, TK));   // [2 parities][2 halves][128]
-    uint64_t* const xbar = &bars->xch[q4];
-    uint32_t xph = 0;                          // exchanges of this warp pair so far
-    // one exchange with the row's other thread: publish v, return the other half's
-    auto exchange = [&](float v, float* other) -> bool {
-      float* xb = xbuf + (xph & 1) * 256;
-      xb[hf * 128 + r] = v;
-      ptx::mbar_arrive(xbar);
-      if (!ptx::mbar_wait(xbar, xph & 1)) return false;
-      *other = xb[(hf ^ 1) * 128 + r];
-      ++xph;
-      return true;
-    };
+    const uint32_t lane_base = (uint32_t)((warp * 32) << 16);
     __half* og = reinterpret_cast<__half*>(a.o);   // O feeds the half-operand O projection
     bool ok = true;
     uint32_t c = 0, qc = 0;
     // With two O buffers an item's O is read out after the next item's first
     // tile, by when its last P.V has long completed; with one, at its end.
     // O buffer ob of the item whose last tile was cl: wait for its last P.V,
-    // read this half's 32 columns, release the buffer, write them normalised
-    // by the row sum l (orow < 0: no row)
+    // release the buffer, write the row normalised by l (orow < 0: no row)
     auto read_out = [&](int ob, uint32_t cl, float l, int64_t orow) -> bool {
       if (!ptx::mbar_wait(&bars->pv_done[cl % NB], (cl / NB) & 1)) return false;
       ptx::tc_fence_after();
-      const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD + 32 * hf;
+      const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD;
       const float inv = l > 0.f ? 1.f / l : 0.f;
-      uint32_t o0[32];
-      ST_TMEM_LD32(o_addr, o0);
-      ptx::tmem_wait_ld();
-      ST_TMEM_TIE32(o0);
-      ptx::tc_fence_before();
-      ptx::mbar_arrive(&bars->o_free[ob]);
-      if (orow >= 0) {
-        uint4* dst = reinterpret_cast<uint4*>(og + orow * HD + 32 * hf);
+      uint4* dst = reinterpret_cast<uint4*>(og + (orow >= 0 ? orow : 0) * HD);
+      // two 32-column halves (the buffer is released once both are loaded)
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        uint32_t o0[32];
+        ST_TMEM_LD32(o_addr + 32 * h, o0);
+        ptx::tmem_wait_ld();
+        ST_TMEM_TIE32(o0);
+        if (h == 1) {
+          ptx::tc_fence_before();
+          ptx::mbar_arrive(&bars->o_free[ob]);
+        }
+        if (orow >= 0) {
 #pragma unroll
-        for (int e = 0; e < 32; e += 8)
-          dst[e / 8] = make_uint4(pack_f16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
-                                  pack_f16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
-                                  pack_f16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
-                                  pack_f16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
+          for (int e = 0; e < 32; e += 8)
+            dst[4 * h + e / 8] =
+                make_uint4(pack_f16(__uint_as_float(o0[e]) * inv, __uint_as_float(o0[e + 1]) * inv),
+                           pack_f16(__uint_as_float(o0[e + 2]) * inv, __uint_as_float(o0[e + 3]) * inv),
+                           pack_f16(__uint_as_float(o0[e + 4]) * inv, __uint_as_float(o0[e + 5]) * inv),
+                           pack_f16(__uint_as_float(o0[e + 6]) * inv, __uint_as_float(o0[e + 7]) * inv));
+        }
       }
       return true;
     };
@@ -674,80 +650,78 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       const Work<MODE, TK>& W = slots[qb];
       const int pos = (W.row_base + r) / W.G;
 
-      // O accumulates in TMEM (buffer ob); the running max m only moves when a
+      // O accumulates in TMEM (buffer qb); the running max m only moves when a
       // row's tile maximum exceeds it by more than 8 (a factor 256 in P), and
       // then the row's O is rescaled in place before the next P.V is issued.
       float m = -INFINITY, l = 0.f;
       const int ob = qc % NB;
-      const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD + 32 * hf;
+      const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD;
       const int lim = MODE == 0 ? W.j0 + pos : W.qoff + pos;   // causal limit of this row
       for (int ti = 0; ti < W.n_tiles; ++ti, ++c) {
         const int b = c % NB;
         const TileInfo T = W.tile(ti);
-        const int nch = (T.kc + 31) >> 5;                        // 32-key chunks any row can see
-        const int mych = min(max(nch - hf * HCH, 0), HCH);       // of them, in this half
+        const int nch = (T.kc + 31) >> 5;           // 32-key chunks any row can see
         const bool causal = (MODE == 0) || T.prompt;
-        // E4M3 document tiles: the K and V scales of this half's 64-slot block,
-        // loaded before the wait for S so that their latency overlaps it
-        float ks = 1.f, vs = 1.f;
-        if (FP8 && !T.prompt && mych > 0) {
-          const float* scp = a.scales + ((W.doc_row0 + T.key0 + hf * HK) >> 6) * 2;
-          ks = scp[0];
-          vs = scp[1];
+        // E4M3 document tiles: one K and one V scale per 64-slot half of the
+        // tile, loaded before the wait for S so that their latency overlaps it
+        float ks[NHALF], vs[NHALF];
+#pragma unroll
+        for (int hf = 0; hf < NHALF; ++hf) ks[hf] = vs[hf] = 1.f;
+        if (FP8 && !T.prompt) {
+          const float* scp = a.scales + ((W.doc_row0 + T.key0) >> 6) * 2;
+          ks[0] = scp[0];
+          vs[0] = scp[1];
+          if (NHALF > 1 && T.count > 64) {
+            ks[NHALF - 1] = scp[2];
+            vs[NHALF - 1] = scp[3];
+          }
         }
         if (!ptx::mbar_wait(&bars->s_full[b], (c / NB) & 1)) { ok = false; break; }
         ptx::tc_fence_after();
-        const uint32_t sb = tmem + lane_base + b * TK + hf * HK;
-        // visible keys of this row in this half (ragged tail, causal limit)
+        const uint32_t sb = tmem + lane_base + b * TK;
+        // the row's visible chunks of S into registers with one wait, then
+        // release the TMEM buffer
+        uint32_t v[TK];
+        ST_TMEM_LD32(sb, v);
+        if (NCH > 1 && nch > 1) ST_TMEM_LD32(sb + 32, (v + 32));
+        if (NCH > 2 && nch > 2) ST_TMEM_LD32(sb + 64, (v + (NCH > 2 ? 64 : 0)));
+        if (NCH > 3 && nch > 3) ST_TMEM_LD32(sb + 96, (v + (NCH > 3 ? 96 : 0)));
+        ptx::tmem_wait_ld();
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) ST_TMEM_TIE32((v + 32 * ch));
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(&bars->s_free[b]);
+        // invisible keys of this row (ragged tail, causal limit) in the loaded
+        // chunks become -inf
         int nvis = T.count;
         if (causal) nvis = min(nvis, lim - T.key0 + 1);
-        nvis -= hf * HK;
-        // chunk ch of this half into v (one tcgen05.ld and its wait), its
-        // invisible keys as -inf
-        uint32_t v[32];
-        auto load_chunk = [&](int ch) {
-          ST_TMEM_LD32(sb + 32 * ch, v);
-          ptx::tmem_wait_ld();
-          ST_TMEM_TIE32(v);
-          const int lo = nvis - 32 * ch;
-          if (lo < 32) {
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int lo = nvis - 32 * ch;    // visible keys of this chunk
+          if (ch < nch && lo < 32) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (j >= lo) v[j] = 0xFF800000u;
+              if (j >= lo) v[32 * ch + j] = 0xFF800000u;
           }
-        };
-        auto release_s = [&]() {
-          ptx::tc_fence_before();
-          ptx::mbar_arrive(&bars->s_free[b]);
-        };
-        // pass 1: this half's maximum of the scaled scores (a positive scale
-        // commutes with the max), one chunk at a time.  With one chunk per half
-        // its values stay in registers and S is released at once; with two, S
-        // is read again in pass 2 (32 live scores instead of 64) and released
-        // after that read.
-        float pm = -INFINITY;
+        }
+        // row maximum of the scaled scores (a positive scale commutes with the max)
+        float cm[4];
 #pragma unroll
-        for (int ch = 0; ch < HCH; ++ch)
-          if (ch < mych) {
-            load_chunk(ch);
-            pm = fmaxf(pm, chunk_max(v));
-          }
-        if (HCH == 1 || mych == 0) release_s();
-        if (mych > 0) pm *= ks;
-        float om;
-        if (!exchange(pm, &om)) { ok = false; break; }
-        const float mx = fmaxf(pm, om) * sl2;
+        for (int ch = 0; ch < 4; ++ch)
+          cm[ch] = (ch < NCH && ch < nch) ? chunk_max(v + 32 * (ch < NCH ? ch : 0)) * ks[(ch < NCH ? ch : 0) >> 1]
+                                          : -INFINITY;
+        const float mx = max3(cm[0], cm[1], fmaxf(cm[2], cm[3])) * sl2;
         const bool need = mx > m + 8.f;
         if (__any_sync(0xffffffffu, need)) {
           const float mn = need ? mx : m;
           const float alpha = need ? ex2(m - mn) : 1.f;
           if (ti > 0) {
-            // O holds this item's earlier P.V products: scale this half of the row in place
+            // O holds this item's earlier P.V products: scale the row in place
             if (!ptx::mbar_wait(&bars->pv_done[(c - 1) % NB], ((c - 1) / NB) & 1)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint64_t a2 = f2pack(alpha, alpha);
 #pragma unroll 1
-            for (int part = 0; part < 2; ++part) {
+            for (int part = 0; part < 4; ++part) {
               uint32_t o0[16];
               ST_TMEM_LD16(o_addr + 16 * part, o0);
               ptx::tmem_wait_ld();
@@ -769,28 +743,23 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         // the P buffer b was last read by the P.V of tile c - NB
         if (c >= (uint32_t)NB && !ptx::mbar_wait(&bars->pv_done[b], ((c - NB) / NB) & 1)) { ok = false; break; }
         ptx::tc_fence_after();
-        // probabilities of this half's visible chunks, packed in pairs (key 2j
-        // low, 2j+1 high), 16 TMEM columns per 32-key chunk
-        const uint32_t pcol = tmem + lane_base + COL_P + b * HD + hf * (HK / 2);
+        // probabilities of the visible chunks, packed in pairs (key 2j low, 2j+1
+        // high), 16 TMEM columns per 32-key chunk
+        const uint32_t pcol = tmem + lane_base + COL_P + b * HD;
         // p = 2^(s * mul - base), two keys per packed FP32 operation
         const uint64_t nb2 = f2pack(-base, -base);
-        const float mul = sl2 * ks;
-        const uint64_t m2 = f2pack(mul, mul), vs2 = f2pack(vs, vs);
         uint64_t rs2[2] = {0, 0};           // packed partial row sums (+0.0f lanes)
 #pragma unroll
-        for (int ch = 0; ch < HCH; ++ch) {
-          if (ch < mych) {
-            if (HCH > 1) {
-              // pass 2: the chunk again (S is released after the half's last chunk)
-              load_chunk(ch);
-              if (ch == mych - 1) release_s();
-            }
+        for (int ch = 0; ch < NCH; ++ch) {
+          if (ch < nch) {
+            const float mul = sl2 * ks[ch >> 1];
+            const uint64_t m2 = f2pack(mul, mul), vs2 = f2pack(vs[ch >> 1], vs[ch >> 1]);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               uint32_t pk[8];
 #pragma unroll
               for (int k = 0; k < 16; k += 2) {
-                const int kk = 16 * h + k;
+                const int kk = 32 * ch + 16 * h + k;
                 const uint64_t y = fma2((uint64_t)v[kk] | ((uint64_t)v[kk + 1] << 32), m2, nb2);
                 const uint64_t p = f2pack(ex2(f2lo(y)), ex2(f2hi(y)));
                 rs2[(k >> 1) & 1] = add2(rs2[(k >> 1) & 1], p);
@@ -815,10 +784,6 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         if (NB == 2 && ti == 0 && pend_on && !(ok = read_out(pend_ob, pend_cl, pend_l, pend_orow))) break;
       }
       if (!ok) break;
-      // the row sum: both halves' partial sums (the same float addition on both threads)
-      float ol;
-      if (!exchange(l, &ol)) { ok = false; break; }
-      const float lt = hf == 0 ? l + ol : ol + l;
       // the output row of this thread (-1: past the item's rows)
       int64_t orow = -1;
       {
@@ -832,12 +797,12 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       ptx::mbar_arrive(&bars->q_empty[qb]);
       if (NB == 1) {
         // a single O buffer is read out at once
-        if (!(ok = read_out(ob, c - 1, lt, orow))) break;
+        if (!(ok = read_out(ob, c - 1, l, orow))) break;
       } else {
         pend_on = true;
         pend_ob = ob;
         pend_cl = c - 1;
-        pend_l = lt;
+        pend_l = l;
         pend_orow = orow;
       }
     }
@@ -846,7 +811,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == WARP_MMA) {
+  if (warp == 5) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, TMEM_COLS);
   }
