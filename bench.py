@@ -53,10 +53,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tuples/s: proxy+FP8 vs plain BF16 at >=99% label agreement; % HBM roofline"
-# DRAM bytes per projection-GEMM launch of the headline workload (k_gemm_tc2 on
-# the 16-layer model's operator pass), from one ncu capture; None until taken
-# for the current kernel.
-GEMM_TRAFFIC_PER_LAUNCH = None
+# DRAM traffic of the projection GEMM (k_gemm_tc2) on the 16-layer model's
+# operator pass, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of one layer's four launches -- QKV, O, gate/up and
+# down projections -- at 32,768 prompt rows (1024 pairs); profiles/
+# gemm_tc2_c3_operator_32768rows.md.  Every term but the weights (3 % of it)
+# grows with the rows, so a launch's traffic is scaled by its FLOPs.
+GEMM_CAPTURE = {"dram_bytes": 3125.74e6, "flops": 2954.9e9, "algorithmic_bytes": 2774.3e6, "launches": 4}
 HEADLINE_SEEDS = {"weights": 5151, "prompt": 5152, "proxy_init": 5153, "batches": 5154,
                   "train": 5200, "val": 5250, "heldout": 5300, "cpu_sample": 5400}
 
@@ -92,6 +95,11 @@ def parse():
     ap.add_argument("--batched-tuples", type=int, default=2048)
     ap.add_argument("--map-tuples", type=int, default=1024)
     ap.add_argument("--map-gen", type=int, default=16)
+    # small cases for ncu captures (a few GB on the device; nothing timed)
+    ap.add_argument("--case", choices=["gemm16", "attn8-bf16", "attn8-e4m3"], default=None,
+                    help="run one small profiling case and exit: gemm16 = the 16-layer operator pass over "
+                         "1024 pairs (32 tuples x 32, 32768 prompt rows, r = 0.25, E4M3 profile), twice; "
+                         "attn8-* = the 8-layer operator over 512 tuples at r = 0.5, twice")
     return ap.parse_args()
 
 
@@ -360,13 +368,17 @@ def headline_arm(args, rank, stretto, synth, torch, on_model=None):
             for k in range(K):
                 a, b = ev(), ev()
                 a.record(stream)
+                torch.cuda.nvtx.range_push("plain")
                 plain()
+                torch.cuda.nvtx.range_pop()
                 b.record(stream)
                 c, d = ev(), ev()
                 l0 = model.launch_count()
                 model.prof_enable(True)
                 c.record(stream)
+                torch.cuda.nvtx.range_push("cascade")     # (ncu's launch list filters on it)
                 counts = casc()
+                torch.cuda.nvtx.range_pop()
                 d.record(stream)
                 model.prof_enable(False)
                 torch.cuda.synchronize()
@@ -976,10 +988,46 @@ def full_path_step(args, stretto, synth, torch):
     return res, (model, kv, cfg, T, tok, op)
 
 
+def profile_case(args):
+    """One small case of the operator pass for an ncu capture (see --case)."""
+    import torch
+    from paper_2602_04430_b300 import build as _b, stretto, synth
+    _b.build()
+    if args.case == "gemm16":
+        cfg, key, n, r, kvd = synth.MODELS["c3_bf16"], "c3", 32, 0.25, stretto.ST_E4M3
+        tb = synth.make_table(synth.TABLES[key], cfg.vocab, seed=5300, n_tuples=n)
+        w = synth.make_weights_device(cfg, seed=HEADLINE_SEEDS["weights"])
+        ids = torch.arange(n, dtype=torch.int32, device="cuda").repeat(32)
+        max_pos = 4096 + 64
+    else:
+        cfg, key, n, r = synth.MODELS["c2_bf16"], "c2", 512, 0.5
+        kvd = stretto.ST_E4M3 if args.case.endswith("e4m3") else stretto.ST_BF16
+        tb = synth.make_table(synth.TABLES[key], cfg.vocab, seed=1000, n_tuples=n)
+        w = synth.make_weights_device(cfg, seed=4242)
+        ids = torch.arange(n, dtype=torch.int32, device="cuda")
+        max_pos = 2048 + 64
+    model = stretto.Model(cfg, w, max_pos=max_pos)
+    kv = model.kv_alloc(tb["offsets"])
+    kv.build(torch.from_numpy(tb["tokens"]).cuda())
+    kv.retain(r, kvd)
+    op = model.operator(synth.make_prompt(32, cfg.vocab, seed=HEADLINE_SEEDS["prompt"], label_ids=(1, 0), r=r))
+    for _ in range(2):
+        lg, _ = op.eval(kv, ids)
+    torch.cuda.synchronize()
+    model.status()
+    print(json.dumps({"case": args.case, "pairs": int(ids.numel()), "max_abs_logit": float(lg.abs().max()),
+                      "device_gb": torch.cuda.max_memory_allocated() / 1e9}))
+    kv.close()
+    model.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return profile_case(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -1047,10 +1095,11 @@ def main():
                               "timed cascade passes", "bound": "tensor", "achieved": gemm_tf, "peak": tf_peak,
                     "unit": "TFLOP/s", "frac": gemm_tf / tf_peak,
                     "peak_source": f"{peak_src} bf16_tflops_sustained",
-                    "traffic": GEMM_TRAFFIC_PER_LAUNCH,
-                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch of one ncu "
-                                      "capture of this workload's operator pass" if GEMM_TRAFFIC_PER_LAUNCH
-                                      else "no capture of the current kernel on this workload",
+                    "traffic": (GEMM_CAPTURE["dram_bytes"] / GEMM_CAPTURE["flops"] * g["flops"] / g["launches"]
+                                if g["launches"] else None),
+                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture (one layer's "
+                                      "four projections at 32768 rows), scaled to this run's mean FLOPs per launch; "
+                                      "1.13x the algorithmic bytes",
                     "launches": g["launches"], "share_of_step": g["share_of_cascade"]}
         parts = {"proxy_fp8_tuples_per_s": value, "plain_bf16_tuples_per_s": plain_value,
                  "proxy_fp8_gain_vs_plain_bf16": value / plain_value,
