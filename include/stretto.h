@@ -56,6 +56,7 @@ extern "C" {
 #define ST_ENAN 5          /* a NaN retention score, or NaN map-operator logits */
 #define ST_EUNSUPPORTED 6  /* shape not supported by the compiled kernels */
 #define ST_ERANGE 7        /* (device status) a tuple id outside [0, T) */
+#define ST_ECHECK 8        /* (device status, checked build only) an index or offset check failed */
 
 /* ---- element types ---- */
 #define ST_F32 0           /* IEEE float32 */
@@ -568,7 +569,9 @@ int st_proxy_eval(st_ctx* ctx, st_proxy* p, const float* x_dev, const int32_t* r
 int st_cascade_compact(st_ctx* ctx, const float* conf_dev, const int32_t* ids_dev, int32_t n,
                        float tau, int32_t* unsure_dev, int32_t* count_dev, void* stream);
 /* Cascade merge: out_dev[i] = proxy_label_dev[i], then
- * out_dev[unsure_pos_dev[j]] = full_label_dev[j] for j < *count_dev. */
+ * out_dev[unsure_pos_dev[j]] = full_label_dev[j] for j < min(*count_dev, n)
+ * (a position outside [0, n) is skipped and recorded in the device status
+ * word, reported by st_status as ST_ERANGE). */
 int st_cascade_merge(st_ctx* ctx, const int32_t* proxy_label_dev, int32_t n,
                      const int32_t* unsure_pos_dev, const int32_t* count_dev,
                      const int32_t* full_label_dev, int32_t* out_dev, void* stream);

@@ -827,7 +827,7 @@ extern "C" int st_kv_indices(st_ctx* ctx, const st_kv* kv, double r, int32_t* id
     return fail(ctx, ST_ECUDA, std::string("st_kv_indices: ") + cudaGetErrorString(cudaGetLastError()));
   if (idx_dev) {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    gather_indices(kv->rank, kv->off, off_dev, kv->T, c.layers * c.hkv, kv->R, o[kv->T], idx_dev, s);
+    gather_indices(kv->rank, kv->off, off_dev, kv->T, c.layers * c.hkv, kv->R, o[kv->T], idx_dev, ctx->dstatus, s);
   }
   CKLAUNCH();
   return ST_OK;
@@ -839,7 +839,9 @@ extern "C" int st_kv_status(st_ctx* ctx, st_kv* kv, void* stream) {
   CK(cudaMemcpyAsync(&h, kv->status, sizeof(int32_t), cudaMemcpyDeviceToHost, S(stream)));
   CK(cudaStreamSynchronize(S(stream)));
   CK(cudaMemsetAsync(kv->status, 0, sizeof(int32_t), S(stream)));
-  if (h != ST_OK) return fail(ctx, h, "device status: NaN retention score");
+  if (h != ST_OK)
+    return fail(ctx, h, h == ST_ECHECK ? "device status: an offset check of the checked build failed in retention"
+                                       : "device status: NaN retention score");
   return ST_OK;
 }
 
@@ -855,6 +857,7 @@ extern "C" int st_status(st_ctx* ctx, void* stream) {
                         : h == ST_ENAN   ? "device status: non-finite logits in a map operator step"
                         : h == ST_EINVAL ? "device status: a token id outside the vocabulary"
                         : h == ST_ERANGE ? "device status: a tuple id outside [0, T)"
+                        : h == ST_ECHECK ? "device status: an index or offset check of the checked build failed"
                                          : "device status: error");
   return ST_OK;
 }
@@ -1249,7 +1252,7 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    label_head(w.x, os, np, w.prow, w.pP, w.pop, w.pj, c.d, c.eps, ctx->w_lm, c.dtype, s);
+    label_head(w.x, os, np, w.prow, w.pP, w.pop, w.pj, c.d, c.eps, ctx->w_lm, c.dtype, M, ctx->dstatus, s);
   }
   CKLAUNCH();
   return ST_OK;

@@ -214,6 +214,37 @@ struct Work {
       qbase = 0;
     }
   }
+  // Checked build (eval items): the item's retained rows lie in its kv head's
+  // plane, its prompt and query rows in their tensors.  A failed check records
+  // ST_ECHECK and reduces the item to one query position attending to prompt
+  // row 0 (every access then lies inside the tensors; the item's outputs are
+  // not meaningful).
+  __device__ void check(const AttnParams& a, int* status) {
+#ifdef ST_CHECK
+    if (MODE != 1) return;
+    const int64_t prow_n = a.kvrows > 0 ? a.kvrows : a.qrows;
+    const bool ok = n_doc >= 0 && doc_row0 >= (int64_t)g * a.Rp_cap &&
+                    doc_row0 + n_doc <= (int64_t)(g + 1) * a.Rp_cap && P >= 1 && prompt_row0 >= 0 &&
+                    prompt_row0 + P <= prow_n && qrow0 >= 0 && rows >= 1 && qrow0 + (rows + G - 1) / G <= a.qrows;
+    if (!ST_CHECKED(ok, status)) {
+      n_doc = 0;
+      n_doc_tiles = 0;
+      doc_row0 = (int64_t)g * a.Rp_cap;
+      P = 1;
+      qoff = 0;
+      row_base = 0;
+      rows = G;
+      lim_max = 0;
+      prompt_row0 = 0;
+      qbase = 0;
+      qrow0 = 0;
+      n_tiles = 1;
+    }
+#else
+    (void)a;
+    (void)status;
+#endif
+  }
   __device__ TileInfo tile(int ti) const {
     TileInfo T;
     if (MODE == 1 && ti >= n_doc_tiles) {
@@ -350,6 +381,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         if (!ptx::mbar_wait(&bars->q_empty[qb], ((qc >> 1) & 1) ^ 1)) { ok = false; break; }
         Work<MODE, TK> W;
         W.decode(a, items, w, zb_count);
+        W.check(a, status);
         slots[qb] = W;
         ptx::mbar_arrive_expect_tx(&bars->q_full[qb], ROWS * 128);
         ptx::tma_load_3d(smem + OFF_Q + qb * ROWS * 128, &tmQ, &bars->q_full[qb], 0, W.g * W.G,

@@ -83,9 +83,10 @@ __global__ void k_stage_zero(int n, int32_t* __restrict__ out) {
   if (i < n) out[i] = 0;
 }
 __global__ void k_scatter_stage(const int32_t* __restrict__ pos, const int32_t* __restrict__ count,
-                                const int32_t* __restrict__ op_stage, int32_t* __restrict__ out) {
+                                const int32_t* __restrict__ op_stage, int32_t* __restrict__ out, int n,
+                                int* status) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < *count) out[pos[j]] = op_stage[j] + 1;
+  if (j < *count && ST_CHECKED((unsigned)pos[j] < (unsigned)n, status)) out[pos[j]] = op_stage[j] + 1;
 }
 
 }  // namespace
@@ -241,7 +242,7 @@ extern "C" int st_proxy_cascade(st_ctx* ctx, st_proxy* p, const float* x_dev, fl
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    k_scatter_stage<<<(n + 255) / 256, 256, 0, s>>>(u_pos, cnt, u_stg, stage_dev);
+    k_scatter_stage<<<(n + 255) / 256, 256, 0, s>>>(u_pos, cnt, u_stg, stage_dev, n, ctx->dstatus);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cfail(ctx, ST_ECUDA, std::string("st_proxy_cascade: merge: ") + cudaGetErrorString(e));

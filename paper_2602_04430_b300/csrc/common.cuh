@@ -28,6 +28,16 @@ struct TraceRange {
 
 typedef __nv_bfloat16 bf16;
 
+// Checked build (-DST_CHECK, libstretto_check.so): the ragged offsets and
+// indices the kernels follow are checked before use; a failed check records
+// ST_ECHECK in the given status word (first error wins) and the caller skips
+// or clamps the access.  In the regular build the condition is not evaluated.
+#ifdef ST_CHECK
+#define ST_CHECKED(cond, status) ((cond) ? true : (atomicCAS((status), ST_OK, ST_ECHECK), false))
+#else
+#define ST_CHECKED(cond, status) true
+#endif
+
 // ---------------------------------------------------------------- conversions
 template <typename T> __device__ __forceinline__ float to_f(T v);
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }

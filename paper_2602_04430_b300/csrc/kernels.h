@@ -90,7 +90,7 @@ void embed_rows(const int32_t* tok, int64_t rows, const act_t* E, int d, int voc
 // st_kv_indices: the first n_t entries of every rank-ordered segment, compacted
 // at out_off (int64 [T+1]) into idx [layers * hkv][out_off[T]].
 void gather_indices(const int32_t* rank, const int64_t* doc_off, const int64_t* out_off, int T, int LH,
-                    int64_t R, int64_t Rn, int32_t* idx, cudaStream_t s);
+                    int64_t R, int64_t Rn, int32_t* idx, int* status, cudaStream_t s);
 void embed_norm_rows(const int32_t* tok, int64_t rows, const bf16* E, int d, int vocab, float eps, float* x,
                      __half* xn, int* status, cudaStream_t s);
 template <typename act_t>
@@ -159,7 +159,7 @@ void bf16_to_f16(void* p, size_t n, cudaStream_t s);
 // Final RMSNorm of each pair's last prompt row, its operator's label logits and decision.
 void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, const int32_t* pP,
                 const int32_t* pop, const int32_t* pj, int d, float eps, const void* w_lm, int dtype,
-                cudaStream_t s);
+                int64_t rows, int* status, cudaStream_t s);
 void swiglu_from_f32(const float* t, int64_t rows, int ffn, float* h, cudaStream_t s);
 void nkeep_offp(const int64_t* off, int T, double r, int32_t* nkeep, int64_t* offp,
                 cudaStream_t s);

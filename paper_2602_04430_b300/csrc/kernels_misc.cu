@@ -589,10 +589,15 @@ template <typename w_t>
 __global__ void k_label_head(const float* __restrict__ x, OpSet os, const int32_t* __restrict__ prow,
                              const int32_t* __restrict__ pP, const int32_t* __restrict__ pop,
                              const int32_t* __restrict__ pj, int d, float eps,
-                             const w_t* __restrict__ w_lm) {
+                             const w_t* __restrict__ w_lm, int64_t rows, int* status) {
   __shared__ float red[32];
   __shared__ float z[8];
   const int i = blockIdx.x;
+  // the pair's operator, its last prompt row within the chunk's rows
+  if (!ST_CHECKED(pop[i] >= 0 && pop[i] < os.n_ops && prow[i] >= 0 && pP[i] >= 1 &&
+                      (int64_t)prow[i] + pP[i] <= rows && pj[i] >= 0 && pj[i] < os.op[pop[i]].n,
+                  status))
+    return;
   const OpDev& o = os.op[pop[i]];
   const float* xr = x + ((int64_t)prow[i] + pP[i] - 1) * d;
   float ss = 0.f;
@@ -628,12 +633,12 @@ __global__ void k_label_head(const float* __restrict__ x, OpSet os, const int32_
 
 void label_head(const float* x, const OpSet& os, int np, const int32_t* prow, const int32_t* pP,
                 const int32_t* pop, const int32_t* pj, int d, float eps, const void* w_lm, int dtype,
-                cudaStream_t s) {
+                int64_t rows, int* status, cudaStream_t s) {
   if (np <= 0) return;
   if (dtype == ST_BF16)   // the BF16 model holds its LM head as IEEE half
-    k_label_head<__half><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const __half*)w_lm);
+    k_label_head<__half><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const __half*)w_lm, rows, status);
   else
-    k_label_head<float><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const float*)w_lm);
+    k_label_head<float><<<np, 256, 0, s>>>(x, os, prow, pP, pop, pj, d, eps, (const float*)w_lm, rows, status);
 }
 
 // ------------------------------------------------------------------ weight conversion

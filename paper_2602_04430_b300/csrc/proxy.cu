@@ -283,10 +283,15 @@ __global__ void k_copy_labels(const int32_t* __restrict__ proxy_label, int n, in
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = proxy_label[i];
 }
+// (pos and count are the caller's: a position outside [0, n) is skipped and
+// recorded as ST_ERANGE)
 __global__ void k_scatter(const int32_t* __restrict__ pos, const int32_t* __restrict__ count,
-                          const int32_t* __restrict__ full, int32_t* __restrict__ out) {
+                          const int32_t* __restrict__ full, int32_t* __restrict__ out, int n, int* status) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < *count) out[pos[j]] = full[j];
+  if (j >= *count) return;
+  const int q = pos[j];
+  if ((unsigned)q < (unsigned)n) out[q] = full[j];
+  else atomicCAS(status, ST_OK, ST_ERANGE);
 }
 
 }  // namespace
@@ -508,7 +513,7 @@ extern "C" int st_cascade_merge(st_ctx* ctx, const int32_t* proxy_label_dev, int
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    k_scatter<<<(n + 255) / 256, 256, 0, s>>>(unsure_pos_dev, count_dev, full_label_dev, out_dev);
+    k_scatter<<<(n + 255) / 256, 256, 0, s>>>(unsure_pos_dev, count_dev, full_label_dev, out_dev, n, ctx->dstatus);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pfail(ctx, ST_ECUDA, cudaGetErrorString(e));

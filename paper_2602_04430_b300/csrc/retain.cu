@@ -64,6 +64,11 @@ __global__ void __launch_bounds__(kRetainThreads) k_retain_copy(RetainParams p) 
   int64_t a;
   sort_segment<T>(p, t, lg, keys, L, a);
   const int n = p.nkeep[t];
+  // the retained count within the segment, its padded copy within the capacity
+  if (!ST_CHECKED(n >= 0 && n <= L && p.offp[t + 1] - p.offp[t] == (int64_t)((n + 63) & ~63) &&
+                      p.offp[t + 1] <= p.Rp_cap,
+                  p.status))
+    return;
   const int npad = (n + 63) & ~63;
   const int hd = p.hd;
   constexpr int VN = 16 / sizeof(T);
@@ -94,6 +99,11 @@ __global__ void __launch_bounds__(kRetainThreads) k_retain_e4m3(RetainParams p) 
   int64_t a;
   sort_segment<bf16>(p, t, lg, keys, L, a);
   const int n = p.nkeep[t];
+  // the retained count within the segment, its padded copy within the capacity
+  if (!ST_CHECKED(n >= 0 && n <= L && p.offp[t + 1] - p.offp[t] == (int64_t)((n + 63) & ~63) &&
+                      p.offp[t + 1] <= p.Rp_cap,
+                  p.status))
+    return;
   const int nblk = (n + 63) >> 6;
   const int hd = p.hd;                // 64: one block = 64 rows x 64 dims = 4096 values
   const bf16* K = reinterpret_cast<const bf16*>(p.K) + ((int64_t)lg * p.R + a) * hd;
@@ -178,19 +188,21 @@ int retain(const RetainParams& p, cudaStream_t s) {
 // ranking covers the whole segment, so every r reads a prefix of it).
 __global__ void k_gather_indices(const int32_t* __restrict__ rank, const int64_t* __restrict__ doc_off,
                                  const int64_t* __restrict__ out_off, int64_t R, int64_t Rn,
-                                 int32_t* __restrict__ idx) {
+                                 int32_t* __restrict__ idx, int* status) {
   const int t = blockIdx.x, lg = blockIdx.y;
   const int64_t o = out_off[t];
   const int n = (int)(out_off[t + 1] - o);
+  // the indices copied lie in the tuple's rank segment, the output in the index array
+  if (!ST_CHECKED(n >= 0 && n <= doc_off[t + 1] - doc_off[t] && o + n <= Rn, status)) return;
   const int32_t* src = rank + (int64_t)lg * R + doc_off[t];
   int32_t* dst = idx + (int64_t)lg * Rn + o;
   for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
 }
 
 void gather_indices(const int32_t* rank, const int64_t* doc_off, const int64_t* out_off, int T, int LH,
-                    int64_t R, int64_t Rn, int32_t* idx, cudaStream_t s) {
+                    int64_t R, int64_t Rn, int32_t* idx, int* status, cudaStream_t s) {
   if (T <= 0 || LH <= 0 || Rn <= 0) return;
-  k_gather_indices<<<dim3((unsigned)T, (unsigned)LH), 128, 0, s>>>(rank, doc_off, out_off, R, Rn, idx);
+  k_gather_indices<<<dim3((unsigned)T, (unsigned)LH), 128, 0, s>>>(rank, doc_off, out_off, R, Rn, idx, status);
 }
 
 }  // namespace st

@@ -16,9 +16,11 @@ import numpy as np
 from . import synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libstretto.so")
+# STRETTO_CHECK=1 selects the checked build (index and offset checks, -DST_CHECK)
+LIB_PATH = os.path.join(HERE, "libstretto_check.so" if os.environ.get("STRETTO_CHECK") == "1"
+                        else "libstretto.so")
 
-ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ENAN, ST_EUNSUPPORTED, ST_ERANGE = range(8)
+ST_OK, ST_EINVAL, ST_ENOMEM, ST_ECUDA, ST_ETIMEOUT, ST_ENAN, ST_EUNSUPPORTED, ST_ERANGE, ST_ECHECK = range(9)
 ST_SCORE_EA_LITE, ST_SCORE_EA_FULL = 0, 1
 ST_F32, ST_BF16, ST_E4M3 = 0, 1, 2
 ST_WS_BUILD, ST_WS_EVAL, ST_WS_ANY = 0, 1, 2

@@ -60,3 +60,16 @@ def test_binding_covers_every_declared_function(libst):
     assert bound == set(declared_functions())
     for name in bound:
         assert getattr(libst, name).argtypes is not None
+
+
+def test_checked_build_exports_every_declared_symbol():
+    """The checked build (-DST_CHECK: index and offset checks that record
+    ST_ECHECK) is the same library with the same exports."""
+    from paper_2602_04430_b300 import build
+    path = build.build(check=True)
+    assert os.path.basename(path) == "libstretto_check.so"
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = ctypes.c_void_p()
+    assert lib.st_create(None, None, None, ctypes.byref(out)) == 1   # ST_EINVAL on the host
