@@ -471,13 +471,16 @@ int st_proxy_cascade(st_ctx* ctx, st_proxy* p, const float* x_dev, float tau, in
  * eval_rows: prompt rows per pass through the layers (the evaluation is cut
  * into chunks of at most this many rows; 0 = library default 262144);
  * attn_nb: tensor-core attention layout, 1 = two CTAs per SM with single S /
- * P / O buffers (default; E4M3 KV then runs 64-key tiles), 2 = one CTA per SM
- * with double buffers; longest_first: attention work items ordered by retained document
+ * P / O buffers (default; 128-key tiles, 64-key tiles with E4M3 KV), 2 = one
+ * CTA per SM with double buffers, 3 = as 1 but with 128-key tiles and one f16
+ * stage for E4M3 KV (the same as 1 for BF16 KV); longest_first: attention work
+ * items ordered by retained document
  * length, longest first (1, default) or in arrival order (0).  ms: measured
  * time of one evaluation (autotuner output).
  * st_autotune_eval times the batched evaluation of its arguments (which it
  * runs, writing the outputs) under candidate schedules — a coordinate search:
- * layout x order at the current chunk size, then chunk sizes 2^15 .. 2^19 —
+ * layout (1, 2, and 3 for E4M3 KV) x order at the current chunk size, then
+ * chunk sizes 2^15 .. 2^19 —
  * each one warm-up and three timed runs (CUDA events on `stream`; it
  * synchronises), keeps the fastest in the context for later evaluations and
  * graphs, and returns it in *best; the first max_tried timed candidates go to

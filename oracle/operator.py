@@ -114,23 +114,35 @@ def retain(scores: np.ndarray, r: float) -> np.ndarray:
 
 
 def retained_kv(cache: KVCache, r: float, idx: Optional[list] = None, kv_fp8: bool = False,
-                fp8_arith: str = "f64"):
+                fp8_arith: str = "f64", fp8_profile_r: Optional[float] = None):
     """Gather the retained keys / values of every (layer, kv head).
 
     ``idx[l][g]`` overrides the retained index lists (to evaluate the operator on
     an externally chosen set); ``kv_fp8`` replaces each by its per-block E4M3
     dequantisation.
+
+    ``fp8_profile_r`` (with ``kv_fp8``): the operator reads an E4M3 profile
+    retained at this larger ratio (one profile shared by operators of smaller
+    r, the retained sets being nested prefixes of one rank order, Sec. 5): the
+    64-slot blocks and their scales are those of the profile's set, quantised
+    first, and the operator reads the first n_keep(L, r) of its rows (the last
+    block's scale then covers slots the operator does not read).  ``idx``, if
+    given, holds the profile's sets.
     """
     Kr, Vr, I = [], [], []
     for l in range(len(cache.k)):
         kl, vl, il = [], [], []
         for g in range(len(cache.k[l])):
-            sel = retain(cache.scores[l][g], r) if idx is None else np.asarray(idx[l][g])
+            r_set = fp8_profile_r if (kv_fp8 and fp8_profile_r is not None) else r
+            sel = retain(cache.scores[l][g], r_set) if idx is None else np.asarray(idx[l][g])
             k = cache.k[l][g][sel]
             v = cache.v[l][g][sel]
             if kv_fp8:
                 k = _fp8.quantize_blocks(k, fp8_arith)[2]
                 v = _fp8.quantize_blocks(v, fp8_arith)[2]
+            if r_set != r:
+                n = n_keep(cache.L, r)
+                sel, k, v = sel[:n], k[:n], v[:n]
             kl.append(k), vl.append(v), il.append(sel)
         Kr.append(kl), Vr.append(vl), I.append(il)
     return Kr, Vr, I

@@ -85,17 +85,36 @@ def _init(cfg, root: str, layers: int):
 def _run_one(task):
     """One tuple: its float64 cache, then every requested operator evaluation.
 
-    task = (key, tokens, ops, want_scores) with ops a list of dicts
-    {prompt, label_ids, r, kv_fp8, idx (optional [l][g] index lists)}.
+    task = (key, tokens, ops, want_scores, given) with ops a list of dicts
+    {prompt, label_ids, r, kv_fp8, idx (optional [l][g] index lists),
+    codes_from_given (optional)} and given None or (K, V), the tuple's keys and
+    values [layers][hkv][L][hd] as another implementation stored them: an op
+    with kv_fp8 and codes_from_given takes its E4M3 codes from those values in
+    float32 (a code is an integer decided by floating point; this is the same
+    decision on the same inputs), everything else from the oracle's own cache.
     Returns (key, result dict)."""
+    from . import fp8 as F8
     from . import operator as O
-    key, tokens, ops, want_scores = task
+    key, tokens, ops, want_scores, given = task
     t0 = time.perf_counter()
     c = O.kv_build(_CFG, _W, tokens)
     t1 = time.perf_counter()
     out = {"L": c.L, "logits": [], "idx": [], "build_s": t1 - t0}
     for o in ops:
-        Kr, Vr, idx = O.retained_kv(c, o["r"], idx=o.get("idx"), kv_fp8=o.get("kv_fp8", False))
+        fp8 = o.get("kv_fp8", False)
+        Kr, Vr, idx = O.retained_kv(c, o["r"], idx=o.get("idx"), kv_fp8=fp8,
+                                    fp8_profile_r=o.get("fp8_profile_r"))
+        if fp8 and o.get("codes_from_given", False):
+            # the codes of the profile's set from the given values, then the operator's prefix
+            Kg, Vg = given
+            pr = o.get("fp8_profile_r") or o["r"]
+            sets = o["idx"] if o.get("idx") is not None else \
+                [[O.retain(c.scores[l][g], pr) for g in range(len(idx[l]))] for l in range(len(idx))]
+            n = len(idx[0][0])
+            Kr = [[F8.quantize_blocks(np.asarray(Kg[l][g], np.float64)[np.asarray(sets[l][g])], "f32")[2][:n]
+                   for g in range(len(idx[l]))] for l in range(len(idx))]
+            Vr = [[F8.quantize_blocks(np.asarray(Vg[l][g], np.float64)[np.asarray(sets[l][g])], "f32")[2][:n]
+                   for g in range(len(idx[l]))] for l in range(len(idx))]
         out["logits"].append(O.op_eval(_CFG, _W, c.L, Kr, Vr, o["prompt"], o["label_ids"]))
         out["idx"].append([[np.asarray(i, dtype=np.int32) for i in row] for row in idx])
     out["eval_s"] = time.perf_counter() - t1
@@ -117,10 +136,11 @@ class OraclePool:
             self.pool = ctx.Pool(self.workers, initializer=_init, initargs=(cfg, self.root, layers))
 
     def run(self, docs: Dict[object, np.ndarray], ops: Sequence[dict], want_scores: bool = False,
-            idx: Optional[Dict[object, List]] = None):
+            idx: Optional[Dict[object, List]] = None, given: Optional[Dict[object, tuple]] = None):
         """Evaluate ``ops`` on every document of ``docs`` ({key: tokens}); longest
         documents first.  ``idx[key][op]``, if given, overrides the retained index
-        sets of that tuple.  Returns {key: result}."""
+        sets of that tuple; ``given[key]`` = (K, V) feeds the ops marked
+        codes_from_given (see ``_run_one``).  Returns {key: result}."""
         order = sorted(docs, key=lambda k: -len(docs[k]))
         tasks = []
         for k in order:
@@ -129,7 +149,8 @@ class OraclePool:
                 for j, o in enumerate(o_k):
                     if idx[k][j] is not None:
                         o["idx"] = idx[k][j]
-            tasks.append((k, np.asarray(docs[k], dtype=np.int64), o_k, want_scores))
+            tasks.append((k, np.asarray(docs[k], dtype=np.int64), o_k, want_scores,
+                          None if given is None else given.get(k)))
         return dict(self.pool.imap_unordered(_run_one, tasks, chunksize=1))
 
     def close(self):

@@ -42,22 +42,28 @@ constexpr int ROWS = 128;        // query rows per work item
 // Two layouts, by the number NB of S, P and O buffers:
 //   NB = 1: two CTAs per SM, each with one S, P and O buffer in 256 TMEM
 //           columns, so every SM sub-partition runs two independent softmax
-//           warps (the default; E4M3 KV then runs 64-key tiles, whose register,
-//           shared-memory and TMEM budget fits two CTAs per SM);
+//           warps (the default).  E4M3 KV runs 64-key tiles (two f16 K/V
+//           stages, 64 scores per softmax thread), whose register, shared-
+//           memory and TMEM budget fits two CTAs per SM; a selectable layout
+//           runs 128-key E4M3 tiles with one f16 K/V stage behind two raw code
+//           stages (98 KB of shared memory), S read from TMEM in two 64-column
+//           passes to fit the 128 registers two CTAs of 256 threads leave the
+//           softmax -- measured 30 % slower: with one f16 stage the widening
+//           of a tile's V waits for the previous tile's P.V;
 //   NB = 2: one CTA per SM with double buffers in 512 TMEM columns.
-// K/V stages: 2 (NB = 1) or 5 (NB = 2; 4 with E4M3 KV), and with E4M3 KV two
-// raw code stages (with 64-key tiles, 3 K/V or 4 raw stages measured no faster).
+// K/V stages: 2 (NB = 1; 1 for E4M3 128-key tiles) or 5 (NB = 2; 4 with
+// E4M3 KV), and with E4M3 KV two raw code stages.
 constexpr int ctas_per_sm(int nb) { return nb == 1 ? 2 : 1; }
 constexpr int NKV_MAX = 5, NRAW_MAX = 2;
-constexpr int nkv(bool fp8, int nb) { return nb == 1 ? 2 : (fp8 ? 4 : 5); }
+constexpr int nkv(bool fp8, int nb, int tk) { return nb == 1 ? (fp8 && tk == 128 ? 1 : 2) : (fp8 ? 4 : 5); }
 constexpr int nraw(bool fp8, int nb) { return fp8 ? 2 : 0; }
 // warps 0-3 softmax, 4 item decode + Q and K/V loads, 5 MMA issue,
 // (E4M3 KV) 6 widens the K codes to f16, 7 the V codes
 constexpr int nthreads(bool fp8) { return fp8 ? 256 : 192; }
 constexpr int OFF_Q = 0;                           // 2 x 16 KB
 constexpr int OFF_K = OFF_Q + 2 * ROWS * 128;      // nkv x 16 KB
-constexpr int off_v(bool fp8, int nb, int tk) { return OFF_K + nkv(fp8, nb) * tk * 128; }   // nkv x tk x 128 B
-constexpr int off_raw(bool fp8, int nb, int tk) { return off_v(fp8, nb, tk) + nkv(fp8, nb) * tk * 128; }
+constexpr int off_v(bool fp8, int nb, int tk) { return OFF_K + nkv(fp8, nb, tk) * tk * 128; }   // nkv x tk x 128 B
+constexpr int off_raw(bool fp8, int nb, int tk) { return off_v(fp8, nb, tk) + nkv(fp8, nb, tk) * tk * 128; }
 constexpr int raw_bytes(int tk) { return 2 * tk * HD; }   // K + V codes of one tile
 constexpr int off_bar(bool fp8, int nb, int tk) { return off_raw(fp8, nb, tk) + nraw(fp8, nb) * raw_bytes(tk); }
 constexpr int off_work(bool fp8, int nb, int tk) { return off_bar(fp8, nb, tk) + 512; }   // 2 decoded work items
@@ -280,10 +286,14 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
   static_assert(sizeof(Work<MODE, TK>) <= 128, "work slot");
   const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
   static_assert(TK == 128 || TK == 64, "tile width");
-  static_assert(!FP8 || NB == 2 || TK == 64, "E4M3 KV: double buffers, or single buffers with 64-key tiles");
-  constexpr int NKV = nkv(FP8, NB), OFF_V = off_v(FP8, NB, TK), OFF_RAW = off_raw(FP8, NB, TK);
+  constexpr int NKV = nkv(FP8, NB, TK), OFF_V = off_v(FP8, NB, TK), OFF_RAW = off_raw(FP8, NB, TK);
+  static_assert(smem_bytes(FP8, NB, TK) <= (NB == 1 ? 113u * 1024 : 227u * 1024), "shared memory per CTA");
   constexpr int RAW_BYTES = raw_bytes(TK), NRAW = FP8 ? nraw(FP8, NB) : 1;   // (1: unused with BF16 KV)
   constexpr int NCH = TK / 32, NHALF = TK / 64;   // 32-key chunks, 64-key halves of a tile
+  // scores the softmax holds in registers at once (E4M3 128-key tiles with
+  // single buffers: two CTAs of 256 threads leave 128 registers a thread)
+  constexpr int VW = (FP8 && NB == 1 && TK == 128) ? 64 : TK;
+  constexpr int CPP = VW / 32, NPASS = TK / VW;   // chunks per pass, passes over S
   constexpr uint32_t TMEM_COLS = tmem_cols(NB), COL_O = col_o(NB, TK), COL_P = col_p(NB, TK);
   const uint32_t sK0 = ptx::smem_u32(smem + OFF_K), sV0 = ptx::smem_u32(smem + OFF_V);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -469,6 +479,10 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
       bool ok = true;
       uint32_t n_tma[NKV] = {}, n_cvt[NKV] = {};   // fills of each stage by kind (parities)
       uint32_t cs = 0, cp = 0;                     // tiles whose S / P.V has been issued
+      // parity of each issued-S tile's K/V fill, read by its P.V: the S cursor
+      // runs up to NB + 1 tiles ahead, so with fewer stages than that a later
+      // fill of the same stage may already be counted when the P.V is checked
+      uint32_t vpar = 0;                           // bit (tile & 7)
       int sw = blockIdx.x, sti = 0;                // S cursor: work item, tile
       uint32_t sq = 0;                             //   and its item counter
       bool s_have = false;                         //   its item's slot and Q have landed
@@ -489,6 +503,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
             uint64_t* fb = widened ? &bars->kc_full[s] : &bars->k_full[s];
             uint32_t& nuse = widened ? n_cvt[s] : n_tma[s];
             if (ptx::mbar_test(fb, nuse & 1) && ptx::mbar_test(&bars->s_free[b], ((cs / NB) & 1) ^ 1)) {
+              vpar = (vpar & ~(1u << (cs & 7))) | ((nuse & 1u) << (cs & 7));
               ++nuse;
               ptx::tc_fence_after();
               // E4M3 KV runs the products in f16 (codes widen exactly; scales act in f32)
@@ -519,10 +534,9 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
           const int b = cp % NB, s = cp % NKV;
           const TileInfo T = W.tile(pti);
           const bool tma_v = !FP8 || T.prompt;
-          // the stage's latest fill of the tile's kind (counted when its S was
-          // issued) is this tile's
-          if ((tma_v ? ptx::mbar_test(&bars->v_full[s], (n_tma[s] - 1) & 1)
-                     : ptx::mbar_test(&bars->vc_full[s], (n_cvt[s] - 1) & 1)) &&
+          // the tile's V is in its stage once the fill recorded at its S issue lands
+          const uint32_t vp = (vpar >> (cp & 7)) & 1u;   // this tile's V fill
+          if ((tma_v ? ptx::mbar_test(&bars->v_full[s], vp) : ptx::mbar_test(&bars->vc_full[s], vp)) &&
               ptx::mbar_test(&bars->p_full[b], (cp / NB) & 1) &&
               (pti != 0 || ptx::mbar_test(&bars->o_free[ob], ((pq / NB) & 1) ^ 1))) {
             ptx::tc_fence_after();
@@ -572,10 +586,14 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     uint64_t* const empty = half == 0 ? bars->k_empty : bars->v_empty;
     uint64_t* const full = half == 0 ? bars->kc_full : bars->vc_full;
     uint8_t* const dst0 = smem + (half == 0 ? OFF_K : OFF_V);
-    // a row's four 16-byte code chunks, visited from a lane-dependent start:
-    // rows are 64 bytes apart, so lanes 2j and 2j + 1 with the same start would
-    // share banks with lanes 2j + 2 ... 2j + 7
-    const int rot = (lane >> 1) & 3;
+    // a row's four 16-byte code chunks in a lane-dependent order: lane l visits
+    // chunk perm[(l >> 1) & 3] ^ j at step j, perm = (0, 2, 3, 1).  Within each
+    // group of 8 lanes (8 consecutive rows: code rows 64 B apart, f16 rows 128 B
+    // apart under the 128-byte swizzle) that makes the 16-byte code loads and
+    // both 16-byte f16 stores of every step hit 8 distinct bank quads, i.e.
+    // conflict-free (a plain rotation (j + (l >> 1)) & 3 keeps the loads
+    // conflict-free but the swizzle folds the stores onto two quads).
+    const int rot = (0x1320 >> (4 * ((lane >> 1) & 3))) & 3;
     bool ok = true;
     uint32_t c = 0, dc = 0, qc = 0;
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
@@ -605,7 +623,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
           const uint4* src = reinterpret_cast<const uint4*>(raw + row * HD);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const int q16 = (j + rot) & 3;
+            const int q16 = rot ^ j;
             const uint4 cw = src[q16];
             const uint32_t words[4] = {cw.x, cw.y, cw.z, cw.w};
             uint32_t out[8];
@@ -711,37 +729,76 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         if (!ptx::mbar_wait(&bars->s_full[b], (c / NB) & 1)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t sb = tmem + lane_base + b * TK;
-        // the row's visible chunks of S into registers with one wait, then
-        // release the TMEM buffer
-        uint32_t v[TK];
-        ST_TMEM_LD32(sb, v);
-        if (NCH > 1 && nch > 1) ST_TMEM_LD32(sb + 32, (v + 32));
-        if (NCH > 2 && nch > 2) ST_TMEM_LD32(sb + 64, (v + (NCH > 2 ? 64 : 0)));
-        if (NCH > 3 && nch > 3) ST_TMEM_LD32(sb + 96, (v + (NCH > 3 ? 96 : 0)));
-        ptx::tmem_wait_ld();
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) ST_TMEM_TIE32((v + 32 * ch));
-        ptx::tc_fence_before();
-        ptx::mbar_arrive(&bars->s_free[b]);
-        // invisible keys of this row (ragged tail, causal limit) in the loaded
-        // chunks become -inf
-        int nvis = T.count;
+        int nvis = T.count;                          // visible keys of this row in the tile
         if (causal) nvis = min(nvis, lim - T.key0 + 1);
+        // The row's visible chunks of S into registers, CPP chunks per pass with
+        // one wait, their invisible keys (ragged tail, causal limit) as -inf.
+        // With one pass (VW = TK) the TMEM buffer is released at once; with two
+        // (E4M3 128-key tiles, whose register budget holds 64 scores) pass 1
+        // takes the row maximum and pass 2 reads each half again for the
+        // exponentials, releasing the buffer after its last read.
+        uint32_t v[VW];
+        auto load_pass = [&](int c0) {
 #pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-          const int lo = nvis - 32 * ch;    // visible keys of this chunk
-          if (ch < nch && lo < 32) {
+          for (int q = 0; q < CPP; ++q)
+            if (q == 0 || c0 + q < nch) ST_TMEM_LD32(sb + 32 * (c0 + q), (v + 32 * q));
+          ptx::tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j >= lo) v[32 * ch + j] = 0xFF800000u;
+          for (int q = 0; q < CPP; ++q) ST_TMEM_TIE32((v + 32 * q));
+#pragma unroll
+          for (int q = 0; q < CPP; ++q) {
+            const int lo = nvis - 32 * (c0 + q);    // visible keys of this chunk
+            if (c0 + q < nch && lo < 32) {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (jj >= lo) v[32 * q + jj] = 0xFF800000u;
+            }
           }
-        }
+        };
+        auto release_s = [&]() {
+          ptx::tc_fence_before();
+          ptx::mbar_arrive(&bars->s_free[b]);
+        };
         // row maximum of the scaled scores (a positive scale commutes with the max)
         float cm[4];
+        if constexpr (NPASS == 1) {
+          // every visible chunk with one wait, then the buffer is released
+          ST_TMEM_LD32(sb, v);
+          if (NCH > 1 && nch > 1) ST_TMEM_LD32(sb + 32, (v + (NCH > 1 ? 32 : 0)));
+          if (NCH > 2 && nch > 2) ST_TMEM_LD32(sb + 64, (v + (NCH > 2 ? 64 : 0)));
+          if (NCH > 3 && nch > 3) ST_TMEM_LD32(sb + 96, (v + (NCH > 3 ? 96 : 0)));
+          ptx::tmem_wait_ld();
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch)
-          cm[ch] = (ch < NCH && ch < nch) ? chunk_max(v + 32 * (ch < NCH ? ch : 0)) * ks[(ch < NCH ? ch : 0) >> 1]
-                                          : -INFINITY;
+          for (int ch = 0; ch < NCH; ++ch) ST_TMEM_TIE32((v + 32 * ch));
+          release_s();
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) {
+            const int lo = nvis - 32 * ch;    // visible keys of this chunk
+            if (ch < nch && lo < 32) {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (jj >= lo) v[32 * ch + jj] = 0xFF800000u;
+            }
+          }
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch)
+            cm[ch] = (ch < NCH && ch < nch) ? chunk_max(v + 32 * (ch < NCH ? ch : 0)) * ks[(ch < NCH ? ch : 0) >> 1]
+                                            : -INFINITY;
+        } else {
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) cm[ch] = -INFINITY;
+#pragma unroll
+          for (int p = 0; p < NPASS; ++p) {
+            if (p * CPP < nch) {
+              load_pass(p * CPP);
+#pragma unroll
+              for (int q = 0; q < CPP; ++q) {
+                const int ch = p * CPP + q;
+                if (ch < nch) cm[ch < 4 ? ch : 0] = chunk_max(v + 32 * q) * ks[ch >> 1];
+              }
+            }
+          }
+        }
         const float mx = max3(cm[0], cm[1], fmaxf(cm[2], cm[3])) * sl2;
         const bool need = mx > m + 8.f;
         if (__any_sync(0xffffffffu, need)) {
@@ -783,6 +840,13 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         uint64_t rs2[2] = {0, 0};           // packed partial row sums (+0.0f lanes)
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
+          if constexpr (NPASS > 1) {
+            if (ch % CPP == 0 && ch < nch) {
+              // pass 2: this half of the row again; S is released after its last read
+              load_pass(ch);
+              if (ch + CPP >= nch) release_s();
+            }
+          }
           if (ch < nch) {
             const float mul = sl2 * ks[ch >> 1];
             const uint64_t m2 = f2pack(mul, mul), vs2 = f2pack(vs[ch >> 1], vs[ch >> 1]);
@@ -791,7 +855,7 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
               uint32_t pk[8];
 #pragma unroll
               for (int k = 0; k < 16; k += 2) {
-                const int kk = 32 * ch + 16 * h + k;
+                const int kk = 32 * (ch % CPP) + 16 * h + k;
                 const uint64_t y = fma2((uint64_t)v[kk] | ((uint64_t)v[kk + 1] << 32), m2, nb2);
                 const uint64_t p = f2pack(ex2(f2lo(y)), ex2(f2hi(y)));
                 rs2[(k >> 1) & 1] = add2(rs2[(k >> 1) & 1], p);
@@ -971,9 +1035,11 @@ int attn_tc_eval(const AttnParams& a, int* status, cudaStream_t s) {
   const int n_work = a.n_work * a.hkv;
   const int zb = 1;   // unused in eval (the work list carries the row block)
   // layout by a.nb (0 or 1: two CTAs per SM with single buffers, 2: one CTA with
-  // double buffers); E4M3 single buffers run 64-key tiles
+  // double buffers, 3: E4M3 single buffers with 128-key tiles)
   if (fp8 && a.nb == 2)
     launch_attn<1, true, 2, 128>(a, a.work, n_work, zb, mq, mk, mv, mkp, mvp, status, s);
+  else if (fp8 && a.nb == 3)
+    launch_attn<1, true, 1, 128>(a, a.work, n_work, zb, mq, mk, mv, mkp, mvp, status, s);
   else if (fp8)
     launch_attn<1, true, 1, 64>(a, a.work, n_work, zb, mq, mk, mv, mkp, mvp, status, s);
   else if (a.nb == 2)

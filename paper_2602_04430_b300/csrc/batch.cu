@@ -158,8 +158,11 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
   const bool tc_kv = ctx->cfg.dtype == ST_BF16;   // tensor-core attention (BF16 or E4M3 KV)
   Sched bestc{start.eval_rows > 0 ? start.eval_rows : (1LL << 18), 1, 1};
   float best_ms = 1e30f, ms = 0.f;
-  for (int nb : {1, 2}) {
-    if (nb == 2 && !tc_kv) continue;
+  // layouts: 1 = two CTAs per SM (E4M3: 64-key tiles), 2 = one CTA per SM with
+  // double buffers, 3 = (E4M3 only) two CTAs per SM with 128-key tiles
+  for (int nb : {1, 2, 3}) {
+    if (nb >= 2 && !tc_kv) continue;
+    if (nb == 3 && kv->kv_dtype != ST_E4M3) continue;
     for (int lf : {1, 0}) {
       const Sched sc{bestc.eval_rows, nb, lf};
       if ((rc = time_sched(sc, &ms)) != ST_OK) break;
@@ -192,7 +195,7 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
 }
 
 extern "C" int st_set_schedule(st_ctx* ctx, const st_tune_choice* sc) {
-  if (!ctx || !sc || sc->eval_rows < 0 || sc->attn_nb < 0 || sc->attn_nb > 2)
+  if (!ctx || !sc || sc->eval_rows < 0 || sc->attn_nb < 0 || sc->attn_nb > 3)
     return bfail(ctx, ST_EINVAL, "st_set_schedule: bad argument");
   ctx->eval_rows_cap = sc->eval_rows;
   ctx->attn_nb = sc->attn_nb;

@@ -229,3 +229,39 @@ def test_bf16_contractions_match_torch_with_rounded_operands():
     for k in ("w1", "w2", "w3"):
         rel = np.abs(g[k] - g64[k]).max() / np.abs(g64[k]).max()
         assert 1e-5 < rel < 3e-2, (k, rel)
+
+
+def test_shared_e4m3_profile_blocks_are_the_profiles():
+    """An E4M3 profile retained at r_p and read by an operator of r < r_p: the
+    blocks and scales are the profile's, the operator reads the first
+    n_keep(L, r) rows.  Pinned against quantize_blocks itself on the profile's
+    rank-ordered set: equal to quantising the operator's own set when its size
+    is a multiple of 64 (blocks coincide), and differing from it only in the
+    last, partial block otherwise."""
+    from oracle import fp8 as F8
+    from oracle import operator as O
+    from paper_2602_04430_b300 import synth
+    cfg = synth.ModelConfig(layers=1, d=64, hq=2, hkv=1, hd=16, ffn=96, vocab=97, dtype="f32", name="prof")
+    w = synth.make_weights(cfg, seed=41, std=0.3)
+    doc = np.random.default_rng(42).integers(0, cfg.vocab, 256)
+    c = O.kv_build(cfg, w, doc)
+    full = O.rank_order(c.scores[0][0])
+    # same ratio: identical to the plain E4M3 path
+    a = O.retained_kv(c, 0.5, kv_fp8=True, fp8_profile_r=0.5)
+    b = O.retained_kv(c, 0.5, kv_fp8=True)
+    np.testing.assert_array_equal(a[0][0][0], b[0][0][0])
+    # n = 128 of a 256-slot profile: whole blocks, equal to quantising the prefix
+    k128 = O.retained_kv(c, 0.5, kv_fp8=True, fp8_profile_r=1.0)[0][0][0]
+    np.testing.assert_array_equal(k128, F8.quantize_blocks(c.k[0][0][full[:128]])[2])
+    # n = n_keep(256, 0.4) (not a multiple of 64): the profile's blocks, cut;
+    # a large key in the partial block beyond n sets that block's scale
+    n = O.n_keep(256, 0.4)
+    assert n % 64 != 0
+    c.k[0][0][full[n]] = 50.0 * c.k[0][0][full[n]]
+    kp = O.retained_kv(c, 0.4, kv_fp8=True, fp8_profile_r=1.0)[0][0][0]
+    prof = F8.quantize_blocks(c.k[0][0][full])[2]
+    np.testing.assert_array_equal(kp, prof[:n])
+    own = F8.quantize_blocks(c.k[0][0][full[:n]])[2]
+    cut = 64 * (n // 64)
+    np.testing.assert_array_equal(kp[:cut], own[:cut])
+    assert not np.array_equal(kp[cut:], own[cut:])    # the partial block's scale differs
