@@ -188,10 +188,10 @@ def test_config4_batching_sharded():
     of 1024 to 4096 tokens -- matches the unmodified float64 oracle (run over
     host processes) for every operator, over the GPU's retained slots, with
     the BF16 profile (<= 2e-2 normwise) and an E4M3 profile of the same cache
-    (<= 5e-2 with the oracle deciding each E4M3 code -- an integer decided by
-    floating point -- from the keys and values the GPU stored, in float32 like
-    the kernel; against codes decided from the oracle's own exact values the
-    error is reported).  The three operators share one profile retained at
+    (<= 5e-2, both with the oracle deciding each E4M3 code -- an integer
+    decided by floating point -- from its own exact keys and values, and from
+    the keys and values the GPU stored, in float32 like the kernel, which
+    isolates the implementation's error).  The three operators share one profile retained at
     r = 1, so an E4M3 operator of smaller r reads the first n_keep(L, r) codes
     of 64-slot blocks formed over the whole rank order (the oracle's
     fp8_profile_r reading);
@@ -248,10 +248,10 @@ def test_config4_batching_sharded():
             sep8 = [op.eval(kv, i) for op, i in zip(ops, ids)]
             torch.cuda.synchronize()
             model.status()
-            # BF16; E4M3 with codes from the GPU's stored values (asserted); E4M3
-            # with codes from the oracle's exact values (reported)
+            # BF16; E4M3 with codes from the GPU's stored values; E4M3 with codes
+            # from the oracle's exact values (the unmodified oracle)
             variants = (("BF16", False, False, True), ("E4M3", True, True, True),
-                        ("E4M3 exact-value codes", True, False, False))
+                        ("E4M3 exact-value codes", True, False, True))
             # the E4M3 operators read the profile retained at r = 1: its 64-slot
             # blocks are those of the whole rank order, the operator reads a prefix
             o_ops = [{"prompt": o.prompt, "label_ids": o.label_ids, "r": o.r, "kv_fp8": f8, "codes_from_given": gv,
