@@ -480,7 +480,8 @@ int st_proxy_cascade(st_ctx* ctx, st_proxy* p, const float* x_dev, float tau, in
  * st_autotune_eval times the batched evaluation of its arguments (which it
  * runs, writing the outputs) under candidate schedules — a coordinate search:
  * layout (1, 2, and 3 for E4M3 KV) x order at the current chunk size, then
- * chunk sizes 2^15 .. 2^19 —
+ * chunk sizes 2^15 .. 2^19, then (when the cache holds documents longer than
+ * 2048 slots) split-KV at 2048 retained slots —
  * each one warm-up and three timed runs (CUDA events on `stream`; it
  * synchronises), keeps the fastest in the context for later evaluations and
  * graphs, and returns it in *best; the first max_tried timed candidates go to
@@ -490,6 +491,10 @@ typedef struct {
   int64_t eval_rows;
   int32_t attn_nb;
   int32_t longest_first;
+  int32_t split_keys;   /* split-KV: retained documents longer than this many slots are cut into
+                           pieces of this many, each a separate work item whose partial
+                           result (unnormalised O, running max, row sum) a merge pass combines
+                           (0 = off, else a multiple of 128 up to 65536) */
   float ms;
 } st_tune_choice;
 int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops, const st_operator* const* ops,

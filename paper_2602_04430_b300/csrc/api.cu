@@ -998,7 +998,17 @@ size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t pairs, char* base, Eva
   b.pP = (int32_t*)take(pairs * 4);
   b.pop = (int32_t*)take(pairs * 4);
   b.pj = (int32_t*)take(pairs * 4);
-  b.order = (int32_t*)take(pairs * max_blocks * WORK_INTS * 4);
+  // (pieces: a split pair has up to 255 entries per row block, within SPLIT_SLOTS slots)
+  const int64_t entries = pairs * max_blocks + (ctx->split_keys > 0 ? SPLIT_SLOTS : 0);
+  b.order = (int32_t*)take(entries * WORK_INTS * 4);
+  b.psplit = b.mlist = b.cnt = nullptr;
+  b.part = nullptr;
+  if (ctx->split_keys > 0 && c.dtype == ST_BF16) {
+    b.psplit = (int32_t*)take(pairs * 4);
+    b.mlist = (int32_t*)take((size_t)SPLIT_SLOTS * 16);
+    b.cnt = (int32_t*)take(16);      // slots, merge entries, list entries
+    b.part = (float*)take((size_t)SPLIT_SLOTS * c.hkv * 128 * SPLIT_STRIDE * 4);
+  }
   if (w) *w = b;
   return off + 256;
 }
@@ -1085,7 +1095,8 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
   }
   if (c.dtype == ST_BF16) {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-    eval_worklist(w.nk, w.pP, w.tup, w.prow, kv->offp, np, G, 0, ctx->longest_first != 0, w.order, s);
+    eval_worklist(w.nk, w.pP, w.tup, w.prow, kv->offp, np, G, 0, ctx->longest_first != 0, w.order,
+                  ctx->split_keys, w.psplit, w.mlist, w.cnt, s);
   }
   {
     Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
@@ -1144,6 +1155,14 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
     a.rowpair = w.rowpair;
     a.work = w.order;
     a.n_work = n_entries;
+    if (w.cnt) {
+      // split-KV: the entry count is the work list kernel's (pieces add up to one
+      // entry per partial-result slot)
+      a.n_work = n_entries + SPLIT_SLOTS;
+      a.nwork_dev = w.cnt + 2;
+      a.part = w.part;
+      a.split_keys = ctx->split_keys;
+    }
     a.qrows = M;
     a.kp = w.kp;
     a.vp = w.vp;
@@ -1151,6 +1170,12 @@ int eval_chunk(st_ctx* ctx, const st_kv* kv, const OpSet& os, int p0, int p1, in
     a.kv_dtype = kv->kv_dtype;
     a.nb = ctx->attn_nb;
     RC(attention(ctx, a, nullptr, 0, s));
+    if (w.cnt) {
+      // split-KV: the pieces' partial rows into the output rows
+      Launch L(ctx, s, ST_PROF_ATTN, 0, 0);
+      split_merge(w.mlist, w.cnt, w.part, w.prow, w.pP, G, c.hq, c.hkv, (__half*)w.o, s);
+      CKLAUNCH();
+    }
     if (qscore) {
       // query-specific scores: this layer's prompt attention mass on the document slots
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
@@ -1502,7 +1527,8 @@ extern "C" int st_map_eval(st_ctx* ctx, const st_kv* kv, const st_operator* op,
     RC(eval_chunk(ctx, kv, os, i0, i0 + nc, (int64_t)i0 * P, (int64_t)nc * P, w, s, &mp));
     if (c.dtype == ST_BF16) {
       Launch L(ctx, s, ST_PROF_OTHER, 0, 0);
-      eval_worklist(w.nk, w.pP, w.tup, w.prow, kv->offp, nc, G, 1, ctx->longest_first != 0, mp.work, s);
+      eval_worklist(w.nk, w.pP, w.tup, w.prow, kv->offp, nc, G, 1, ctx->longest_first != 0, mp.work, 0, nullptr,
+                    nullptr, nullptr, s);
     }
     for (int t = 1; t < n_gen; ++t) RC(decode_step(ctx, kv, P, nc, t, w, mp, s));
   }

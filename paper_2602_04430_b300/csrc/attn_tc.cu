@@ -171,19 +171,25 @@ struct Work {
   int t, j0, L;             // prefill
   int lim_max;              // largest causal limit (query position) among the rows
   int qoff;                 // (eval) position of the first query among the prompt keys
+  int piece, pieces, pslot; // (eval, split-KV) this piece of the pair, their number, its partial-result slot
+  int k_lo, k_hi;           // retained slots of the item: [k_lo, k_hi)
   int64_t doc_row0, prompt_row0, qrow0, qbase;
 
   __device__ void decode(const AttnParams& a, const int32_t* items, int w, int zb_count) {
     G = a.hq / a.hkv;
     if (MODE == 1) {
-      // work list record (pair, 128-row block, P, retained slots, prompt row,
-      // -, offp of the tuple), longest documents first; kv head fastest
+      // work list record (pair, 128-row block | piece | pieces, P, retained
+      // slots, prompt row, partial-result slot, offp of the tuple), longest
+      // documents first; kv head fastest
       const int e = w / a.hkv;
       g = w % a.hkv;
       const int4* rec = reinterpret_cast<const int4*>(items + (int64_t)WORK_INTS * e);
       const int4 r0 = rec[0], r1 = rec[1];
       i = r0.x;
-      const int zb = r0.y;
+      const int zb = r0.y & 0xFF;
+      piece = (r0.y >> 8) & 0xFF;
+      pieces = max(1, (r0.y >> 16) & 0xFF);
+      pslot = r1.y;
       P = r0.z;                                    // prompt keys of the pair
       prompt_row0 = r1.x;
       qbase = prompt_row0;
@@ -201,8 +207,12 @@ struct Work {
       n_doc = r0.w;
       doc_row0 = (int64_t)g * a.Rp_cap + (int64_t)(((uint64_t)(uint32_t)r1.w << 32) | (uint32_t)r1.z);
       qrow0 = qbase + row_base / G;
-      n_doc_tiles = (n_doc + TK - 1) / TK;
-      n_tiles = n_doc_tiles + (min(P, lim_max + 1) + TK - 1) / TK;
+      // a piece of a split pair takes split_keys of the retained slots; the
+      // prompt's keys go with the last piece
+      k_lo = pieces > 1 ? piece * a.split_keys : 0;
+      k_hi = pieces > 1 ? min(n_doc, k_lo + a.split_keys) : n_doc;
+      n_doc_tiles = (k_hi - k_lo + TK - 1) / TK;
+      n_tiles = n_doc_tiles + (piece == pieces - 1 ? (min(P, lim_max + 1) + TK - 1) / TK : 0);
     } else {
       const int it = w / a.hkv;
       g = w % a.hkv;
@@ -218,6 +228,11 @@ struct Work {
       n_tiles = n_doc_tiles;
       qoff = 0;
       qbase = 0;
+      piece = 0;
+      pieces = 1;
+      pslot = -1;
+      k_lo = 0;
+      k_hi = L;
     }
   }
   // Checked build (eval items): the item's retained rows lie in its kv head's
@@ -235,6 +250,10 @@ struct Work {
     if (!ST_CHECKED(ok, status)) {
       n_doc = 0;
       n_doc_tiles = 0;
+      k_lo = k_hi = 0;
+      piece = 0;
+      pieces = 1;
+      pslot = -1;
       doc_row0 = (int64_t)g * a.Rp_cap;
       P = 1;
       qoff = 0;
@@ -259,8 +278,8 @@ struct Work {
       T.count = min(TK, P - T.key0);
     } else {
       T.prompt = false;
-      T.key0 = ti * TK;
-      T.count = min(TK, (MODE == 1 ? n_doc : L) - T.key0);
+      T.key0 = k_lo + ti * TK;
+      T.count = min(TK, k_hi - T.key0);
     }
     T.kc = (MODE == 0 || T.prompt) ? min(T.count, lim_max - T.key0 + 1) : T.count;
     return T;
@@ -284,6 +303,8 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
   Bars* bars = reinterpret_cast<Bars*>(smem + off_bar(FP8, NB, TK));
   Work<MODE, TK>* slots = reinterpret_cast<Work<MODE, TK>*>(smem + off_work(FP8, NB, TK));
   static_assert(sizeof(Work<MODE, TK>) <= 128, "work slot");
+  // split-KV: the work list's entry count is on the device (the launch used a bound)
+  if (MODE == 1 && a.nwork_dev) n_work = min(n_work, *a.nwork_dev * a.hkv);
   const uint32_t sQ0 = ptx::smem_u32(smem + OFF_Q);
   static_assert(TK == 128 || TK == 64, "tile width");
   constexpr int NKV = nkv(FP8, NB, TK), OFF_V = off_v(FP8, NB, TK), OFF_RAW = off_raw(FP8, NB, TK);
@@ -659,7 +680,9 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     // tile, by when its last P.V has long completed; with one, at its end.
     // O buffer ob of the item whose last tile was cl: wait for its last P.V,
     // release the buffer, write the row normalised by l (orow < 0: no row)
-    auto read_out = [&](int ob, uint32_t cl, float l, int64_t orow) -> bool {
+    // (split-KV piece: pidx >= 0 is the row's partial-result index; the
+    // unnormalised O, the running max m and the row sum l go there instead)
+    auto read_out = [&](int ob, uint32_t cl, float l, int64_t orow, int64_t pidx, float mrow) -> bool {
       if (!ptx::mbar_wait(&bars->pv_done[cl % NB], (cl / NB) & 1)) return false;
       ptx::tc_fence_after();
       const uint32_t o_addr = tmem + lane_base + COL_O + ob * HD;
@@ -676,7 +699,13 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
           ptx::tc_fence_before();
           ptx::mbar_arrive(&bars->o_free[ob]);
         }
-        if (orow >= 0) {
+        if (MODE == 1 && pidx >= 0) {
+          float* pr = a.part + pidx * SPLIT_STRIDE;
+#pragma unroll
+          for (int e = 0; e < 32; e += 4)
+            *reinterpret_cast<uint4*>(pr + 32 * h + e) = make_uint4(o0[e], o0[e + 1], o0[e + 2], o0[e + 3]);
+          if (h == 1) *reinterpret_cast<float2*>(pr + 64) = make_float2(mrow, l);
+        } else if (orow >= 0) {
 #pragma unroll
           for (int e = 0; e < 32; e += 8)
             dst[4 * h + e / 8] =
@@ -692,7 +721,8 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
     int pend_ob = 0;
     uint32_t pend_cl = 0;
     float pend_l = 0.f;
-    int64_t pend_orow = -1;
+    int64_t pend_orow = -1, pend_pidx = -1;
+    float pend_m = 0.f;
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++qc) {
       const int qb = qc & 1;
       if (!ptx::mbar_wait(&bars->q_full[qb], (qc >> 1) & 1)) { ok = false; break; }
@@ -877,32 +907,38 @@ __global__ void __launch_bounds__(nthreads(FP8), ctas_per_sm(NB))
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
         ptx::mbar_arrive(&bars->p_full[b]);
-        if (NB == 2 && ti == 0 && pend_on && !(ok = read_out(pend_ob, pend_cl, pend_l, pend_orow))) break;
+        if (NB == 2 && ti == 0 && pend_on &&
+            !(ok = read_out(pend_ob, pend_cl, pend_l, pend_orow, pend_pidx, pend_m)))
+          break;
       }
       if (!ok) break;
-      // the output row of this thread (-1: past the item's rows)
-      int64_t orow = -1;
+      // the output row of this thread (-1: past the item's rows), or for a
+      // piece of a split pair its partial-result row
+      int64_t orow = -1, pidx = -1;
       {
         const int rr = W.row_base + r, hh = rr % W.G;
         const bool row_ok = r < W.rows && (MODE == 1 || (W.j0 + pos) < W.L);
         if (row_ok) {
-          if (MODE == 1) orow = (W.qbase + pos) * a.hq + (int64_t)W.g * W.G + hh;
+          if (MODE == 1 && W.pieces > 1) pidx = ((int64_t)W.pslot * a.hkv + W.g) * ROWS + r;
+          else if (MODE == 1) orow = (W.qbase + pos) * a.hq + (int64_t)W.g * W.G + hh;
           else orow = (a.off[W.t] - a.r0 + W.j0 + pos) * a.hq + (int64_t)W.g * W.G + hh;
         }
       }
       ptx::mbar_arrive(&bars->q_empty[qb]);
       if (NB == 1) {
         // a single O buffer is read out at once
-        if (!(ok = read_out(ob, c - 1, l, orow))) break;
+        if (!(ok = read_out(ob, c - 1, l, orow, pidx, m))) break;
       } else {
         pend_on = true;
         pend_ob = ob;
         pend_cl = c - 1;
         pend_l = l;
         pend_orow = orow;
+        pend_pidx = pidx;
+        pend_m = m;
       }
     }
-    if (ok && pend_on) ok = read_out(pend_ob, pend_cl, pend_l, pend_orow);
+    if (ok && pend_on) ok = read_out(pend_ob, pend_cl, pend_l, pend_orow, pend_pidx, pend_m);
     if (!ok) atomicExch(status, ST_ETIMEOUT);
   }
   ptx::tc_fence_before();

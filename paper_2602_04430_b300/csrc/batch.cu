@@ -35,13 +35,14 @@ int bfail(st_ctx* ctx, int code, const std::string& msg) {
 // Schedule of the context while a candidate is timed.
 struct Sched {
   int64_t eval_rows;
-  int attn_nb, longest_first;
+  int attn_nb, longest_first, split_keys;
 };
-Sched get(const st_ctx* c) { return {c->eval_rows_cap, c->attn_nb, c->longest_first}; }
+Sched get(const st_ctx* c) { return {c->eval_rows_cap, c->attn_nb, c->longest_first, c->split_keys}; }
 void set(st_ctx* c, const Sched& s) {
   c->eval_rows_cap = s.eval_rows;
   c->attn_nb = s.attn_nb;
   c->longest_first = s.longest_first;
+  c->split_keys = s.split_keys;
 }
 
 }  // namespace
@@ -150,13 +151,13 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
     float t = 0.f;
     cudaEventElapsedTime(&t, a, b);
     *ms = t / 3.f;
-    log.push_back({sc.eval_rows, sc.attn_nb, sc.longest_first, *ms});
+    log.push_back({sc.eval_rows, sc.attn_nb, sc.longest_first, sc.split_keys, *ms});
     return ST_OK;
   };
   // Coordinate search: the attention layout and work order at the default
   // chunk size, then the chunk size (prompt rows per pass of the layers).
   const bool tc_kv = ctx->cfg.dtype == ST_BF16;   // tensor-core attention (BF16 or E4M3 KV)
-  Sched bestc{start.eval_rows > 0 ? start.eval_rows : (1LL << 18), 1, 1};
+  Sched bestc{start.eval_rows > 0 ? start.eval_rows : (1LL << 18), 1, 1, 0};
   float best_ms = 1e30f, ms = 0.f;
   // layouts: 1 = two CTAs per SM (E4M3: 64-key tiles), 2 = one CTA per SM with
   // double buffers, 3 = (E4M3 only) two CTAs per SM with 128-key tiles
@@ -164,7 +165,7 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
     if (nb >= 2 && !tc_kv) continue;
     if (nb == 3 && kv->kv_dtype != ST_E4M3) continue;
     for (int lf : {1, 0}) {
-      const Sched sc{bestc.eval_rows, nb, lf};
+      const Sched sc{bestc.eval_rows, nb, lf, 0};
       if ((rc = time_sched(sc, &ms)) != ST_OK) break;
       if (ms < best_ms) { best_ms = ms; bestc = sc; }
     }
@@ -175,9 +176,18 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
   for (int64_t er : {1LL << 15, 1LL << 16, 1LL << 17, 1LL << 18, 1LL << 19}) {
     if (rc != ST_OK) break;
     if (er == bestc.eval_rows || er < maxP || er > 2 * std::max<int64_t>(rows, 1 << 15)) continue;
-    const Sched sc{er, bestc.attn_nb, bestc.longest_first};
+    const Sched sc{er, bestc.attn_nb, bestc.longest_first, 0};
     if ((rc = time_sched(sc, &ms)) != ST_OK) break;
     if (ms < best_ms) { best_ms = ms; bestc = sc; }
+  }
+  // split-KV, when some retained document can be longer than a piece
+  constexpr int kSplitCandidate = 2048;
+  if (rc == ST_OK && tc_kv && kv->max_len > kSplitCandidate) {
+    const Sched sc{bestc.eval_rows, bestc.attn_nb, bestc.longest_first, kSplitCandidate};
+    if ((rc = time_sched(sc, &ms)) == ST_OK && ms < best_ms) {
+      best_ms = ms;
+      bestc = sc;
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -187,7 +197,7 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
     return rc;
   }
   set(ctx, bestc);
-  *best = {bestc.eval_rows, bestc.attn_nb, bestc.longest_first, best_ms};
+  *best = {bestc.eval_rows, bestc.attn_nb, bestc.longest_first, bestc.split_keys, best_ms};
   if (n_tried) *n_tried = (int32_t)log.size();
   if (tried)
     for (int k = 0; k < (int)log.size() && k < max_tried; ++k) tried[k] = log[k];
@@ -195,11 +205,13 @@ extern "C" int st_autotune_eval(st_ctx* ctx, const st_kv* kv, int32_t n_ops,
 }
 
 extern "C" int st_set_schedule(st_ctx* ctx, const st_tune_choice* sc) {
-  if (!ctx || !sc || sc->eval_rows < 0 || sc->attn_nb < 0 || sc->attn_nb > 3)
+  if (!ctx || !sc || sc->eval_rows < 0 || sc->attn_nb < 0 || sc->attn_nb > 3 || sc->split_keys < 0 ||
+      sc->split_keys % 128 != 0 || sc->split_keys > 65536)
     return bfail(ctx, ST_EINVAL, "st_set_schedule: bad argument");
   ctx->eval_rows_cap = sc->eval_rows;
   ctx->attn_nb = sc->attn_nb;
   ctx->longest_first = sc->longest_first != 0;
+  ctx->split_keys = sc->split_keys;
   return ST_OK;
 }
 

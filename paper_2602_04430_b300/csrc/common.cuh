@@ -160,6 +160,7 @@ struct st_ctx {
   // (0 / 1 = two CTAs per SM, 2 = one CTA per SM) and longest-first work order
   int attn_nb = 0;
   int longest_first = 1;
+  int split_keys = 0;             // split-KV piece length in retained slots (0 = off)
   // retention scores of st_kv_build (st_set_scoring): ST_SCORE_EA_LITE or
   // ST_SCORE_EA_FULL with its horizon F and the averaged rotation table
   // rope_avg[L][hd/2] = (mean cos, mean sin) over positions L .. L+F-1

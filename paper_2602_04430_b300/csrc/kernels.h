@@ -113,13 +113,22 @@ void eval_rows(const OpSet& os, int p0, int64_t row_base, int64_t rows, const in
 // documents first; G = query heads per kv head.
 // nq: query positions per pair (0: its prompt length).
 // Each entry is a fully decoded item record of WORK_INTS int32 (32 bytes, one
-// pair of 16-byte loads in the attention kernel): pair, row block, prompt
-// length, retained slots, first prompt row, (unused), and the tuple's padded
-// retained offset offp[tup] as an int64 in two words.
+// pair of 16-byte loads in the attention kernel): pair, row block | piece << 8
+// | pieces << 16, prompt length, retained slots, first prompt row, the piece's
+// partial-result slot (-1: not split), and the tuple's padded retained offset
+// offp[tup] as an int64 in two words.  split_keys > 0 (with nq = 0): a pair
+// whose retained slots exceed it is cut into pieces of split_keys slots (at
+// most 255), while SPLIT_SLOTS partial-result slots last; cnt[0] counts the
+// slots taken, cnt[1] the merge list's entries (pair, row block, first slot,
+// pieces), cnt[2] the list's entries; psplit[pair] is the pair's first slot or -1.
 constexpr int WORK_INTS = 8;
 void eval_worklist(const int32_t* nk, const int32_t* pP, const int32_t* tup, const int32_t* prow,
                    const int64_t* offp, int np, int G, int nq, bool longest_first, int32_t* list,
-                   cudaStream_t s);
+                   int split_keys, int32_t* psplit, int32_t* mlist, int32_t* cnt, cudaStream_t s);
+// Split-KV merge: for every (split pair, row block) of the merge list and kv
+// head, the output rows from the pieces' partial results (f16, O's layout).
+void split_merge(const int32_t* mlist, const int32_t* cnt, const float* part, const int32_t* prow,
+                 const int32_t* pP, int G, int hq, int hkv, __half* o, cudaStream_t s);
 template <typename act_t>
 void qstats(const act_t* q, const int64_t* off, int t0, int t1, int64_t r0, int hq, int hkv,
             int hd, float* mu, float* s2, cudaStream_t s);
@@ -207,6 +216,9 @@ struct AttnParams {
   const int32_t* pP = nullptr;    // [n] prompt length of each pair
   const int32_t* rowpair = nullptr; // [qrows] pair of each prompt row (CUDA-core path)
   const int32_t* work = nullptr;  // tensor-core path: (pair, 128-row block) entries
+  float* part = nullptr;          // split-KV partial results [slot][hkv][128 rows][SPLIT_STRIDE]
+  const int32_t* nwork_dev = nullptr;  // split-KV: the list's entry count on the device (n_work: a bound)
+  int split_keys = 0;             // split-KV piece length (0: no item is split)
   int n_work = 0;                 // entries in work
   int64_t qrows = 0;              // prompt rows of the call
   int nb = 0;                     // BF16-KV attention layout: 0 / 1 = two CTAs per SM, 2 = one
@@ -247,7 +259,14 @@ struct EvalBufs {
   int32_t *pos, *tok, *rowpair;                       // per prompt row
   int32_t *tup, *len, *nk, *prow, *pP, *pop, *pj;     // per (operator, tuple) pair
   int32_t* order;                                     // attention work list
+  // split-KV (with ctx->split_keys > 0): each split (pair, row block)'s first
+  // slot, the partial results, the merge list and two counters
+  int32_t *psplit, *mlist, *cnt;
+  float* part;
 };
+// Split-KV: partial-result slots per evaluation chunk, floats per row of a slot
+// (64 unnormalised output values, the running max, the row sum, padding).
+constexpr int SPLIT_SLOTS = 512, SPLIT_STRIDE = 68;
 // Lays the buffers for `rows` prompt rows of `pairs` (operator, tuple) pairs out
 // from `base` (nullptr: layout only); returns the bytes needed.
 size_t eval_bufs(const st_ctx* ctx, int64_t rows, int64_t pairs, char* base, EvalBufs* w);

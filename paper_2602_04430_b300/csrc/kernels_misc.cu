@@ -138,15 +138,39 @@ __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restric
                                                         const int32_t* __restrict__ tup,
                                                         const int32_t* __restrict__ prow,
                                                         const int64_t* __restrict__ offp, int n, int G,
-                                                        int nq, int sorted, int32_t* list) {
+                                                        int nq, int sorted, int32_t* list, int split_keys,
+                                                        int32_t* psplit, int32_t* mlist, int32_t* gcnt) {
   __shared__ int cnt[1024];
   __shared__ int wsum[32];
+  __shared__ int slots, merges, total;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   cnt[tid] = 0;
+  if (tid == 0) slots = merges = total = 0;
   __syncthreads();
-  auto bucket = [&](int i) { return sorted ? 1023 - min((nk[i] + 127) / 128, 1023) : 0; };
-  auto blocks = [&](int i) { return ((nq > 0 ? nq : pP[i]) * G + 127) / 128; };
-  for (int i = tid; i < n; i += 1024) atomicAdd(&cnt[bucket(i)], blocks(i));
+  const bool split = split_keys > 0 && nq == 0;
+  auto zblocks = [&](int i) { return ((nq > 0 ? nq : pP[i]) * G + 127) / 128; };
+  auto pieces = [&](int i) { return min((nk[i] + split_keys - 1) / split_keys, 255); };
+  // split pairs: reserve their partial-result slots (pieces x row blocks) while they last
+  if (split)
+    for (int i = tid; i < n; i += 1024) {
+      int base = -1;
+      if (nk[i] > split_keys) {
+        const int need = pieces(i) * zblocks(i);
+        const int b = atomicAdd(&slots, need);
+        if (b + need <= SPLIT_SLOTS) base = b;
+      }
+      psplit[i] = base;
+    }
+  __syncthreads();
+  auto np_of = [&](int i) { return (split && psplit[i] >= 0) ? pieces(i) : 1; };
+  auto bucket = [&](int i) {
+    const int keys = np_of(i) > 1 ? split_keys : nk[i];   // the longest piece of the pair
+    return sorted ? 1023 - min((keys + 127) / 128, 1023) : 0;
+  };
+  for (int i = tid; i < n; i += 1024) {
+    atomicAdd(&cnt[bucket(i)], zblocks(i) * np_of(i));
+    atomicAdd(&total, zblocks(i) * np_of(i));
+  }
   __syncthreads();
   // exclusive prefix sum over the buckets
   const int x = cnt[tid];
@@ -171,22 +195,87 @@ __global__ void __launch_bounds__(1024) k_eval_worklist(const int32_t* __restric
   cnt[tid] = wsum[wid] + inc - x;
   __syncthreads();
   for (int i = tid; i < n; i += 1024) {
-    const int nb = blocks(i);
-    const int at = atomicAdd(&cnt[bucket(i)], nb);
+    const int nz = zblocks(i), npc = np_of(i);
+    const int at = atomicAdd(&cnt[bucket(i)], nz * npc);
     const int64_t o = offp[tup[i]];
-    for (int z = 0; z < nb; ++z) {
-      int4* e = reinterpret_cast<int4*>(list + (int64_t)WORK_INTS * (at + z));
-      e[0] = make_int4(i, z, pP[i], nk[i]);
-      e[1] = make_int4(prow[i], 0, (int)(uint32_t)o, (int)(o >> 32));
+    const int base = npc > 1 ? psplit[i] : -1;
+    for (int z = 0; z < nz; ++z) {
+      for (int pc = 0; pc < npc; ++pc) {
+        int4* e = reinterpret_cast<int4*>(list + (int64_t)WORK_INTS * (at + z * npc + pc));
+        e[0] = make_int4(i, z | (pc << 8) | (npc << 16), pP[i], nk[i]);
+        e[1] = make_int4(prow[i], base >= 0 ? base + z * npc + pc : -1, (int)(uint32_t)o, (int)(o >> 32));
+      }
+      if (base >= 0) {
+        const int m = atomicAdd(&merges, 1);
+        reinterpret_cast<int4*>(mlist)[m] = make_int4(i, z, base + z * npc, npc);
+      }
     }
+  }
+  __syncthreads();
+  if (tid == 0 && gcnt) {
+    gcnt[0] = min(slots, SPLIT_SLOTS);
+    gcnt[1] = merges;
+    gcnt[2] = total;   // entries of the list (the attention's work count)
   }
 }
 
 void eval_worklist(const int32_t* nk, const int32_t* pP, const int32_t* tup, const int32_t* prow,
                    const int64_t* offp, int np, int G, int nq, bool longest_first, int32_t* list,
-                   cudaStream_t s) {
+                   int split_keys, int32_t* psplit, int32_t* mlist, int32_t* cnt, cudaStream_t s) {
   if (np <= 0) return;
-  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, tup, prow, offp, np, G, nq, longest_first ? 1 : 0, list);
+  if (!psplit || !mlist || !cnt) split_keys = 0;
+  k_eval_worklist<<<1, 1024, 0, s>>>(nk, pP, tup, prow, offp, np, G, nq, longest_first ? 1 : 0, list, split_keys,
+                                     psplit, mlist, cnt);
+}
+
+// Split-KV merge.  Block (merge entry e, kv head g), thread = query row r of
+// the entry's row block: the pieces' partial rows (O_s unnormalised, running
+// max m_s in the softmax's scaled log2 units, row sum l_s) combine as
+// O = sum_s 2^(m_s - M) O_s / sum_s 2^(m_s - M) l_s with M = max_s m_s, written
+// as the f16 output row the unsplit item would have written.
+__global__ void __launch_bounds__(128) k_split_merge(const int32_t* __restrict__ mlist,
+                                                     const int32_t* __restrict__ cnt,
+                                                     const float* __restrict__ part,
+                                                     const int32_t* __restrict__ prow,
+                                                     const int32_t* __restrict__ pP, int G, int hq, int hkv,
+                                                     __half* __restrict__ o) {
+  const int e = blockIdx.x, g = blockIdx.y, r = threadIdx.x;
+  if (e >= cnt[1]) return;
+  const int4 m4 = reinterpret_cast<const int4*>(mlist)[e];
+  const int i = m4.x, z = m4.y, slot0 = m4.z, ns = m4.w;
+  const int rows = min(128, pP[i] * G - z * 128);
+  if (r >= rows) return;
+  auto row_of = [&](int sidx) { return part + (((int64_t)(slot0 + sidx) * hkv + g) * 128 + r) * SPLIT_STRIDE; };
+  float M = -INFINITY;
+  for (int sidx = 0; sidx < ns; ++sidx) M = fmaxf(M, row_of(sidx)[64]);
+  float acc[64];
+#pragma unroll
+  for (int c = 0; c < 64; ++c) acc[c] = 0.f;
+  float L = 0.f;
+  for (int sidx = 0; sidx < ns; ++sidx) {
+    const float* pr = row_of(sidx);
+    const float w = exp2f(pr[64] - M);
+    L += w * pr[65];
+#pragma unroll
+    for (int c = 0; c < 64; c += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(pr + c);
+      acc[c] += w * v.x;
+      acc[c + 1] += w * v.y;
+      acc[c + 2] += w * v.z;
+      acc[c + 3] += w * v.w;
+    }
+  }
+  const float inv = L > 0.f ? 1.f / L : 0.f;
+  const int rr = z * 128 + r;
+  const int64_t orow = ((int64_t)prow[i] + rr / G) * hq + (int64_t)g * G + rr % G;
+  __half2* dst = reinterpret_cast<__half2*>(o + orow * 64);
+#pragma unroll
+  for (int c = 0; c < 64; c += 2) dst[c / 2] = __floats2half2_rn(acc[c] * inv, acc[c + 1] * inv);
+}
+
+void split_merge(const int32_t* mlist, const int32_t* cnt, const float* part, const int32_t* prow,
+                 const int32_t* pP, int G, int hq, int hkv, __half* o, cudaStream_t s) {
+  k_split_merge<<<dim3(SPLIT_SLOTS, (unsigned)hkv), 128, 0, s>>>(mlist, cnt, part, prow, pP, G, hq, hkv, o);
 }
 
 // Retained counts and padded (64-slot) offsets of every tuple, one block.

@@ -60,11 +60,12 @@ VP = ctypes.c_void_p
 class TuneChoice(ctypes.Structure):
     """st_tune_choice: an operator-evaluation schedule and its measured time."""
     _fields_ = [("eval_rows", ctypes.c_int64), ("attn_nb", ctypes.c_int32),
-                ("longest_first", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("longest_first", ctypes.c_int32), ("split_keys", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self):
         return {"eval_rows": int(self.eval_rows), "attn_nb": int(self.attn_nb),
-                "longest_first": int(self.longest_first), "ms": float(self.ms)}
+                "longest_first": int(self.longest_first), "split_keys": int(self.split_keys),
+                "ms": float(self.ms)}
 
 
 class StageDesc(ctypes.Structure):
@@ -633,8 +634,9 @@ def autotune(model: Model, kv: KVCache, ops, tuple_ids, logits=None, labels=None
     return best.as_dict(), [tried[i].as_dict() for i in range(nt.value)]
 
 
-def set_schedule(model: Model, eval_rows: int = 0, attn_nb: int = 1, longest_first: int = 1):
-    sc = TuneChoice(int(eval_rows), int(attn_nb), int(longest_first), 0.0)
+def set_schedule(model: Model, eval_rows: int = 0, attn_nb: int = 1, longest_first: int = 1,
+                 split_keys: int = 0):
+    sc = TuneChoice(int(eval_rows), int(attn_nb), int(longest_first), int(split_keys), 0.0)
     model.check(model.L.st_set_schedule(model.h, ctypes.byref(sc)))
 
 

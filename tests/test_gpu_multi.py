@@ -161,7 +161,7 @@ def test_autotune_schedules_agree(bf16_env):
     model.status()
     assert len(tried) >= 4 and best["ms"] == min(t["ms"] for t in tried)
     for sc in tried:
-        st.set_schedule(model, sc["eval_rows"], sc["attn_nb"], sc["longest_first"])
+        st.set_schedule(model, sc["eval_rows"], sc["attn_nb"], sc["longest_first"], sc["split_keys"])
         lg, lb = st.eval_multi(model, kv, ops, sets)
         torch.cuda.synchronize()
         model.status()
