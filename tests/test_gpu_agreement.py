@@ -22,7 +22,7 @@ configuration.  Compared per sampled tuple:
   oracle score lies within twice the largest GPU-oracle score difference of the
   oracle's boundary score; the mean overlap is reported.
 
-Bars (the benchmark spec): BF16 logits <= 2e-2 with >= 99.5 % agreement; E4M3 KV
+Bars: BF16 logits <= 2e-2 with >= 99.5 % agreement; E4M3 KV
 <= 5e-2 with >= 99 % agreement, against the oracle's own E4M3 variant.
 """
 import numpy as np
