@@ -319,6 +319,7 @@ class KVCache:
             kv_dtype = ST_BF16 if self.model.cfg.dtype == "bf16" else ST_F32
         self.model.check(self.L.st_kv_retain(self.model.h, self.h, float(r), int(kv_dtype),
                                              _stream(stream)))
+        self.kv_dtype, self.r = int(kv_dtype), float(r)
 
     def status(self, stream=None):
         self.model.check(self.L.st_kv_status(self.model.h, self.h, _stream(stream)))
