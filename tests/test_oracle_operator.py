@@ -292,6 +292,36 @@ def test_oracle_pool_matches_serial_oracle():
                     np.testing.assert_allclose(res[t]["scores"][l][g], c.scores[l][g], rtol=1e-12)
 
 
+def test_oracle_pool_codes_from_given_values_and_shared_profiles():
+    """The pool's E4M3 options: codes decided from given keys and values (here
+    the oracle's own, so the result must equal its float32-arithmetic E4M3
+    path), and a profile shared at a larger r (the operator reads a prefix of
+    the profile's quantised set), on given index sets."""
+    from oracle import pool as OP
+    cfg = synth.ModelConfig(layers=2, d=32, hq=4, hkv=2, hd=8, ffn=48, vocab=64, dtype="f32", name="q")
+    w = synth.make_weights(cfg, seed=51, std=0.2)
+    table = synth.make_table_from_lengths([70, 150], cfg.vocab, seed=52)
+    op = synth.make_prompt(4, cfg.vocab, seed=53, r=0.4)
+    docs = {t: table["tokens"][table["offsets"][t]:table["offsets"][t + 1]] for t in range(2)}
+    caches = {t: O.kv_build(cfg, w, d) for t, d in docs.items()}
+    given = {t: (c.k, c.v) for t, c in caches.items()}
+    full = {t: [[O.rank_order(c.scores[l][g]) for g in range(cfg.hkv)] for l in range(cfg.layers)]
+            for t, c in caches.items()}
+    ops = [{"prompt": op.prompt, "label_ids": op.label_ids, "r": 0.4, "kv_fp8": True, "codes_from_given": True,
+            "fp8_profile_r": 1.0},
+           {"prompt": op.prompt, "label_ids": op.label_ids, "r": 0.4, "kv_fp8": True, "fp8_profile_r": 1.0}]
+    idx = {t: [full[t], full[t]] for t in docs}
+    with OP.OraclePool(cfg, w, workers=2) as pool:
+        res = pool.run(docs, ops, idx=idx, given=given)
+    for t, c in caches.items():
+        Kr, Vr, _ = O.retained_kv(c, 0.4, kv_fp8=True, fp8_arith="f32", fp8_profile_r=1.0)
+        z32 = O.op_eval(cfg, w, c.L, Kr, Vr, op.prompt, op.label_ids)
+        np.testing.assert_allclose(res[t]["logits"][0], z32, rtol=1e-12, atol=1e-12)
+        Kr, Vr, _ = O.retained_kv(c, 0.4, kv_fp8=True, fp8_profile_r=1.0)
+        z64 = O.op_eval(cfg, w, c.L, Kr, Vr, op.prompt, op.label_ids)
+        np.testing.assert_allclose(res[t]["logits"][1], z64, rtol=1e-12, atol=1e-12)
+
+
 def test_oracle_workers_hold_a_cache_and_match_serial_oracle():
     """Persistent workers (the benchmark's CPU legs): each builds one tuple's
     cache, then every step evaluates the operator on it; the logits equal a
